@@ -1,0 +1,179 @@
+"""CPU oracle for the CHIME X-engine correlation.  TEST INFRASTRUCTURE ONLY.
+
+Only ``tests/``, ``__graft_entry__.smoke()`` and the CPU legs of ``bench.py``
+(``cpu_baseline`` and ``--impl reference``) may import this package.  The product
+path (``paper_2005_09481_gb300``) never imports it and shares no code with it.
+
+Two forms of the same definition, V_ij = sum_t x_i(t) conj(x_j(t)) for i <= j
+(Denman et al. 2020, section 1 and section 2.2; 4-bit real + 4-bit imaginary samples,
+section 2.2; channels independent, section 2.3):
+
+* ``correlate`` / ``pairs``: the plain C triple loop in ``xe_oracle.c`` (int64).
+* ``correlate_dense``: the definition written as the matrix product V = X X^H with a
+  library complex128 matmul.  It is exact, not approximate: every product and every
+  partial sum is an integer of magnitude below 2 * 64 * T, far below 2**53, so no
+  floating-point rounding can occur in any summation order.  It exists so that full
+  outputs at N=2048 can be checked in seconds; tests pin it to the C loop.
+
+Readings where the paper is silent (listed in the design doc as well): high nibble = real,
+low nibble = imaginary, two's complement, conjugate on the second index, row-major
+packed upper triangle with {Re, Im} interleaved.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xe_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libxe_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile the C oracle (gcc -O2 -fopenmp, plain C; no target-specific flags)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    if not force and os.path.exists(_LIB) and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC):
+        return _LIB
+    tmp = _LIB + f".{os.getpid()}.tmp"
+    subprocess.check_call(["gcc", "-O2", "-fopenmp", "-std=c11", "-fPIC", "-shared",
+                           "-o", tmp, _SRC])
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            i64, p = ctypes.c_int64, ctypes.c_void_p
+            lib.xe_oracle_decode.argtypes = [p, i64, p, p]
+            lib.xe_oracle_tri_index.argtypes = [i64, i64, i64]
+            lib.xe_oracle_tri_index.restype = i64
+            lib.xe_oracle_n_baselines.argtypes = [i64]
+            lib.xe_oracle_n_baselines.restype = i64
+            lib.xe_oracle_correlate.argtypes = [p, i64, i64, i64, p]
+            lib.xe_oracle_correlate.restype = ctypes.c_int
+            lib.xe_oracle_pairs.argtypes = [p, i64, i64, i64, p, p, p, p]
+            lib.xe_oracle_pairs.restype = ctypes.c_int
+            lib.xe_oracle_cmac.argtypes = [i64, i64, i64]
+            lib.xe_oracle_cmac.restype = ctypes.c_double
+            lib.xe_oracle_threads.restype = ctypes.c_int
+            _lib = lib
+    return _lib
+
+
+def _ptr(a: np.ndarray) -> int:
+    return a.ctypes.data
+
+
+def decode(packed: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+    """Packed bytes -> (re, im) int64 arrays of the same shape."""
+    b = np.ascontiguousarray(packed, dtype=np.uint8)
+    re = np.empty(b.shape, np.int64)
+    im = np.empty(b.shape, np.int64)
+    _load().xe_oracle_decode(_ptr(b), b.size, _ptr(re), _ptr(im))
+    return re, im
+
+
+def tri_index(N: int, i: int, j: int) -> int:
+    return int(_load().xe_oracle_tri_index(N, i, j))
+
+
+def n_baselines(N: int) -> int:
+    return int(_load().xe_oracle_n_baselines(N))
+
+
+def cmac(N: int, T: int, C: int = 1) -> float:
+    """Complex MACs of one correlation, C * T * N(N+1)/2 (section 2.2, eta / delta-nu)."""
+    return float(_load().xe_oracle_cmac(N, T, C))
+
+
+def threads() -> int:
+    return int(_load().xe_oracle_threads())
+
+
+def _check_in(packed: np.ndarray, N: int, T: int, C: int) -> np.ndarray:
+    b = np.ascontiguousarray(packed, dtype=np.uint8).reshape(-1)
+    if b.size != C * T * N:
+        raise ValueError(f"packed has {b.size} bytes, expected C*T*N = {C * T * N}")
+    return b
+
+
+def correlate64(packed: np.ndarray, N: int, T: int, C: int = 1) -> np.ndarray:
+    """Plain C triple loop.  Returns int64 [C, N(N+1)/2, 2]."""
+    b = _check_in(packed, N, T, C)
+    out = np.empty((C, n_baselines(N), 2), np.int64)
+    rc = _load().xe_oracle_correlate(_ptr(b), N, T, C, _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_correlate rejected its arguments")
+    return out
+
+
+def to_int32(v64: np.ndarray) -> np.ndarray:
+    """int64 visibilities -> int32, refusing values that do not fit (overflow reading)."""
+    if v64.size and (v64.max() > np.iinfo(np.int32).max or v64.min() < np.iinfo(np.int32).min):
+        raise OverflowError("visibility does not fit int32")
+    return v64.astype(np.int32)
+
+
+def correlate(packed: np.ndarray, N: int, T: int, C: int = 1) -> np.ndarray:
+    """Plain C triple loop, int32 result [C, N(N+1)/2, 2]."""
+    return to_int32(correlate64(packed, N, T, C))
+
+
+def pairs(packed: np.ndarray, N: int, T: int, C: int, c, i, j) -> np.ndarray:
+    """Selected baselines (c[k], i[k], j[k]) one by one; int64 [n, 2]."""
+    b = _check_in(packed, N, T, C)
+    c = np.ascontiguousarray(c, np.int64)
+    i = np.ascontiguousarray(i, np.int64)
+    j = np.ascontiguousarray(j, np.int64)
+    if not (c.shape == i.shape == j.shape) or (c.size and c.max() >= C):
+        raise ValueError("bad pair arrays")
+    out = np.empty((c.size, 2), np.int64)
+    rc = _load().xe_oracle_pairs(_ptr(b), N, T, c.size, _ptr(c), _ptr(i), _ptr(j), _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_pairs rejected a pair")
+    return out
+
+
+def voltages(packed_chan: np.ndarray, N: int, T: int) -> np.ndarray:
+    """One channel's packed [T][N] bytes -> complex128 X with X[i, t] = x_i(t)."""
+    re, im = decode(np.asarray(packed_chan, np.uint8).reshape(T, N))
+    return (re + 1j * im).T.astype(np.complex128)
+
+
+def correlate_dense(packed: np.ndarray, N: int, T: int, C: int = 1,
+                    t_chunk: int = 4096) -> np.ndarray:
+    """V = X X^H with a complex128 library matmul; int32 [C, N(N+1)/2, 2].
+
+    The time sum is taken in chunks of ``t_chunk`` samples (the sum over t is an exact
+    integer sum, so splitting it changes nothing).  Exact while 2*64*T < 2**53.
+    """
+    b = _check_in(packed, N, T, C).reshape(C, T, N)
+    iu = np.triu_indices(N)               # row-major (i, j >= i): the packed order
+    out = np.empty((C, n_baselines(N), 2), np.int64)
+    for c in range(C):
+        V = np.zeros((N, N), np.complex128)
+        for t0 in range(0, T, t_chunk):
+            X = voltages(b[c, t0:t0 + t_chunk], N, min(t_chunk, T - t0))
+            V += X @ X.conj().T
+        tri = V[iu]
+        out[c, :, 0] = np.rint(tri.real).astype(np.int64)
+        out[c, :, 1] = np.rint(tri.imag).astype(np.int64)
+    return to_int32(out)
+
+
+def unpack_triangle(vis: np.ndarray, N: int) -> np.ndarray:
+    """Packed [N(N+1)/2, 2] -> full Hermitian complex matrix (test helper)."""
+    iu = np.triu_indices(N)
+    V = np.zeros((N, N), np.complex128)
+    V[iu] = vis[:, 0] + 1j * vis[:, 1]
+    V[(iu[1], iu[0])] = vis[:, 0] - 1j * vis[:, 1]
+    return V

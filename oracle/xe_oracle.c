@@ -1,0 +1,138 @@
+/*
+ * xe_oracle.c -- CPU oracle for the X-engine correlation.  TEST INFRASTRUCTURE ONLY.
+ *
+ * Only tests/, __graft_entry__.smoke() and bench.py's cpu_baseline / reference arm may
+ * load this library.  It shares no code, header or table with the CUDA path.
+ *
+ * What it computes (Denman et al., "A GPU Spatial Processing System for CHIME",
+ * arXiv 2005.09481):
+ *   - section 1 (introduction): the signal of each receiver is correlated against every
+ *     other receiver, per frequency channel, after channelisation ("FX" correlator);
+ *   - section 2.2 ("Computational Requirements"): the X stage includes the
+ *     autocorrelations, i.e. N(N+1)/2 complex multiply-accumulates per sample, and the
+ *     samples carry 4 bits of real and 4 bits of imaginary part (d = 8 bits);
+ *   - section 2.3 ("GPU Processing Nodes"): frequency channels are processed
+ *     independently.
+ * The quantity itself is the visibility V_ij = sum_t x_i(t) * conj(x_j(t)) for i <= j,
+ * accumulated exactly in integers.  The paper prints no formula for V_ij; the readings
+ * taken where it is silent are:
+ *   (R1) byte layout: high nibble = real part, low nibble = imaginary part;
+ *   (R2) nibble encoding: two's complement, values -8..7;
+ *   (R3) conjugation on the second index: x_i * conj(x_j);
+ *   (R4) output: row-major upper triangle including the diagonal,
+ *        idx(i,j) = i*N - i*(i-1)/2 + (j - i), {Re, Im} interleaved.
+ *
+ * This file is the plain definition: decode each byte, then a triple loop over
+ * (i <= j, t) accumulating in int64.  No blocking, no reordering, no vectorisation
+ * tricks.  OpenMP only distributes the independent rows i over cores.
+ */
+#include <stdint.h>
+#include <stddef.h>
+
+/* (R1), (R2): one packed sample byte -> (re, im), each a two's-complement 4-bit integer. */
+static void decode_sample(uint8_t byte, int64_t *re, int64_t *im)
+{
+    int64_t hi = (byte >> 4) & 0xF;
+    int64_t lo = byte & 0xF;
+    *re = (hi >= 8) ? hi - 16 : hi;
+    *im = (lo >= 8) ? lo - 16 : lo;
+}
+
+/* Exported decode, for the decode-table pin (all 256 bytes). */
+void xe_oracle_decode(const uint8_t *bytes, int64_t n, int64_t *re, int64_t *im)
+{
+    for (int64_t k = 0; k < n; ++k)
+        decode_sample(bytes[k], &re[k], &im[k]);
+}
+
+/* (R4): position of baseline (i, j), i <= j, in the packed upper triangle. */
+int64_t xe_oracle_tri_index(int64_t N, int64_t i, int64_t j)
+{
+    return i * N - (i * (i - 1)) / 2 + (j - i);
+}
+
+/* Number of baselines including autocorrelations, N(N+1)/2 (section 2.2). */
+int64_t xe_oracle_n_baselines(int64_t N)
+{
+    return N * (N + 1) / 2;
+}
+
+/* One visibility: V_ij = sum_t x_i(t) conj(x_j(t)) over channel data in[t][n].
+ * Re{(a + ib)(p - iq)} = a p + b q,  Im{(a + ib)(p - iq)} = b p - a q. */
+static void visibility(const uint8_t *chan, int64_t N, int64_t T, int64_t i, int64_t j,
+                       int64_t *sr, int64_t *si)
+{
+    int64_t acc_re = 0, acc_im = 0;
+    for (int64_t t = 0; t < T; ++t) {
+        int64_t a, b, p, q;
+        decode_sample(chan[t * N + i], &a, &b);
+        decode_sample(chan[t * N + j], &p, &q);
+        acc_re += a * p + b * q;
+        acc_im += b * p - a * q;
+    }
+    *sr = acc_re;
+    *si = acc_im;
+}
+
+/*
+ * Full correlation.  in: uint8 [C][T][N]; vis: int64 [C][N(N+1)/2][2].
+ * Returns 0, or -1 on bad sizes.
+ */
+int xe_oracle_correlate(const uint8_t *in, int64_t N, int64_t T, int64_t C, int64_t *vis)
+{
+    if (N < 1 || T < 0 || C < 1 || !in || !vis)
+        return -1;
+    const int64_t B = xe_oracle_n_baselines(N);
+    for (int64_t c = 0; c < C; ++c) {
+        const uint8_t *chan = in + c * T * N;
+        int64_t *out = vis + c * B * 2;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < N; ++i) {
+            for (int64_t j = i; j < N; ++j) {
+                int64_t sr, si;
+                visibility(chan, N, T, i, j, &sr, &si);
+                int64_t k = xe_oracle_tri_index(N, i, j);
+                out[2 * k + 0] = sr;
+                out[2 * k + 1] = si;
+            }
+        }
+    }
+    return 0;
+}
+
+/*
+ * Selected baselines only (for sampled checks at full size): for each k,
+ * (c[k], i[k], j[k]) with i <= j; out: int64 [n][2].  Returns 0, or -1 on a bad pair.
+ */
+int xe_oracle_pairs(const uint8_t *in, int64_t N, int64_t T, int64_t n,
+                    const int64_t *c, const int64_t *i, const int64_t *j, int64_t *out)
+{
+    for (int64_t k = 0; k < n; ++k)
+        if (i[k] < 0 || j[k] < i[k] || j[k] >= N || c[k] < 0)
+            return -1;
+#pragma omp parallel for schedule(dynamic, 16)
+    for (int64_t k = 0; k < n; ++k) {
+        int64_t sr, si;
+        visibility(in + c[k] * T * N, N, T, i[k], j[k], &sr, &si);
+        out[2 * k + 0] = sr;
+        out[2 * k + 1] = si;
+    }
+    return 0;
+}
+
+/* Complex multiply-accumulates of one correlation: C * T * N(N+1)/2 (section 2.2). */
+double xe_oracle_cmac(int64_t N, int64_t T, int64_t C)
+{
+    return (double)C * (double)T * (double)xe_oracle_n_baselines(N);
+}
+
+/* Threads OpenMP will use (reported beside the CPU timing). */
+int xe_oracle_threads(void)
+{
+#ifdef _OPENMP
+    extern int omp_get_max_threads(void);
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
