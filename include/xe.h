@@ -1,0 +1,225 @@
+/*
+ * xe.h -- C ABI of libxe, an exact X-engine correlator for GB300 (sm_103a).
+ *
+ * The operation (Denman et al. 2020, "A GPU Spatial Processing System for CHIME",
+ * section 1 and section 2.2): for every frequency channel, correlate every receiver input
+ * against every other, autocorrelations included:
+ *
+ *     V_ij = sum_{t < T} x_i(t) * conj(x_j(t)),   0 <= i <= j < N,
+ *
+ * over channelised complex voltages with 4 bits real + 4 bits imaginary per sample
+ * (section 2.2, d = 8).  Channels are independent (section 2.3).  The sums are exact
+ * integers: every call returns bit-identical results for the same input.
+ *
+ * Data formats (shared by every entry point):
+ *   input   uint8  in[C][T][N]   one byte per sample; high nibble = real part, low
+ *                                nibble = imaginary part, each two's complement (-8..7).
+ *                                Per channel, time-major: all N inputs of one sample are
+ *                                contiguous (the corner-turned order, section 2.3).
+ *   output  int32  vis[C][B][2]  B = N(N+1)/2 baselines, row-major upper triangle
+ *                                including the diagonal: baseline (i, j), i <= j, is at
+ *                                k = i*N - i*(i-1)/2 + (j - i); {Re, Im} interleaved
+ *                                (8 bytes per visibility, as in Table tab:data-flow).
+ *
+ * Ownership: unless an entry point says otherwise, `in` and `vis` are caller-owned
+ * DEVICE pointers (e.g. torch tensors on cuda).  The library never frees them.  Work is
+ * enqueued on the given stream (0 = the legacy default stream) and the call returns
+ * without synchronising; the caller synchronises the stream before reading `vis`.
+ * Scratch memory is owned by the library, cached per device, and reused across calls.
+ *
+ * Errors: every int-returning entry point returns XE_OK (0) or a negative XE_E* code.
+ * A failed call enqueues nothing and leaves `vis` untouched.  xe_last_error() gives a
+ * human-readable detail of the last failure on the calling thread.
+ *
+ * Exactness limit: |Re|, |Im| <= 128 * T must fit int32, so T <= XE_MAX_T.
+ */
+#ifndef XE_H
+#define XE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define XE_OK         0
+#define XE_EINVAL    -1   /* bad argument: N < 1, T < 1, C < 1, null or misaligned pointer */
+#define XE_EOVERFLOW -2   /* T > XE_MAX_T: the int32 result could overflow */
+#define XE_ENOMEM    -3   /* device or host allocation failed */
+#define XE_EBUDGET   -4   /* a stream request exceeds its HBM budget */
+#define XE_EAGAIN    -5   /* nothing ready yet / not admitted now; try again */
+#define XE_ETIMEOUT  -6   /* a bounded device or host wait gave up */
+#define XE_ECUDA     -7   /* a CUDA runtime call failed (detail in xe_last_error) */
+#define XE_ENODEV    -8   /* no usable sm_103 device */
+#define XE_ECLOSED   -9   /* the stream was closed */
+
+#define XE_MAX_T 16777215LL   /* 128 * T < 2^31 */
+#define XE_MAX_N 65536
+
+/* Kernel families.  XE_ALGO_TC is the tcgen05 tensor-core path (FP8 e4m3 operands,
+ * exact because every operand is an integer in [-8, 8] and every partial sum stays below
+ * 2^24); XE_ALGO_IMMA is the legacy warp-level int8 mma.sync path (exact by construction,
+ * int32 accumulate).  XE_ALGO_AUTO picks XE_ALGO_TC. */
+#define XE_ALGO_AUTO 0
+#define XE_ALGO_TC   1
+#define XE_ALGO_IMMA 2
+
+/* ---- library ------------------------------------------------------------------- */
+
+/* Human-readable name of an XE_* code.  Never NULL; the string is static. */
+const char *xe_strerror(int code);
+
+/* Detail of the last failed call on this thread (static per-thread buffer). */
+const char *xe_last_error(void);
+
+/* Library version as 10000*major + 100*minor + patch. */
+int xe_version(void);
+
+/* Number of complex multiply-accumulates of one correlation: C * T * N(N+1)/2
+ * (the cost metric eta / delta-nu of section 2.2). */
+double xe_cmac(int64_t N, int64_t T, int64_t C);
+
+/* ---- one-shot correlation (section 2.2 X stage) ------------------------------------ */
+
+/* Correlate C channels of N inputs over T samples: in (device) -> vis (device), on the
+ * current legacy default stream.  vis is overwritten, never accumulated into.
+ * Returns XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_ECUDA or XE_ENODEV. */
+int xe_correlate(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis);
+
+/* As xe_correlate, enqueued on `stream` (a cudaStream_t passed as void*), with an
+ * explicit kernel family (XE_ALGO_*). */
+int xe_correlate_async(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis,
+                       int algo, void *stream);
+
+/* As xe_correlate, but `host_in` and `host_vis` are HOST pointers (pinned memory gives the
+ * full copy bandwidth).  The library copies the input to device memory it owns, correlates
+ * and copies the visibilities back before returning (synchronous).  For callers that do
+ * not manage device memory.  Returns as xe_correlate. */
+int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis,
+                      int algo);
+
+/* ---- batched correlation (one persistent launch over many jobs) ------------------- */
+
+/* One job of a batch: n_chan channels of N inputs over T samples, with its own
+ * device input and output pointers in the formats above. */
+typedef struct xe_job {
+    const uint8_t *in;
+    int32_t *vis;
+    int N;
+    int n_chan;
+    int64_t T;
+} xe_job;
+
+/* Correlate every job of the batch (jobs may differ in N and T) in ONE persistent
+ * kernel launch whose work list covers all triangle tiles of all jobs; jobs[] is a
+ * host array read during the call.  With use_graph != 0, the launch sequence is captured
+ * into a CUDA graph keyed on the batch shape and replayed on later calls of the same
+ * shape (pointers are refreshed in place).  Returns as xe_correlate_async. */
+int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stream);
+
+/* ---- host-side planning (no GPU needed; exposed for tests and tooling) ------------ */
+
+/* Work plan the persistent scheduler would use for a batch: number of triangle tiles,
+ * total k-iterations and the number of CTA segments that end in a partial (split) tile,
+ * for `n_cta` persistent CTAs.  Pure host computation; returns XE_OK or XE_EINVAL. */
+int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
+                  int64_t *n_tiles, int64_t *n_iters, int64_t *n_split_tiles);
+
+/* ---- streaming server (continuous integration of frames) --------------------------- */
+
+typedef struct xe_stream_cfg {
+    int N;                    /* inputs per channel */
+    int64_t frame_T;          /* samples per frame (e.g. 8192) */
+    int64_t integ_T;          /* samples per integration, a multiple of frame_T (e.g. 32768) */
+    int max_chan;             /* channel slots to admit at most */
+    int64_t hbm_budget;       /* bytes of device memory the stream may hold */
+    int ring_frames;          /* frame slots in the device ring per channel (>= 2) */
+    double sample_rate;       /* samples/s per channel the producer emits (390625 for CHIME) */
+    int device_source;        /* 1: xe_stream_push takes device pointers; 0: host pointers */
+} xe_stream_cfg;
+
+typedef struct xe_stream xe_stream;
+
+/* One completed integration returned by xe_stream_poll. */
+typedef struct xe_result {
+    int chan;                 /* channel slot */
+    int64_t integ_index;      /* integration number within the channel (0, 1, ...) */
+    int64_t n_samples;        /* samples accumulated (== integ_T unless frames were lost) */
+    int complete;             /* 1 if every frame of the integration arrived */
+    const int32_t *vis;       /* HOST pointer, [B][2] int32; valid until xe_stream_release */
+    int64_t t_first_arrival_ns; /* arrival time of the integration's first frame */
+    int64_t t_last_arrival_ns;  /* arrival time of its last frame */
+    int64_t t_ready_ns;       /* time the visibilities were on the host */
+    int64_t handle;           /* pass to xe_stream_release */
+} xe_result;
+
+/* Open a stream on the current device.  Validates the configuration, checks that at
+ * least one channel slot fits the HBM budget, and allocates nothing per channel until
+ * channels are admitted.  Returns XE_OK and *out, or XE_EINVAL / XE_EBUDGET / XE_ENOMEM. */
+int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out);
+
+/* Admit a channel slot if the HBM budget allows it.  Returns XE_OK, XE_EBUDGET when the
+ * budget is full, XE_EINVAL for a bad channel id. */
+int xe_stream_admit(xe_stream *s, int chan);
+
+/* Release a channel slot (its pending integration is dropped, its memory returned). */
+int xe_stream_evict(xe_stream *s, int chan);
+
+/* Push one frame (frame_T samples x N inputs, [T][N] packed bytes) of channel `chan`
+ * with sequence number `seq` (frame index since the channel started) and arrival time
+ * t_arrival_ns (CLOCK_MONOTONIC).  The bytes are copied before the call returns (host
+ * source) or before the frame's slot is reused (device source).  Returns XE_OK,
+ * XE_EAGAIN when the channel's ring is full, XE_EINVAL for an unknown channel or a frame
+ * older than the open integration, XE_ECLOSED after close. */
+int xe_stream_push(xe_stream *s, int chan, const uint8_t *frame, int64_t seq,
+                   int64_t t_arrival_ns);
+
+/* Flush what has been pushed so far: schedule every ready frame now. */
+int xe_stream_flush(xe_stream *s);
+
+/* Return the next completed integration, or XE_EAGAIN if none is ready yet.  Blocks for
+ * at most timeout_ms milliseconds (0 = do not block). */
+int xe_stream_poll(xe_stream *s, xe_result *r, int timeout_ms);
+
+/* Hand a result buffer back to the stream. */
+int xe_stream_release(xe_stream *s, int64_t handle);
+
+/* Counters: admitted channels, frames processed, integrations completed, frames dropped. */
+int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *integrations,
+                    int64_t *dropped);
+
+/* Close the stream: stops its threads, waits (bounded) for in-flight work and frees all
+ * of its memory.  Results not yet released become invalid. */
+void xe_stream_close(xe_stream *s);
+
+/* ---- diagnostics -------------------------------------------------------------------- */
+
+/* Tuning / diagnostic options (process-wide; take effect on the next call):
+ *   "operand_bytes"  1 = FP8 e4m3 tensor-core operands (default), 2 = f16 operands;
+ *   "exact_chunk_t"  samples summed by one f32 tensor-memory accumulation before the
+ *                    partial sum is moved to int32 (64 .. 131072, default 131072);
+ *   "n_cta"          persistent CTAs per launch (0 = one per SM, the default);
+ *   "timing"         1 = record device times of each call (see xe_last_timing).
+ * Returns XE_OK or XE_EINVAL. */
+int xe_set_option(const char *key, int64_t value);
+
+/* Synchronise `stream`, then read and clear the device status word of the scratch bound
+ * to it.  Returns XE_OK, or XE_ETIMEOUT if a kernel gave up on a bounded wait (its output
+ * is then invalid). */
+int xe_device_status(void *stream);
+
+/* Bit pattern of the small integer v in [-16, 16] as an MMA operand: e4m3 when
+ * elem_bytes == 1, f16 when elem_bytes == 2.  Host-only; for tests of the encoder. */
+uint32_t xe_debug_operand_code(int v, int elem_bytes);
+
+/* Device time in milliseconds of the kernels of the last xe_correlate* call on this
+ * thread, split as {stage, correlate}; filled only when timing was enabled with
+ * xe_set_timing(1).  Returns XE_OK or XE_EAGAIN if nothing was recorded. */
+int xe_set_timing(int enable);
+int xe_last_timing(float *stage_ms, float *correlate_ms);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* XE_H */

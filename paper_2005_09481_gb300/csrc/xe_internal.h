@@ -1,0 +1,96 @@
+// xe_internal.h -- structures shared by the libxe kernels and the host runtime.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace xe {
+
+// ---- tensor-core tiling (tcgen05 path) ------------------------------------------------
+constexpr int kBM = 128;           // inputs i per tile (MMA M)
+constexpr int kBN = 256;           // inputs j per tile (MMA N; 128 on half tiles)
+constexpr int kRowBytes = 64;      // bytes of one operand row per pipeline stage
+constexpr int kStages = 4;         // shared-memory pipeline depth
+constexpr int kNPad = 256;         // inputs are padded to a multiple of this (zeros)
+constexpr int kAPlane = kBM * kRowBytes;              // 8 KB
+constexpr int kBPlane = kBN * kRowBytes;              // 16 KB
+constexpr int kStageBytes = 2 * kAPlane + 2 * kBPlane;  // 48 KB
+constexpr int kTcThreads = 192;    // 4 epilogue warps, 1 producer warp, 1 MMA warp
+constexpr int kTcSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kMaxJobs = 128;      // jobs per launch (passed by value)
+
+// Samples per stage: 64 with 1-byte (e4m3) operands, 32 with 2-byte (f16) operands.
+__host__ __device__ constexpr int samples_per_stage(int elem_bytes) {
+    return kRowBytes / elem_bytes;
+}
+
+// Largest sample count one f32 tensor-memory accumulator may sum before its partial sums
+// could leave the exactly-representable integer range (|partial| <= 128 per sample,
+// kept below 2^24).
+constexpr int64_t kExactChunkT = (1LL << 24) / 128;  // 131072
+
+// One job as the kernels see it.
+struct JobDev {
+    const uint8_t *in;        // packed input [C][T][N]
+    const uint8_t *planes;    // staged operands [C][kblocks][2][n_pad][64 B]
+    int32_t *vis;             // output [C][B][2]
+    int64_t T;                // samples in this launch (time window)
+    int64_t t0;               // first sample of the window within `in`
+    int64_t T_in;             // samples per channel in `in` (row stride over channels)
+    int64_t plane_chan_bytes; // bytes of planes per channel
+    int64_t vis_chan_elems;   // int32 elements of vis per channel (= 2B)
+    int N;
+    int n_pad;
+    int C;
+    int kblocks;              // ceil(T / samples_per_stage)
+    int64_t stage_block0;     // first block of this job in the stage (or anchor) grid
+};
+
+struct JobTable {
+    int n_jobs;
+    int accumulate;           // 1: add into vis instead of overwriting
+    int64_t total_stage_blocks;
+    JobDev jobs[kMaxJobs];
+};
+
+// One output tile of the triangle: rows [i0, i0+128), columns [j0, j0+nj).
+struct Tile {
+    int job;
+    int chan;
+    int i0;
+    int j0;
+    int nj;                   // 256, or 128 on half tiles next to the diagonal
+    int kblocks;              // k-iterations (pipeline stages) of this tile
+    int64_t iter_begin;       // prefix sum of kblocks over the tile list
+};
+
+// Device-resident plan of one persistent launch.
+struct PlanDev {
+    const Tile *tiles;
+    int n_tiles;
+    int n_cta;
+    int64_t total_iters;
+    int32_t *ws;              // partial-tile workspace: 2 slots per CTA
+    int *counters;            // one arrival counter per tile, zero between launches
+    int *status;              // device status word (0 = ok)
+};
+
+constexpr int64_t kWsSlotElems = 2LL * kBN * kBM;  // re and im planes, [col][row] int32
+
+enum DeviceStatus : int {
+    kStatusOk = 0,
+    kStatusTimeoutProducer = 1,
+    kStatusTimeoutMma = 2,
+    kStatusTimeoutEpilogue = 3,
+};
+
+// Kernel launchers (xe_tc.cu, xe_imma.cu).
+cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s);
+cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s);
+cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
+int64_t imma_blocks(int N, int C);
+int tc_smem_bytes();
+
+// Host encoders of a small integer as an MMA operand (e4m3 for 1 byte, f16 for 2 bytes).
+uint32_t operand_code(int v, int elem_bytes);
+
+}  // namespace xe

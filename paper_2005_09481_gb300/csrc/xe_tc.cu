@@ -1,0 +1,487 @@
+// xe_tc.cu -- the tensor-core X-engine: operand staging and the tcgen05 correlation kernel.
+//
+// The X stage of an FX correlator (Denman et al. 2020, sections 1 and 2.2): for every
+// channel, V_ij = sum_t x_i(t) conj(x_j(t)) over all i <= j, autocorrelations included.
+// With x = a + ib this is four real products,
+//     Re V = A_I A_J^T + B_I B_J^T,     Im V = B_I A_J^T - A_I B_J^T,
+// where A and B are the real and imaginary planes (inputs x time).  Each is a dense
+// integer contraction over time, run here on the 5th-generation tensor cores.
+//
+// sm_103a has no integer tcgen05 kind, so the operands are carried as FP8 e4m3 (or f16):
+// every sample component is an integer in [-8, 7], exactly representable, every product
+// is an integer of magnitude <= 64, and every partial sum is an integer of magnitude
+// below 2^24 as long as one accumulation covers at most 131072 samples, so the f32
+// tensor-memory accumulator holds the exact integer.  The host splits longer integrations.
+//
+// Kernels:
+//   stage_kernel  packed 4+4-bit bytes [T][N] -> per-stage operand planes [kb][re|im][n][64 B]
+//                 in the exact shared-memory image the MMA reads (64-byte swizzle), so the
+//                 correlation kernel fetches each plane tile with one bulk copy.
+//   tc_kernel     persistent, one CTA per SM, stream-K over all triangle tiles of all jobs:
+//                 warp 4 streams planes into a 4-stage shared-memory ring with bulk copies,
+//                 warp 5 issues tcgen05.mma (M=128, N=256/128, K=32 bytes) into two f32
+//                 accumulators in tensor memory (Re: columns 0-255, Im: 256-511),
+//                 warps 0-3 drain them (tcgen05.ld), convert to int32 and store the packed
+//                 upper triangle.  A tile split between CTAs is summed exactly through a
+//                 workspace by the last CTA to finish it (arrival counter, no spinning).
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "xe_internal.h"
+#include "xe_ptx.cuh"
+
+namespace xe {
+
+// ---- operand encodings ---------------------------------------------------------------
+
+// e4m3: sign bit 7, 4-bit exponent (bias 7) in bits 3-6, 3-bit mantissa.  Integers up to
+// 16 in magnitude are exact.  f16: sign bit 15, 5-bit exponent (bias 15), 10-bit mantissa.
+__host__ __device__ constexpr uint32_t encode_small_int(int v, int elem_bytes) {
+    if (v == 0) return 0u;
+    const uint32_t neg = v < 0 ? 1u : 0u;
+    const int m = v < 0 ? -v : v;
+    const int e = m >= 16 ? 4 : m >= 8 ? 3 : m >= 4 ? 2 : m >= 2 ? 1 : 0;
+    const int frac = m - (1 << e);
+    if (elem_bytes == 1)
+        return (neg << 7) | (uint32_t(e + 7) << 3) | uint32_t(frac << (3 - e));
+    return (neg << 15) | (uint32_t(e + 15) << 10) | uint32_t(frac << (10 - e));
+}
+
+uint32_t operand_code(int v, int elem_bytes) { return encode_small_int(v, elem_bytes); }
+
+__host__ __device__ constexpr int nibble_value(int nib) { return nib >= 8 ? nib - 16 : nib; }
+
+struct NibbleCodes {
+    uint16_t c[16];
+};
+__host__ __device__ constexpr NibbleCodes make_codes(int elem_bytes) {
+    NibbleCodes t{};
+    for (int n = 0; n < 16; ++n) t.c[n] = uint16_t(encode_small_int(nibble_value(n), elem_bytes));
+    return t;
+}
+__constant__ NibbleCodes c_codes_e4m3 = make_codes(1);
+__constant__ NibbleCodes c_codes_f16 = make_codes(2);
+
+// ---- staging kernel ----------------------------------------------------------------------
+
+__device__ __forceinline__ int find_job(const JobTable &jt, int64_t blk) {
+    int lo = 0, hi = jt.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jt.jobs[mid].stage_block0 <= blk) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+// One block: KS samples x 256 inputs of one channel -> the re and im plane tiles
+// (256 rows x 64 bytes each) of pipeline stage kb.
+template <int EB>
+__global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ JobTable jt) {
+    constexpr int KS = samples_per_stage(EB);
+    __shared__ __align__(16) uint8_t raw[KS][256];
+    __shared__ uint32_t lut[256];
+
+    const int tid = threadIdx.x;
+    {
+        const NibbleCodes &nc = EB == 1 ? c_codes_e4m3 : c_codes_f16;
+        lut[tid] = uint32_t(nc.c[tid >> 4]) | (uint32_t(nc.c[tid & 15]) << 16);
+    }
+
+    const int64_t blk = blockIdx.x;
+    const JobDev &jb = jt.jobs[find_job(jt, blk)];
+    const int64_t local = blk - jb.stage_block0;
+    const int nblk = jb.n_pad / 256;
+    const int nb = int(local % nblk);
+    const int64_t rest = local / nblk;
+    const int kb = int(rest % jb.kblocks);
+    const int c = int(rest / jb.kblocks);
+    const int n0 = nb * 256;
+    const int64_t t0 = int64_t(kb) * KS;
+    const uint8_t *src = jb.in + (int64_t(c) * jb.T_in + jb.t0) * jb.N;
+
+    // Load the packed [KS][256] tile; zeros outside [0,T) x [0,N) (value 0 + 0i, exact).
+    if ((jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0) {
+        const int seg = tid & 15;          // 16-byte segment of the 256-byte row
+        for (int r = tid >> 4; r < KS; r += 16) {
+            const int64_t t = t0 + r;
+            const int n = n0 + seg * 16;
+            uint4 v = make_uint4(0, 0, 0, 0);
+            if (t < jb.T && n < jb.N)
+                v = __ldg(reinterpret_cast<const uint4 *>(src + t * jb.N + n));
+            *reinterpret_cast<uint4 *>(&raw[r][seg * 16]) = v;
+        }
+    } else {
+        for (int r = 0; r < KS; ++r) {
+            const int64_t t = t0 + r;
+            const int n = n0 + tid;
+            raw[r][tid] = (t < jb.T && n < jb.N) ? src[t * jb.N + n] : uint8_t(0);
+        }
+    }
+    __syncthreads();
+
+    // Row n0+tid of both planes: 4 chunks of 16 bytes each, 64-byte swizzle.
+    const int row = n0 + tid;
+    uint8_t *pre = const_cast<uint8_t *>(jb.planes) + int64_t(c) * jb.plane_chan_bytes +
+                   ((int64_t(kb) * 2 + 0) * jb.n_pad + row) * kRowBytes;
+    uint8_t *pim = pre + int64_t(jb.n_pad) * kRowBytes;
+    const int sw = (tid >> 1) & 3;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t wr[4], wi[4];
+        if (EB == 1) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                uint32_t xr = 0, xi = 0;
+#pragma unroll
+                for (int b = 0; b < 4; ++b) {
+                    const uint32_t code = lut[raw[q * 16 + w * 4 + b][tid]];
+                    xr |= (code & 0xFFu) << (8 * b);
+                    xi |= ((code >> 16) & 0xFFu) << (8 * b);
+                }
+                wr[w] = xr;
+                wi[w] = xi;
+            }
+        } else {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t c0 = lut[raw[q * 8 + w * 2 + 0][tid]];
+                const uint32_t c1 = lut[raw[q * 8 + w * 2 + 1][tid]];
+                wr[w] = (c0 & 0xFFFFu) | (c1 << 16);
+                wi[w] = (c0 >> 16) | (c1 & 0xFFFF0000u);
+            }
+        }
+        const int off = ((q ^ sw) << 4);
+        *reinterpret_cast<uint4 *>(pre + off) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+        *reinterpret_cast<uint4 *>(pim + off) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
+    }
+}
+
+cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s) {
+    if (jt.total_stage_blocks <= 0) return cudaSuccess;
+    if (jt.total_stage_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
+    const dim3 grid(unsigned(jt.total_stage_blocks));
+    if (elem_bytes == 1) stage_kernel<1><<<grid, 256, 0, s>>>(jt);
+    else stage_kernel<2><<<grid, 256, 0, s>>>(jt);
+    return cudaGetLastError();
+}
+
+// ---- persistent tensor-core correlation kernel -----------------------------------------------
+
+__device__ __forceinline__ int find_tile(const PlanDev &p, int64_t it) {
+    int lo = 0, hi = p.n_tiles - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (p.tiles[mid].iter_begin <= it) lo = mid; else hi = mid - 1;
+    }
+    return lo;
+}
+
+__device__ __forceinline__ int64_t range_start(int64_t b, int64_t W, int64_t G) {
+    return b * W / G;
+}
+
+// The CTA whose iteration range holds iteration x (all ranges are non-empty: G <= W).
+__device__ __forceinline__ int64_t cta_of(int64_t x, int64_t W, int64_t G) {
+    return ((x + 1) * G - 1) / W;
+}
+
+__device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
+
+__device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
+
+// Store (or add) one row run of final visibilities: row i, columns j0+col0 .. +31.
+__device__ __forceinline__ void store_run(const JobDev &jb, int chan, int i, int jbase,
+                                          const int (&re)[32], const int (&im)[32], int acc) {
+    if (i >= jb.N) return;
+    const int64_t N = jb.N;
+    int32_t *rowp = jb.vis + int64_t(chan) * jb.vis_chan_elems +
+                    2 * (int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 - i);
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        const int j = jbase + k;
+        if (j >= i && j < jb.N) {
+            int2 *p = reinterpret_cast<int2 *>(rowp + 2 * int64_t(j));
+            if (acc) {
+                const int2 o = *p;
+                *p = make_int2(o.x + re[k], o.y + im[k]);
+            } else {
+                *p = make_int2(re[k], im[k]);
+            }
+        }
+    }
+}
+
+template <int EB>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_kernel(const __grid_constant__ JobTable jt, const __grid_constant__ PlanDev plan) {
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>(
+        (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    uint64_t *full = reinterpret_cast<uint64_t *>(smem + kStages * kStageBytes);
+    uint64_t *empty = full + kStages;
+    uint64_t *acc_full = empty + kStages;
+    uint64_t *acc_empty = acc_full + 1;
+    uint64_t *drain = acc_empty + 1;
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    volatile int *epi_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    volatile int *status = plan.status;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&full[s], 1);
+            mbar_init(&empty[s], 1);
+        }
+        mbar_init(acc_full, 1);
+        mbar_init(acc_empty, 128);
+        mbar_init(drain, 1);
+        fence_mbar_init();
+    }
+    if (warp == 5) {
+        tmem_alloc(tmem_slot, 512);
+        tmem_relinquish();
+    }
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = *tmem_slot;
+
+    const int64_t G = plan.n_cta;
+    const int64_t W = plan.total_iters;
+    const int64_t b = blockIdx.x;
+    const int64_t r_start = range_start(b, W, G);
+    const int64_t r_end = range_start(b + 1, W, G);
+    const int t_first = find_tile(plan, r_start);
+    constexpr uint32_t kFmt = 0;  // E4M3 for kind::f8f6f4, F16 for kind::f16
+
+    if (warp == 4) {
+        // ---------------- producer: bulk copies of plane tiles ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t ph = 0;
+            int64_t fills = 0;
+            bool ok = true;
+            for (int t = t_first; ok && t < plan.n_tiles && plan.tiles[t].iter_begin < r_end; ++t) {
+                const Tile tl = plan.tiles[t];
+                const JobDev &jb = jt.jobs[tl.job];
+                const int64_t lo = (r_start > tl.iter_begin ? r_start : tl.iter_begin) - tl.iter_begin;
+                const int64_t te = tl.iter_begin + tl.kblocks;
+                const int64_t hi = (r_end < te ? r_end : te) - tl.iter_begin;
+                const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
+                const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
+                for (int64_t k = lo; k < hi; ++k) {
+                    if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
+                        set_status(plan.status, kStatusTimeoutProducer);
+                        ok = false;
+                        break;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], 2 * kAPlane + 2 * bbytes);
+                    uint8_t *st = smem + stage * kStageBytes;
+                    const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
+                    const uint8_t *pim = pre + int64_t(jb.n_pad) * kRowBytes;
+                    bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
+                    bulk_g2s(st + kAPlane, pim + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
+                    bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
+                    bulk_g2s(st + 2 * kAPlane + kBPlane, pim + int64_t(tl.j0) * kRowBytes, bbytes,
+                             &full[stage]);
+                    ++fills;
+                    if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                }
+            }
+            if (!ok) {
+                // Let copies already in flight land before the CTA can exit.
+                const int64_t n = fills < kStages ? fills : kStages;
+                int s = stage;
+                uint32_t p = ph;
+                for (int64_t q = 0; q < n; ++q) {
+                    if (--s < 0) { s = kStages - 1; p ^= 1u; }
+                    const long long t0 = clock64();
+                    while (!mbar_try_wait(&full[s], p) && clock64() - t0 < kWaitBudgetCycles) {}
+                }
+            }
+        }
+    } else if (warp == 5) {
+        // ---------------- MMA issuer ----------------
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t ph = 0, acc_ph = 0;
+            bool ok = true;
+            const uint32_t d_re = tmem, d_im = tmem + 256;
+            for (int t = t_first; ok && t < plan.n_tiles && plan.tiles[t].iter_begin < r_end; ++t) {
+                const Tile tl = plan.tiles[t];
+                const int64_t lo = (r_start > tl.iter_begin ? r_start : tl.iter_begin) - tl.iter_begin;
+                const int64_t te = tl.iter_begin + tl.kblocks;
+                const int64_t hi = (r_end < te ? r_end : te) - tl.iter_begin;
+                const uint32_t idesc = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, false);
+                const uint32_t idesc_neg = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, true);
+                if (!mbar_wait(acc_empty, acc_ph ^ 1u, status)) {
+                    set_status(plan.status, kStatusTimeoutMma);
+                    ok = false;
+                    break;
+                }
+                acc_ph ^= 1u;
+                tc_fence_after();
+                for (int64_t k = lo; k < hi; ++k) {
+                    if (!mbar_wait(&full[stage], ph, status)) {
+                        set_status(plan.status, kStatusTimeoutMma);
+                        ok = false;
+                        break;
+                    }
+                    tc_fence_after();
+                    const uint32_t base = smem_u32(smem + stage * kStageBytes);
+#pragma unroll
+                    for (int s = 0; s < 2; ++s) {
+                        const uint32_t off = 32u * s;
+                        const uint64_t a_re = sdesc_k_sw64(base + off);
+                        const uint64_t a_im = sdesc_k_sw64(base + kAPlane + off);
+                        const uint64_t b_re = sdesc_k_sw64(base + 2 * kAPlane + off);
+                        const uint64_t b_im = sdesc_k_sw64(base + 2 * kAPlane + kBPlane + off);
+                        const uint32_t acc = (k > lo || s > 0) ? 1u : 0u;
+                        if (EB == 1) {
+                            mma_f8f6f4(d_re, a_re, b_re, idesc, acc);      // + A_I A_J^T
+                            mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);       // + B_I B_J^T
+                            mma_f8f6f4(d_im, a_im, b_re, idesc, acc);      // + B_I A_J^T
+                            mma_f8f6f4(d_im, a_re, b_im, idesc_neg, 1u);   // - A_I B_J^T
+                        } else {
+                            mma_f16(d_re, a_re, b_re, idesc, acc);
+                            mma_f16(d_re, a_im, b_im, idesc, 1u);
+                            mma_f16(d_im, a_im, b_re, idesc, acc);
+                            mma_f16(d_im, a_re, b_im, idesc_neg, 1u);
+                        }
+                    }
+                    mma_commit(&empty[stage]);
+                    if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                }
+                if (ok) mma_commit(acc_full);
+            }
+            if (!ok) {
+                // Wait (bounded) for every MMA already issued before TMEM is released.
+                mma_commit(drain);
+                const long long t0 = clock64();
+                while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitBudgetCycles) {}
+            }
+        }
+    } else {
+        // ---------------- epilogue: TMEM -> int32 -> packed triangle ----------------
+        uint32_t acc_ph = 0;
+        const int r = warp * 32 + lane;
+        const uint32_t lane_base = uint32_t(warp * 32) << 16;
+        for (int t = t_first; t < plan.n_tiles && plan.tiles[t].iter_begin < r_end; ++t) {
+            const Tile tl = plan.tiles[t];
+            const JobDev &jb = jt.jobs[tl.job];
+            const int64_t tb = tl.iter_begin;
+            const int64_t te = tb + tl.kblocks;
+            if (threadIdx.x == 0) {
+                const bool ok = mbar_wait(acc_full, acc_ph, status);
+                if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
+                *epi_flag = ok ? 1 : 0;
+            }
+            epi_bar();
+            if (*epi_flag == 0) break;
+            acc_ph ^= 1u;
+            tc_fence_after();
+
+            const int i = tl.i0 + r;
+            const bool whole = r_start <= tb && r_end >= te;
+            if (whole) {
+                for (int cc = 0; cc < tl.nj; cc += 32) {
+                    uint32_t fre[32], fim[32];
+                    tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
+                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + cc, fim);
+                    tmem_ld_wait();
+                    int re[32], im[32];
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        re[k] = __float2int_rn(__uint_as_float(fre[k]));
+                        im[k] = __float2int_rn(__uint_as_float(fim[k]));
+                    }
+                    store_run(jb, tl.chan, i, tl.j0 + cc, re, im, jt.accumulate);
+                }
+            } else {
+                // Partial tile: publish this CTA's share, the last contributor sums all.
+                const int64_t slot = 2 * b + (r_start < tb ? 1 : 0);
+                int32_t *ws = plan.ws + slot * kWsSlotElems;
+                for (int cc = 0; cc < tl.nj; cc += 32) {
+                    uint32_t fre[32], fim[32];
+                    tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
+                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + cc, fim);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        __stcg(ws + int64_t(cc + k) * kBM + r, __float2int_rn(__uint_as_float(fre[k])));
+                        __stcg(ws + int64_t(kBN + cc + k) * kBM + r,
+                               __float2int_rn(__uint_as_float(fim[k])));
+                    }
+                }
+                __threadfence();
+                epi_bar();
+                const int64_t b_first = cta_of(tb, W, G);
+                const int64_t b_last = cta_of(te - 1, W, G);
+                if (threadIdx.x == 0) {
+                    const int n_contrib = int(b_last - b_first + 1);
+                    const int old = atomicAdd(&plan.counters[t], 1);
+                    const bool last = old == n_contrib - 1;
+                    if (last) plan.counters[t] = 0;  // ready for the next launch
+                    *epi_flag = last ? 2 : 1;
+                }
+                epi_bar();
+                if (*epi_flag == 2) {
+                    __threadfence();
+                    const bool first_split = range_start(b_first, W, G) < tb;
+                    for (int cc = 0; cc < tl.nj; cc += 32) {
+                        int re[32], im[32];
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) { re[k] = 0; im[k] = 0; }
+                        for (int64_t bb = b_first; bb <= b_last; ++bb) {
+                            const int64_t sl = 2 * bb + ((bb == b_first && first_split) ? 1 : 0);
+                            const int32_t *w = plan.ws + sl * kWsSlotElems;
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) {
+                                re[k] += __ldcg(w + int64_t(cc + k) * kBM + r);
+                                im[k] += __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
+                            }
+                        }
+                        store_run(jb, tl.chan, i, tl.j0 + cc, re, im, jt.accumulate);
+                    }
+                }
+            }
+            tc_fence_before();
+            mbar_arrive(acc_empty);
+        }
+    }
+
+    tc_fence_before();
+    __syncthreads();
+    if (warp == 5) {
+        tc_fence_after();
+        tmem_dealloc(tmem, 512);
+    }
+}
+
+int tc_smem_bytes() { return kTcSmem; }
+
+cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s) {
+    if (plan.n_cta <= 0 || plan.total_iters <= 0) return cudaSuccess;
+    static bool attr_set[3] = {false, false, false};
+    cudaError_t e = cudaSuccess;
+    if (elem_bytes == 1) {
+        if (!attr_set[1]) {
+            e = cudaFuncSetAttribute(tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+            if (e != cudaSuccess) return e;
+            attr_set[1] = true;
+        }
+        tc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+    } else {
+        if (!attr_set[2]) {
+            e = cudaFuncSetAttribute(tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+            if (e != cudaSuccess) return e;
+            attr_set[2] = true;
+        }
+        tc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace xe

@@ -1,0 +1,180 @@
+"""Thin ctypes binding of libxe (include/xe.h).  Argument marshalling only: every step of
+the correlation runs in the CUDA library.  There is no CPU fallback: if the library cannot
+be built or loaded, every call raises.
+
+Tensors: inputs are uint8 ``[C, T, N]`` (or ``[T, N]``) CUDA tensors of packed 4+4-bit
+samples; outputs are int32 ``[C, N(N+1)/2, 2]`` CUDA tensors (row-major upper triangle,
+{Re, Im}).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_EBUDGET = 0, -1, -2, -3, -4
+XE_EAGAIN, XE_ETIMEOUT, XE_ECUDA, XE_ENODEV, XE_ECLOSED = -5, -6, -7, -8, -9
+ALGOS = {"auto": 0, "tc": 1, "imma": 2}
+
+_lock = threading.Lock()
+_lib = None
+
+
+class XeError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str):
+        super().__init__(f"{where}: {detail} (code {code})")
+        self.code = code
+
+
+class Job(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("vis", ctypes.c_void_p), ("N", ctypes.c_int),
+                ("n_chan", ctypes.c_int), ("T", ctypes.c_int64)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Build (if stale) and load libxe.so.  Raises if nvcc or the library is unavailable."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.build()
+        L = ctypes.CDLL(path)
+        i64, i32, p, d = ctypes.c_int64, ctypes.c_int, ctypes.c_void_p, ctypes.c_double
+        sigs = {
+            "xe_strerror": ([i32], ctypes.c_char_p),
+            "xe_last_error": ([], ctypes.c_char_p),
+            "xe_version": ([], i32),
+            "xe_cmac": ([i64, i64, i64], d),
+            "xe_correlate": ([p, i32, i64, i32, p], i32),
+            "xe_correlate_async": ([p, i32, i64, i32, p, i32, p], i32),
+            "xe_correlate_host": ([p, i32, i64, i32, p, i32], i32),
+            "xe_correlate_batch": ([p, i32, i32, p], i32),
+            "xe_plan_stats": ([p, p, p, i32, i32, p, p, p], i32),
+            "xe_set_option": ([ctypes.c_char_p, i64], i32),
+            "xe_set_timing": ([i32], i32),
+            "xe_last_timing": ([p, p], i32),
+            "xe_device_status": ([p], i32),
+            "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
+        }
+        for name, (args, res) in sigs.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = L
+        return L
+
+
+def _check(rc: int, where: str):
+    if rc != XE_OK:
+        L = load()
+        raise XeError(rc, where, L.xe_last_error().decode(errors="replace"))
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def n_baselines(N: int) -> int:
+    return N * (N + 1) // 2
+
+
+def cmac(N: int, T: int, C: int = 1) -> float:
+    return float(load().xe_cmac(N, T, C))
+
+
+def set_option(key: str, value: int):
+    _check(load().xe_set_option(key.encode(), int(value)), f"xe_set_option({key})")
+
+
+def set_timing(enable: bool):
+    _check(load().xe_set_timing(1 if enable else 0), "xe_set_timing")
+
+
+def last_timing() -> tuple[float, float]:
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _check(load().xe_last_timing(ctypes.byref(a), ctypes.byref(b)), "xe_last_timing")
+    return a.value, b.value
+
+
+def device_status(stream=None):
+    _check(load().xe_device_status(_stream_handle(stream)), "xe_device_status")
+
+
+def operand_code(v: int, elem_bytes: int) -> int:
+    return int(load().xe_debug_operand_code(v, elem_bytes))
+
+
+def plan_stats(shapes, n_cta: int):
+    """shapes: list of (N, T, C).  Returns (n_tiles, n_iters, n_split_tiles)."""
+    n = len(shapes)
+    Ns = (ctypes.c_int * n)(*[s[0] for s in shapes])
+    Ts = (ctypes.c_int64 * n)(*[s[1] for s in shapes])
+    Cs = (ctypes.c_int * n)(*[s[2] for s in shapes])
+    a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().xe_plan_stats(Ns, Ts, Cs, n, n_cta, ctypes.byref(a), ctypes.byref(b),
+                                ctypes.byref(c)), "xe_plan_stats")
+    return a.value, b.value, c.value
+
+
+def _shape(inp, N, T, C):
+    import torch
+    if inp.dtype != torch.uint8:
+        raise TypeError("input must be uint8 packed samples")
+    if not inp.is_contiguous():
+        raise ValueError("input must be contiguous")
+    if inp.numel() != C * T * N:
+        raise ValueError(f"input has {inp.numel()} bytes, expected C*T*N = {C * T * N}")
+
+
+def empty_vis(N: int, C: int = 1, device="cuda"):
+    import torch
+    return torch.empty((C, n_baselines(N), 2), dtype=torch.int32, device=device)
+
+
+def correlate(inp, N: int, T: int, C: int = 1, out=None, algo: str = "auto", stream=None):
+    """Visibilities of C channels: device input -> device int32 [C, B, 2] (async on stream)."""
+    _shape(inp, N, T, C)
+    if not inp.is_cuda:
+        raise ValueError("input must be a CUDA tensor (use correlate_host for host buffers)")
+    if out is None:
+        out = empty_vis(N, C, inp.device)
+    rc = load().xe_correlate_async(ctypes.c_void_p(inp.data_ptr()), N, T, C,
+                                   ctypes.c_void_p(out.data_ptr()), ALGOS[algo],
+                                   _stream_handle(stream))
+    _check(rc, "xe_correlate_async")
+    return out
+
+
+def correlate_host(inp, N: int, T: int, C: int = 1, out=None, algo: str = "auto"):
+    """Host (CPU, ideally pinned) input -> host int32 [C, B, 2]; synchronous."""
+    import torch
+    _shape(inp, N, T, C)
+    if inp.is_cuda:
+        raise ValueError("correlate_host takes host tensors")
+    if out is None:
+        out = torch.empty((C, n_baselines(N), 2), dtype=torch.int32,
+                          pin_memory=inp.is_pinned())
+    rc = load().xe_correlate_host(ctypes.c_void_p(inp.data_ptr()), N, T, C,
+                                  ctypes.c_void_p(out.data_ptr()), ALGOS[algo])
+    _check(rc, "xe_correlate_host")
+    return out
+
+
+def correlate_batch(jobs, use_graph: bool = False, stream=None):
+    """jobs: list of (input, out, N, T, C) with device tensors; one persistent launch."""
+    arr = (Job * len(jobs))()
+    for k, (inp, out, N, T, C) in enumerate(jobs):
+        _shape(inp, N, T, C)
+        arr[k] = Job(inp.data_ptr(), out.data_ptr(), N, C, T)
+    rc = load().xe_correlate_batch(arr, len(jobs), 1 if use_graph else 0, _stream_handle(stream))
+    _check(rc, "xe_correlate_batch")
+    return [j[1] for j in jobs]

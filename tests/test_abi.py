@@ -1,0 +1,144 @@
+"""CPU-side checks of the C ABI: the library builds for sm_103a, loads, and exports every
+function include/xe.h declares; host-only entry points behave (no GPU needed)."""
+import ctypes
+import os
+import re
+import struct
+
+import numpy as np
+import pytest
+
+from paper_2005_09481_gb300 import xe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        src = open(os.path.join(ROOT, "include", h)).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        names += re.findall(r"^[A-Za-z_][\w\s\*]*?\b(xe_\w+)\s*\(", src, flags=re.M)
+    return sorted(set(names))
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for required in ("xe_correlate", "xe_correlate_async", "xe_correlate_batch",
+                     "xe_stream_open", "xe_stream_push", "xe_stream_poll", "xe_stream_close",
+                     "xe_strerror"):
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported():
+    L = xe.load()
+    missing = [n for n in _declared() if not hasattr(L, n)]
+    assert not missing, f"declared in include/*.h but not exported: {missing}"
+
+
+def test_strerror_and_version():
+    L = xe.load()
+    assert L.xe_strerror(0) == b"ok"
+    for code in range(-9, 0):
+        assert L.xe_strerror(code) and L.xe_strerror(code) != b"unknown error"
+    assert L.xe_version() >= 100
+
+
+def test_cmac_count():
+    assert xe.cmac(2048, 32768, 1) == 2_098_176 * 32768
+    assert xe.cmac(64, 1024, 3) == 3 * 1024 * 2080
+
+
+def test_argument_validation_before_any_device_call():
+    L = xe.load()
+    buf = (ctypes.c_uint8 * 64)()
+    out = (ctypes.c_int32 * 64)()
+    cases = [
+        (None, 4, 4, 1, out, xe.XE_EINVAL),
+        (buf, 4, 4, 1, None, xe.XE_EINVAL),
+        (buf, 0, 4, 1, out, xe.XE_EINVAL),
+        (buf, 4, 0, 1, out, xe.XE_EINVAL),
+        (buf, 4, 4, 0, out, xe.XE_EINVAL),
+        (buf, 4, 16777216, 1, out, xe.XE_EOVERFLOW),
+        (buf, 70000, 4, 1, out, xe.XE_EINVAL),
+    ]
+    for inp, N, T, C, o, want in cases:
+        rc = L.xe_correlate_async(inp, N, T, C, o, 1, None)
+        assert rc == want, (N, T, C, rc)
+    misaligned = ctypes.c_void_p(ctypes.addressof(out) + 4)
+    assert L.xe_correlate_async(buf, 4, 4, 1, misaligned, 1, None) == xe.XE_EINVAL
+    assert L.xe_correlate_async(buf, 4, 4, 1, out, 9, None) == xe.XE_EINVAL
+    assert L.xe_last_error()
+
+
+def test_options_validation():
+    with pytest.raises(xe.XeError):
+        xe.set_option("operand_bytes", 3)
+    with pytest.raises(xe.XeError):
+        xe.set_option("exact_chunk_t", 1 << 30)
+    with pytest.raises(xe.XeError):
+        xe.set_option("no_such_option", 1)
+    xe.set_option("operand_bytes", 1)
+
+
+def _e4m3_value(code):
+    s = -1.0 if code & 0x80 else 1.0
+    e = (code >> 3) & 0xF
+    m = code & 7
+    if e == 0:
+        return s * (m / 8.0) * 2.0 ** -6
+    return s * (1 + m / 8.0) * 2.0 ** (e - 7)
+
+
+def test_operand_encoder_is_exact():
+    # e4m3 (sign, 4-bit exponent bias 7, 3-bit mantissa) and IEEE half represent every
+    # integer in [-16, 16] exactly; the encoder must produce those bit patterns.
+    for v in range(-16, 17):
+        c8 = xe.operand_code(v, 1)
+        assert c8 < 256 and _e4m3_value(c8) == v
+        c16 = xe.operand_code(v, 2)
+        assert struct.unpack("<e", struct.pack("<H", c16))[0] == v
+
+
+def _tiles_py(N):
+    """Independent enumeration of the tile cover: every (i, j >= i) exactly once."""
+    cover = np.zeros((N, N), np.int32)
+    tiles = 0
+    for i0 in range(0, N, 128):
+        j0 = i0
+        spans = []
+        if j0 % 256:
+            spans.append((j0, 128))
+            j0 += 128
+        while j0 < N:
+            spans.append((j0, 256))
+            j0 += 256
+        for (a, w) in spans:
+            tiles += 1
+            for i in range(i0, min(i0 + 128, N)):
+                lo = max(a, i)
+                if lo < min(a + w, N):
+                    cover[i, lo:min(a + w, N)] += 1
+    return tiles, cover
+
+
+@pytest.mark.parametrize("N", [1, 100, 128, 129, 255, 256, 257, 384, 600, 2048])
+def test_plan_covers_triangle_once(N):
+    tiles, cover = _tiles_py(N)
+    iu = np.triu_indices(N)
+    assert (cover[iu] == 1).all() and cover.sum() == N * (N + 1) // 2
+    n_tiles, n_iters, _ = xe.plan_stats([(N, 1000, 1)], 152)
+    assert n_tiles == tiles
+    assert n_iters == tiles * ((1000 + 63) // 64)
+
+
+def test_plan_stats_batch_and_split():
+    n_tiles, n_iters, n_split = xe.plan_stats([(2048, 32768, 1)], 152)
+    assert n_tiles == 72 and n_iters == 72 * 512
+    assert 0 < n_split <= 72
+    # one CTA: nothing is split
+    assert xe.plan_stats([(2048, 32768, 1)], 1)[2] == 0
+    t2, i2, _ = xe.plan_stats([(256, 4096, 2), (512, 8192, 1)], 152)
+    assert t2 == 2 * 2 + 6 and i2 == 4 * 64 + 6 * 128
