@@ -193,6 +193,34 @@ int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *i
  * of its memory.  Results not yet released become invalid. */
 void xe_stream_close(xe_stream *s);
 
+/* ---- allocation-free correlation ------------------------------------------------------ */
+
+/* Size of the fixed scratch array libxe.so compiles in for xe_correlate_noalloc (device
+ * memory every GPU that loads the library holds until the process exits), and the most
+ * triangle tiles one call may have. */
+#define XE_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define XE_NOALLOC_MAX_TILES 4096
+
+/* xe_correlate_noalloc: as xe_correlate_async with XE_ALGO_TC, for callers that cannot
+ * call cudaMalloc (a real-time pipeline that forbids allocation once running, or a host
+ * application whose own pool owns all device memory).  It allocates nothing: its scratch
+ * (staged operands, tile table, status word) lives in one fixed 32 MiB device array
+ * compiled into the library.  There is no counterpart in the paper; this is an interface
+ * for constrained callers.
+ *
+ * in, vis: caller-owned device pointers, formats as above; enqueued on `stream`.
+ * Limits: T <= 131072, 2 * n_chan * ceil(N/256)*256 * ceil(T/64)*64 bytes of staged
+ * operands must fit the array (e.g. N=2048, T=4096, one channel uses 16 MiB), and at most
+ * XE_NOALLOC_MAX_TILES tiles; larger requests return XE_EINVAL with a message in
+ * xe_last_error() and enqueue nothing.
+ * The first call on a device (with that device current) looks up the array's device
+ * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call shares the one array, which keeps the previous call's contents: calls that
+ * overlap on the GPU (other streams, unordered threads) race and give wrong results.
+ * Returns XE_OK, XE_EINVAL, XE_ECUDA or XE_ENODEV. */
+int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis,
+                         void *stream);
+
 /* ---- diagnostics -------------------------------------------------------------------- */
 
 /* Tuning / diagnostic options (process-wide; take effect on the next call):

@@ -29,6 +29,8 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+int record_error(int code, const char *msg) { return fail(code, "%s", msg); }
+
 #define XE_CUDA(call)                                                                     \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \

@@ -90,6 +90,9 @@ cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
 
+// Record a failure for xe_last_error() on this thread; returns `code`.
+int record_error(int code, const char *msg);
+
 // Host encoders of a small integer as an MMA operand (e4m3 for 1 byte, f16 for 2 bytes).
 uint32_t operand_code(int v, int elem_bytes);
 

@@ -1,0 +1,174 @@
+// xe_noalloc.cu -- an entry point of the tensor-core correlation that allocates nothing.
+//
+// Some callers cannot call cudaMalloc: a real-time pipeline that forbids allocation once
+// it is running (an allocation can block on the driver and stall a frame deadline), a host
+// application or plugin framework that owns all device memory through its own pool, or
+// code that must not change the device's memory footprint after start-up.  For them,
+// xe_correlate_noalloc runs the same staging and tcgen05 kernels as xe_correlate_async, but
+// takes all of its scratch memory (staged operand planes, tile table, status word) from
+// one fixed array compiled into this library, instead of allocating it.
+//
+// The array is a file-scope __device__ array of XE_NOALLOC_SCRATCH_BYTES (32 MiB): every
+// GPU that loads the library holds it until the process exits.  Every call shares it, and
+// it keeps the last call's contents; calls that overlap on the GPU (different streams, or
+// different host threads without ordering) race on it and corrupt each other's results.
+//
+// Host code cannot use the array's name as a device address: in host code the name is a
+// host-side stand-in.  So the first call on each device (with that device current) looks up
+// its device address with cudaGetSymbolAddress and caches it; that first call should come
+// before any stream capture.  Device code here could name the array directly; the kernels
+// receive the looked-up address as an argument.
+#include <cstdint>
+#include <mutex>
+
+#include <cuda_runtime.h>
+
+#include "xe.h"
+#include "xe_internal.h"
+
+namespace xe {
+
+static __device__ __align__(256) uint8_t g_noalloc_scratch[XE_NOALLOC_SCRATCH_BYTES];
+
+// Layout of the array: [status | pad][tile table][planes].
+constexpr size_t kNaStatusBytes = 256;
+constexpr size_t kNaTileBytes = size_t(XE_NOALLOC_MAX_TILES) * sizeof(Tile);
+constexpr size_t kNaPlaneOffset = (kNaStatusBytes + kNaTileBytes + 1023) / 1024 * 1024;
+constexpr size_t kNaPlaneBytes = size_t(XE_NOALLOC_SCRATCH_BYTES) - kNaPlaneOffset;
+static_assert(kNaPlaneOffset < size_t(XE_NOALLOC_SCRATCH_BYTES), "scratch layout");
+
+constexpr int kMaxDevices = 64;
+static uint8_t *g_na_ptr[kMaxDevices] = {nullptr};
+static std::mutex g_na_mu;
+static int na_fail(int code, const char *msg) { return record_error(code, msg); }
+
+// Enumerate the triangle tiles of one job (same cover and order as the allocating path:
+// row blocks of 128, 256-wide column tiles aligned to 256, a 128-wide half tile where a row
+// block starts mid-way through a column block) straight into the scratch tile table.
+// One thread: at most XE_NOALLOC_MAX_TILES entries.
+__global__ void na_tiles_kernel(Tile *tiles, int N, int C, int kb, int *status) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    *status = 0;
+    int64_t it = 0;
+    int k = 0;
+    for (int c = 0; c < C; ++c)
+        for (int i0 = 0; i0 < N; i0 += kBM) {
+            int j0 = i0;
+            if (j0 % kBN != 0) {
+                tiles[k++] = Tile{0, c, i0, j0, kBM, kb, it};
+                it += kb;
+                j0 += kBM;
+            }
+            for (; j0 < N; j0 += kBN) {
+                tiles[k++] = Tile{0, c, i0, j0, kBN, kb, it};
+                it += kb;
+            }
+        }
+}
+
+static int64_t na_tile_count(int N, int C) {
+    int64_t n = 0;
+    for (int i0 = 0; i0 < N; i0 += kBM) {
+        int j0 = i0;
+        if (j0 % kBN != 0) { ++n; j0 += kBM; }
+        if (j0 < N) n += (N - j0 + kBN - 1) / kBN;
+    }
+    return n * C;
+}
+
+// Device address of the array on the current device (looked up once per device).
+static int na_scratch(uint8_t **out) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(XE_ECUDA, "cudaGetDevice failed");
+    if (dev < 0 || dev >= kMaxDevices) return na_fail(XE_ENODEV, "device index out of range");
+    std::lock_guard<std::mutex> lk(g_na_mu);
+    if (!g_na_ptr[dev]) {
+        int major = 0, minor = 0;
+        cudaDeviceGetAttribute(&major, cudaDevAttrComputeCapabilityMajor, dev);
+        cudaDeviceGetAttribute(&minor, cudaDevAttrComputeCapabilityMinor, dev);
+        if (!(major == 10 && minor == 3)) return na_fail(XE_ENODEV, "not an sm_103 device");
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess || !p)
+            return na_fail(XE_ECUDA, "cudaGetSymbolAddress of the no-alloc scratch failed");
+        g_na_ptr[dev] = static_cast<uint8_t *>(p);
+    }
+    *out = g_na_ptr[dev];
+    return XE_OK;
+}
+
+}  // namespace xe
+
+using namespace xe;
+
+extern "C" {
+
+int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis,
+                         void *stream) {
+    if (!in || !vis) return na_fail(XE_EINVAL, "null input or output pointer");
+    if (N < 1 || T < 1 || n_chan < 1) return na_fail(XE_EINVAL, "N, T and n_chan must be >= 1");
+    if (reinterpret_cast<uintptr_t>(vis) & 7) return na_fail(XE_EINVAL, "vis must be 8-byte aligned");
+    if (T > kExactChunkT)
+        return na_fail(XE_EINVAL, "xe_correlate_noalloc: T exceeds 131072 samples per call");
+    if (N > XE_MAX_N) return na_fail(XE_EINVAL, "xe_correlate_noalloc: N too large");
+    const int eb = 1;
+    const int n_pad = (N + kNPad - 1) / kNPad * kNPad;
+    const int64_t kb = (T + samples_per_stage(eb) - 1) / samples_per_stage(eb);
+    const int64_t plane_chan = kb * 2 * n_pad * kRowBytes;
+    if (double(plane_chan) * n_chan > double(kNaPlaneBytes))
+        return na_fail(XE_EINVAL,
+                       "xe_correlate_noalloc: 2 * n_chan * ceil(N/256)*256 * ceil(T/64)*64 bytes of "
+                       "staged operands exceed the fixed scratch");
+    const int64_t n_tiles = na_tile_count(N, n_chan);
+    if (n_tiles > XE_NOALLOC_MAX_TILES)
+        return na_fail(XE_EINVAL, "xe_correlate_noalloc: too many triangle tiles for the fixed scratch");
+
+    uint8_t *base = nullptr;
+    int rc = na_scratch(&base);
+    if (rc) return rc;
+    cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    int *status = reinterpret_cast<int *>(base);
+    Tile *tiles = reinterpret_cast<Tile *>(base + kNaStatusBytes);
+    uint8_t *planes = base + kNaPlaneOffset;
+
+    JobTable jt{};
+    jt.n_jobs = 1;
+    jt.accumulate = 0;
+    JobDev &jd = jt.jobs[0];
+    jd.in = in;
+    jd.vis = vis;
+    jd.planes = planes;
+    jd.T = T;
+    jd.t0 = 0;
+    jd.T_in = T;
+    jd.N = N;
+    jd.n_pad = n_pad;
+    jd.C = n_chan;
+    jd.kblocks = int(kb);
+    jd.plane_chan_bytes = plane_chan;
+    jd.vis_chan_elems = int64_t(N) * (N + 1);
+    jd.stage_block0 = 0;
+    jt.total_stage_blocks = int64_t(n_chan) * kb * (n_pad / 256);
+
+    // One CTA per tile, each covering its whole tile: no tile is split across CTAs, so the
+    // split-tile workspace and arrival counters of the allocating path are never touched.
+    PlanDev pd{};
+    pd.tiles = tiles;
+    pd.n_tiles = int(n_tiles);
+    pd.n_cta = int(n_tiles);
+    pd.total_iters = n_tiles * kb;
+    pd.ws = nullptr;
+    pd.counters = nullptr;
+    pd.status = status;
+
+    na_tiles_kernel<<<1, 32, 0, s>>>(tiles, N, n_chan, int(kb), status);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return na_fail(XE_ECUDA, cudaGetErrorString(e));
+    e = launch_stage(jt, eb, s);
+    if (e != cudaSuccess) return na_fail(XE_ECUDA, cudaGetErrorString(e));
+    e = launch_tc(jt, pd, eb, s);
+    if (e != cudaSuccess) return na_fail(XE_ECUDA, cudaGetErrorString(e));
+    return XE_OK;
+}
+
+}  // extern "C"

@@ -55,6 +55,7 @@ def load():
             "xe_correlate_async": ([p, i32, i64, i32, p, i32, p], i32),
             "xe_correlate_host": ([p, i32, i64, i32, p, i32], i32),
             "xe_correlate_batch": ([p, i32, i32, p], i32),
+            "xe_correlate_noalloc": ([p, i32, i64, i32, p, p], i32),
             "xe_plan_stats": ([p, p, p, i32, i32, p, p, p], i32),
             "xe_set_option": ([ctypes.c_char_p, i64], i32),
             "xe_set_timing": ([i32], i32),
@@ -178,3 +179,15 @@ def correlate_batch(jobs, use_graph: bool = False, stream=None):
     rc = load().xe_correlate_batch(arr, len(jobs), 1 if use_graph else 0, _stream_handle(stream))
     _check(rc, "xe_correlate_batch")
     return [j[1] for j in jobs]
+
+
+def correlate_noalloc(inp, N: int, T: int, C: int = 1, out=None, stream=None):
+    """As correlate(algo="tc"), through the entry point that allocates nothing (its scratch
+    is a fixed array inside the library; see include/xe.h for the limits)."""
+    _shape(inp, N, T, C)
+    if out is None:
+        out = empty_vis(N, C, inp.device)
+    rc = load().xe_correlate_noalloc(ctypes.c_void_p(inp.data_ptr()), N, T, C,
+                                     ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(rc, "xe_correlate_noalloc")
+    return out
