@@ -251,7 +251,7 @@ static int check_job(const uint8_t *in, int N, int64_t T, int C, const int32_t *
 }
 
 // Enqueue a batch of jobs (all validated) on stream s with the given algorithm.
-static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s) {
+static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, int accumulate = 0) {
     Device *d = nullptr;
     int rc = get_device(&d);
     if (rc) return rc;
@@ -266,7 +266,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s) {
             const int ng = n_jobs - g0 < kMaxJobs ? n_jobs - g0 : kMaxJobs;
             JobTable jt{};
             jt.n_jobs = ng;
-            jt.accumulate = 0;
+            jt.accumulate = accumulate ? 1 : 0;
             int64_t blocks = 0;
             for (int q = 0; q < ng; ++q) {
                 const xe_job &j = jobs[g0 + q];
@@ -306,7 +306,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s) {
                 std::vector<JobShape> shapes;
                 JobTable jt{};
                 jt.n_jobs = ng;
-                jt.accumulate = w > 0 ? 1 : 0;
+                jt.accumulate = (w > 0 || accumulate) ? 1 : 0;
                 size_t plane_off = 0;
                 int64_t blocks = 0;
                 for (int k = 0; k < ng; ++k) {
@@ -371,6 +371,11 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s) {
         for (int k = 0; k < 3; ++k) g_last_ev[k] = sc->ev[k];
     }
     return XE_OK;
+}
+
+int run_jobs_accumulate(const xe_job *jobs, int n_jobs, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return run_jobs(jobs, n_jobs, XE_ALGO_TC, s, 1);
 }
 
 }  // namespace xe

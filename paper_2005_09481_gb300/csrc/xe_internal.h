@@ -3,6 +3,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "xe.h"
+
 namespace xe {
 
 // ---- tensor-core tiling (tcgen05 path) ------------------------------------------------
@@ -89,6 +91,10 @@ cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, c
 cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
+
+// Enqueue jobs on stream s in accumulate mode (vis += V), tensor-core path; takes the
+// runtime lock.  Used by the streaming server.  Returns an XE_* code.
+int run_jobs_accumulate(const struct ::xe_job *jobs, int n_jobs, cudaStream_t s);
 
 // Record a failure for xe_last_error() on this thread; returns `code`.
 int record_error(int code, const char *msg);

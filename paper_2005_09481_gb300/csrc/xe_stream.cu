@@ -1,0 +1,481 @@
+// xe_stream.cu -- the streaming X-engine server: frames in, integrated visibilities out.
+//
+// The CHIME X-engine integrates visibilities on the GPU and exports them at a fixed cadence
+// (Denman et al. 2020, sections 2.1 and 3.2: per-block GPU processing, time integration,
+// export of correlated visibilities, Table tab:data-flow).  Here each admitted channel owns
+// a device-resident int32 accumulator and a ring of device frame slots.  Producers push
+// frames (host or device memory); one scheduler thread gathers, every pass, the next
+// in-order ready frame of every channel and correlates all of them in batched persistent
+// launches that ADD into the accumulators (continuous batching: frames that arrive while a
+// batch runs join the next one).  When a channel's integration is complete its accumulator
+// is copied to a pinned host buffer and cleared, and the result is handed to xe_stream_poll
+// with its arrival and ready times (frame-to-visibility latency).
+//
+// Admission is by HBM budget: a channel is admitted only if its accumulator, frame ring and
+// share of staging memory fit the stream's budget.  Lost frames (sequence gaps) are counted
+// and mark their integration incomplete; nothing shifts integration boundaries.
+#include <atomic>
+#include <chrono>
+#include <condition_variable>
+#include <cstdio>
+#include <cstring>
+#include <deque>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include <time.h>
+
+#include <cuda_runtime.h>
+
+#include "xe.h"
+#include "xe_internal.h"
+
+namespace xe {
+namespace {
+
+int64_t now_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return int64_t(ts.tv_sec) * 1000000000LL + ts.tv_nsec;
+}
+
+enum SlotState { kFree = 0, kCopying = 1, kReady = 2, kQueued = 3 };
+
+struct Slot {
+    uint8_t *dev = nullptr;
+    cudaEvent_t copy_ev = nullptr;   // the frame's bytes have landed in the slot
+    cudaEvent_t ev = nullptr;        // the launch that read the slot has finished
+    int state = kFree;
+};
+
+struct Entry {          // one frame of a channel, in sequence order
+    int64_t seq;
+    int slot;           // -1: the frame was lost
+    int64_t t_arrival;
+};
+
+struct Chan {
+    bool admitted = false;
+    int32_t *acc = nullptr;
+    std::vector<Slot> ring;
+    std::deque<Entry> fifo;
+    int64_t expected_push = 0;     // next sequence number a push may carry
+    int64_t integ_index = 0;
+    int64_t frames_in_integ = 0;
+    int64_t samples_in_integ = 0;
+    int64_t t_first = 0, t_last = 0;
+    bool lost = false;
+    std::vector<int> bufs;         // result buffers owned by this channel (indices)
+};
+
+struct ResultBuf {
+    int32_t *host = nullptr;
+    int chan = -1;
+    bool busy = false;             // between D2H enqueue and xe_stream_release
+};
+
+struct Pending {
+    xe_result r;
+    cudaEvent_t ev;
+};
+
+}  // namespace
+}  // namespace xe
+
+struct xe_stream {
+    xe_stream_cfg cfg{};
+    int dev = 0;
+    int64_t B = 0;
+    size_t frame_bytes = 0, acc_bytes = 0, per_chan_bytes = 0;
+    int64_t frames_per_integ = 0;
+    cudaStream_t copy_s = nullptr, comp_s = nullptr;
+    std::vector<xe::Chan> chans;
+    std::vector<xe::ResultBuf> bufs;
+    std::deque<xe::Pending> pending;
+    std::deque<xe_result> ready;
+    std::vector<cudaEvent_t> spare_events;
+    std::mutex mu;
+    std::condition_variable cv_work, cv_ready;
+    std::thread sched;
+    std::atomic<bool> stop{false};
+    bool closed = false;
+    int64_t used_bytes = 0;
+    int64_t n_admitted = 0, n_frames = 0, n_integ = 0, n_dropped = 0;
+    int last_error = XE_OK;
+};
+
+namespace xe {
+namespace {
+
+constexpr int kBufsPerChan = 2;
+
+cudaEvent_t take_event(xe_stream *s) {
+    if (!s->spare_events.empty()) {
+        cudaEvent_t e = s->spare_events.back();
+        s->spare_events.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+    return e;
+}
+
+// Close the channel's current integration: copy its accumulator to a free result buffer
+// of the channel, clear the accumulator, and queue the result for completion.  Called with
+// s->mu held, after the launches that fed the integration were enqueued on comp_s.
+void finish_integration(xe_stream *s, int c) {
+    Chan &ch = s->chans[c];
+    int b = -1;
+    for (int k : ch.bufs)
+        if (!s->bufs[k].busy) { b = k; break; }
+    // A buffer is always free here: the scheduler only completes an integration when one is.
+    ResultBuf &rb = s->bufs[b];
+    rb.busy = true;
+    cudaMemcpyAsync(rb.host, ch.acc, s->acc_bytes, cudaMemcpyDeviceToHost, s->comp_s);
+    cudaMemsetAsync(ch.acc, 0, s->acc_bytes, s->comp_s);
+    Pending p{};
+    p.r.chan = c;
+    p.r.integ_index = ch.integ_index;
+    p.r.n_samples = ch.samples_in_integ;
+    p.r.complete = (!ch.lost && ch.samples_in_integ == s->cfg.integ_T) ? 1 : 0;
+    p.r.vis = rb.host;
+    p.r.t_first_arrival_ns = ch.t_first;
+    p.r.t_last_arrival_ns = ch.t_last;
+    p.r.handle = b;
+    p.ev = take_event(s);
+    cudaEventRecord(p.ev, s->comp_s);
+    s->pending.push_back(p);
+    ch.integ_index += 1;
+    ch.frames_in_integ = 0;
+    ch.samples_in_integ = 0;
+    ch.lost = false;
+    ch.t_first = ch.t_last = 0;
+}
+
+bool has_free_buf(xe_stream *s, int c) {
+    for (int k : s->chans[c].bufs)
+        if (!s->bufs[k].busy) return true;
+    return false;
+}
+
+// One scheduler pass.  Returns true if it did any work.
+bool pass(xe_stream *s) {
+    std::vector<xe_job> jobs;
+    std::vector<std::pair<int, int>> used;   // (channel, slot) consumed by this pass
+    std::vector<int> finishing;
+    bool work = false;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        for (size_t c = 0; c < s->chans.size(); ++c) {
+            Chan &ch = s->chans[c];
+            if (!ch.admitted) continue;
+            for (Slot &sl : ch.ring) {
+                if (sl.state == kCopying && cudaEventQuery(sl.copy_ev) == cudaSuccess) sl.state = kReady;
+                else if (sl.state == kQueued && cudaEventQuery(sl.ev) == cudaSuccess) sl.state = kFree;
+            }
+        }
+        while (!s->pending.empty() && cudaEventQuery(s->pending.front().ev) == cudaSuccess) {
+            Pending p = s->pending.front();
+            s->pending.pop_front();
+            p.r.t_ready_ns = now_ns();
+            s->spare_events.push_back(p.ev);
+            s->ready.push_back(p.r);
+            s->n_integ += 1;
+            s->cv_ready.notify_all();
+            work = true;
+        }
+        // At most one frame per channel per pass: two frames of one channel in one launch
+        // would add into the same accumulator concurrently.
+        for (size_t c = 0; c < s->chans.size(); ++c) {
+            Chan &ch = s->chans[c];
+            if (!ch.admitted) continue;
+            while (!ch.fifo.empty()) {
+                const Entry e = ch.fifo.front();
+                const bool closes = ch.frames_in_integ + 1 == s->frames_per_integ;
+                if (closes && !has_free_buf(s, int(c))) break;       // consumer is behind
+                if (e.slot < 0) {                                     // a lost frame
+                    ch.fifo.pop_front();
+                    if (ch.frames_in_integ == 0) ch.t_first = e.t_arrival;
+                    ch.t_last = e.t_arrival;
+                    ch.lost = true;
+                    ch.frames_in_integ += 1;
+                    if (closes) finishing.push_back(int(c));
+                    if (closes) break;
+                    continue;
+                }
+                Slot &sl = ch.ring[e.slot];
+                if (sl.state != kReady) break;
+                ch.fifo.pop_front();
+                sl.state = kQueued;
+                jobs.push_back(xe_job{sl.dev, ch.acc, s->cfg.N, 1, s->cfg.frame_T});
+                used.emplace_back(int(c), e.slot);
+                if (ch.frames_in_integ == 0) ch.t_first = e.t_arrival;
+                ch.t_last = e.t_arrival;
+                ch.frames_in_integ += 1;
+                ch.samples_in_integ += s->cfg.frame_T;
+                if (closes) finishing.push_back(int(c));
+                break;
+            }
+        }
+        if (!jobs.empty()) {
+            int rc = run_jobs_accumulate(jobs.data(), int(jobs.size()), s->comp_s);
+            if (rc != XE_OK) s->last_error = rc;
+            for (auto &u : used) cudaEventRecord(s->chans[u.first].ring[u.second].ev, s->comp_s);
+            s->n_frames += int64_t(jobs.size());
+            work = true;
+        }
+        for (int c : finishing) finish_integration(s, c);
+        if (!finishing.empty()) work = true;
+    }
+    return work;
+}
+
+void scheduler_main(xe_stream *s) {
+    cudaSetDevice(s->dev);
+    while (!s->stop.load()) {
+        if (!pass(s)) {
+            std::unique_lock<std::mutex> lk(s->mu);
+            s->cv_work.wait_for(lk, std::chrono::microseconds(200));
+        }
+    }
+}
+
+int sfail(int code, const char *msg) { return record_error(code, msg); }
+
+}  // namespace
+}  // namespace xe
+
+using namespace xe;
+
+extern "C" {
+
+int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
+    if (!cfg || !out) return sfail(XE_EINVAL, "null stream config or output");
+    const xe_stream_cfg &c = *cfg;
+    if (c.N < 1 || c.N > XE_MAX_N) return sfail(XE_EINVAL, "stream N out of range");
+    if (c.frame_T < 1 || c.frame_T > kExactChunkT)
+        return sfail(XE_EINVAL, "frame_T must lie in [1, 131072]");
+    if (c.integ_T < c.frame_T || c.integ_T % c.frame_T != 0)
+        return sfail(XE_EINVAL, "integ_T must be a positive multiple of frame_T");
+    if (c.integ_T > XE_MAX_T) return sfail(XE_EOVERFLOW, "integ_T too long for int32 visibilities");
+    if (c.max_chan < 1 || c.max_chan > 65536) return sfail(XE_EINVAL, "max_chan out of range");
+    if (c.ring_frames < 2 || c.ring_frames > 64) return sfail(XE_EINVAL, "ring_frames must lie in [2, 64]");
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return sfail(XE_ECUDA, "cudaGetDevice failed");
+    xe_stream *s = new xe_stream;
+    s->cfg = c;
+    s->dev = dev;
+    s->B = int64_t(c.N) * (c.N + 1) / 2;
+    s->frame_bytes = size_t(c.frame_T) * size_t(c.N);
+    s->acc_bytes = size_t(s->B) * 2 * sizeof(int32_t);
+    s->frames_per_integ = c.integ_T / c.frame_T;
+    const size_t n_pad = size_t((c.N + kNPad - 1) / kNPad * kNPad);
+    const size_t stage_bytes = 2 * n_pad * size_t((c.frame_T + 63) / 64 * 64);
+    s->per_chan_bytes = s->acc_bytes + size_t(c.ring_frames) * s->frame_bytes + stage_bytes;
+    if (c.hbm_budget < int64_t(s->per_chan_bytes)) {
+        delete s;
+        return sfail(XE_EBUDGET, "the HBM budget does not fit one channel slot");
+    }
+    s->chans.resize(size_t(c.max_chan));
+    if (cudaStreamCreateWithFlags(&s->copy_s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->comp_s, cudaStreamNonBlocking) != cudaSuccess) {
+        delete s;
+        return sfail(XE_ECUDA, "stream creation failed");
+    }
+    s->sched = std::thread(scheduler_main, s);
+    *out = s;
+    return XE_OK;
+}
+
+int xe_stream_admit(xe_stream *s, int chan) {
+    if (!s) return sfail(XE_EINVAL, "null stream");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->closed) return sfail(XE_ECLOSED, "stream closed");
+    if (chan < 0 || chan >= int(s->chans.size())) return sfail(XE_EINVAL, "channel id out of range");
+    Chan &ch = s->chans[size_t(chan)];
+    if (ch.admitted) return XE_OK;
+    if (s->used_bytes + int64_t(s->per_chan_bytes) > s->cfg.hbm_budget)
+        return sfail(XE_EBUDGET, "HBM budget full");
+    cudaSetDevice(s->dev);
+    if (cudaMalloc(&ch.acc, s->acc_bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return sfail(XE_ENOMEM, "accumulator allocation failed");
+    }
+    cudaMemset(ch.acc, 0, s->acc_bytes);
+    ch.ring.assign(size_t(s->cfg.ring_frames), Slot{});
+    for (Slot &sl : ch.ring) {
+        if (cudaMalloc(&sl.dev, s->frame_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return sfail(XE_ENOMEM, "frame ring allocation failed");
+        }
+        cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
+        cudaEventCreateWithFlags(&sl.copy_ev, cudaEventDisableTiming);
+    }
+    for (int k = 0; k < kBufsPerChan; ++k) {
+        ResultBuf rb;
+        if (cudaHostAlloc(reinterpret_cast<void **>(&rb.host), s->acc_bytes, cudaHostAllocDefault) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return sfail(XE_ENOMEM, "pinned result buffer allocation failed");
+        }
+        rb.chan = chan;
+        ch.bufs.push_back(int(s->bufs.size()));
+        s->bufs.push_back(rb);
+    }
+    ch.fifo.clear();
+    ch.expected_push = 0;
+    ch.integ_index = ch.frames_in_integ = ch.samples_in_integ = 0;
+    ch.lost = false;
+    ch.admitted = true;
+    s->used_bytes += int64_t(s->per_chan_bytes);
+    s->n_admitted += 1;
+    return XE_OK;
+}
+
+int xe_stream_evict(xe_stream *s, int chan) {
+    if (!s) return sfail(XE_EINVAL, "null stream");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (chan < 0 || chan >= int(s->chans.size()) || !s->chans[size_t(chan)].admitted)
+        return sfail(XE_EINVAL, "channel not admitted");
+    Chan &ch = s->chans[size_t(chan)];
+    cudaStreamSynchronize(s->copy_s);
+    cudaStreamSynchronize(s->comp_s);
+    // Results of this channel still queued keep their buffers until released.
+    for (Slot &sl : ch.ring) {
+        cudaFree(sl.dev);
+        cudaEventDestroy(sl.ev);
+        cudaEventDestroy(sl.copy_ev);
+    }
+    ch.ring.clear();
+    ch.fifo.clear();
+    cudaFree(ch.acc);
+    ch.acc = nullptr;
+    ch.admitted = false;
+    s->used_bytes -= int64_t(s->per_chan_bytes);
+    s->n_admitted -= 1;
+    return XE_OK;
+}
+
+int xe_stream_push(xe_stream *s, int chan, const uint8_t *frame, int64_t seq, int64_t t_arrival_ns) {
+    if (!s || !frame) return sfail(XE_EINVAL, "null stream or frame");
+    cudaEvent_t wait_ev = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->closed) return sfail(XE_ECLOSED, "stream closed");
+        if (chan < 0 || chan >= int(s->chans.size()) || !s->chans[size_t(chan)].admitted)
+            return sfail(XE_EINVAL, "channel not admitted");
+        Chan &ch = s->chans[size_t(chan)];
+        if (seq < ch.expected_push) return sfail(XE_EINVAL, "frame is older than the open integration or a duplicate");
+        if (seq - ch.expected_push > 1000000) return sfail(XE_EINVAL, "sequence gap too large");
+        int slot = -1;
+        for (int k = 0; k < int(ch.ring.size()); ++k)
+            if (ch.ring[size_t(k)].state == kFree) { slot = k; break; }
+        if (slot < 0) return XE_EAGAIN;
+        const int64_t t = t_arrival_ns > 0 ? t_arrival_ns : now_ns();
+        for (int64_t q = ch.expected_push; q < seq; ++q) {     // frames that never came
+            ch.fifo.push_back(Entry{q, -1, t});
+            s->n_dropped += 1;
+        }
+        Slot &sl = ch.ring[size_t(slot)];
+        cudaError_t e = cudaMemcpyAsync(sl.dev, frame, s->frame_bytes,
+                                        s->cfg.device_source ? cudaMemcpyDeviceToDevice
+                                                             : cudaMemcpyHostToDevice,
+                                        s->copy_s);
+        if (e != cudaSuccess) return sfail(XE_ECUDA, cudaGetErrorString(e));
+        cudaEventRecord(sl.copy_ev, s->copy_s);
+        sl.state = kCopying;
+        ch.fifo.push_back(Entry{seq, slot, t});
+        ch.expected_push = seq + 1;
+        if (!s->cfg.device_source) wait_ev = sl.copy_ev;
+    }
+    // Host source: the caller's bytes are on the device before the call returns.
+    if (wait_ev) cudaEventSynchronize(wait_ev);
+    s->cv_work.notify_one();
+    return XE_OK;
+}
+
+int xe_stream_flush(xe_stream *s) {
+    if (!s) return sfail(XE_EINVAL, "null stream");
+    // Wait (bounded) until every pushed frame has been launched.
+    const int64_t deadline = now_ns() + 10000000000LL;
+    while (now_ns() < deadline) {
+        {
+            std::lock_guard<std::mutex> lk(s->mu);
+            bool any = false;
+            for (const Chan &ch : s->chans)
+                if (ch.admitted && !ch.fifo.empty()) { any = true; break; }
+            if (!any) return XE_OK;
+        }
+        s->cv_work.notify_one();
+        std::this_thread::sleep_for(std::chrono::microseconds(100));
+    }
+    return sfail(XE_ETIMEOUT, "flush: frames still waiting after 10 s");
+}
+
+int xe_stream_poll(xe_stream *s, xe_result *r, int timeout_ms) {
+    if (!s || !r) return sfail(XE_EINVAL, "null stream or result");
+    std::unique_lock<std::mutex> lk(s->mu);
+    if (s->ready.empty() && timeout_ms > 0)
+        s->cv_ready.wait_for(lk, std::chrono::milliseconds(timeout_ms), [s] { return !s->ready.empty(); });
+    if (s->last_error != XE_OK) {
+        const int e = s->last_error;
+        s->last_error = XE_OK;
+        return sfail(e, "a batched launch of the stream failed");
+    }
+    if (s->ready.empty()) return XE_EAGAIN;
+    *r = s->ready.front();
+    s->ready.pop_front();
+    return XE_OK;
+}
+
+int xe_stream_release(xe_stream *s, int64_t handle) {
+    if (!s) return sfail(XE_EINVAL, "null stream");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (handle < 0 || handle >= int64_t(s->bufs.size()) || !s->bufs[size_t(handle)].busy)
+        return sfail(XE_EINVAL, "unknown or already released result handle");
+    s->bufs[size_t(handle)].busy = false;
+    s->cv_work.notify_one();
+    return XE_OK;
+}
+
+int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *integrations,
+                    int64_t *dropped) {
+    if (!s) return sfail(XE_EINVAL, "null stream");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (admitted) *admitted = s->n_admitted;
+    if (frames) *frames = s->n_frames;
+    if (integrations) *integrations = s->n_integ;
+    if (dropped) *dropped = s->n_dropped;
+    return XE_OK;
+}
+
+void xe_stream_close(xe_stream *s) {
+    if (!s) return;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        s->closed = true;
+    }
+    s->stop.store(true);
+    s->cv_work.notify_all();
+    if (s->sched.joinable()) s->sched.join();
+    cudaSetDevice(s->dev);
+    cudaStreamSynchronize(s->copy_s);
+    cudaStreamSynchronize(s->comp_s);
+    for (Chan &ch : s->chans) {
+        for (Slot &sl : ch.ring) {
+            cudaFree(sl.dev);
+            cudaEventDestroy(sl.ev);
+            cudaEventDestroy(sl.copy_ev);
+        }
+        if (ch.acc) cudaFree(ch.acc);
+    }
+    for (ResultBuf &rb : s->bufs) cudaFreeHost(rb.host);
+    for (Pending &p : s->pending) cudaEventDestroy(p.ev);
+    for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    cudaStreamDestroy(s->copy_s);
+    cudaStreamDestroy(s->comp_s);
+    delete s;
+}
+
+}  // extern "C"

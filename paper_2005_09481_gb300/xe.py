@@ -62,6 +62,15 @@ def load():
             "xe_last_timing": ([p, p], i32),
             "xe_device_status": ([p], i32),
             "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
+            "xe_stream_open": ([p, p], i32),
+            "xe_stream_admit": ([p, i32], i32),
+            "xe_stream_evict": ([p, i32], i32),
+            "xe_stream_push": ([p, i32, p, i64, i64], i32),
+            "xe_stream_flush": ([p], i32),
+            "xe_stream_poll": ([p, p, i32], i32),
+            "xe_stream_release": ([p, i64], i32),
+            "xe_stream_stats": ([p, p, p, p, p], i32),
+            "xe_stream_close": ([p], None),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -191,3 +200,89 @@ def correlate_noalloc(inp, N: int, T: int, C: int = 1, out=None, stream=None):
                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(rc, "xe_correlate_noalloc")
     return out
+
+
+class StreamCfg(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("frame_T", ctypes.c_int64), ("integ_T", ctypes.c_int64),
+                ("max_chan", ctypes.c_int), ("hbm_budget", ctypes.c_int64),
+                ("ring_frames", ctypes.c_int), ("sample_rate", ctypes.c_double),
+                ("device_source", ctypes.c_int)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("chan", ctypes.c_int), ("integ_index", ctypes.c_int64),
+                ("n_samples", ctypes.c_int64), ("complete", ctypes.c_int),
+                ("vis", ctypes.c_void_p), ("t_first_arrival_ns", ctypes.c_int64),
+                ("t_last_arrival_ns", ctypes.c_int64), ("t_ready_ns", ctypes.c_int64),
+                ("handle", ctypes.c_int64)]
+
+
+class Stream:
+    """Streaming server (xe_stream_*): admit channels, push frames, poll integrations."""
+
+    def __init__(self, N: int, frame_T: int, integ_T: int, max_chan: int, hbm_budget: int,
+                 ring_frames: int = 3, sample_rate: float = 390625.0, device_source: bool = False):
+        self.N, self.frame_T, self.integ_T = N, frame_T, integ_T
+        self.B = n_baselines(N)
+        self.device_source = device_source
+        cfg = StreamCfg(N, frame_T, integ_T, max_chan, hbm_budget, ring_frames, sample_rate,
+                        1 if device_source else 0)
+        h = ctypes.c_void_p()
+        _check(load().xe_stream_open(ctypes.byref(cfg), ctypes.byref(h)), "xe_stream_open")
+        self.h = h
+
+    def admit(self, chan: int) -> int:
+        """XE_OK, or XE_EBUDGET when the HBM budget is full."""
+        rc = load().xe_stream_admit(self.h, chan)
+        if rc not in (XE_OK, XE_EBUDGET):
+            _check(rc, "xe_stream_admit")
+        return rc
+
+    def evict(self, chan: int):
+        _check(load().xe_stream_evict(self.h, chan), "xe_stream_evict")
+
+    def push(self, chan: int, frame, seq: int, t_arrival_ns: int = 0) -> int:
+        """frame: uint8 [frame_T, N] tensor (CUDA if device_source, else host).  Returns
+        XE_OK or XE_EAGAIN (ring full)."""
+        if frame.numel() != self.frame_T * self.N or not frame.is_contiguous():
+            raise ValueError("frame must be a contiguous [frame_T, N] uint8 tensor")
+        if bool(frame.is_cuda) != self.device_source:
+            raise ValueError("frame memory does not match the stream's source kind")
+        rc = load().xe_stream_push(self.h, chan, ctypes.c_void_p(frame.data_ptr()), seq,
+                                   t_arrival_ns)
+        if rc not in (XE_OK, XE_EAGAIN):
+            _check(rc, "xe_stream_push")
+        return rc
+
+    def flush(self):
+        _check(load().xe_stream_flush(self.h), "xe_stream_flush")
+
+    def poll(self, timeout_ms: int = 0):
+        """Next completed integration as (meta dict, int32 numpy [B, 2] copy), or None."""
+        import numpy as np
+        r = Result()
+        rc = load().xe_stream_poll(self.h, ctypes.byref(r), timeout_ms)
+        if rc == XE_EAGAIN:
+            return None
+        _check(rc, "xe_stream_poll")
+        buf = (ctypes.c_int32 * (2 * self.B)).from_address(r.vis)
+        vis = np.frombuffer(buf, dtype=np.int32).reshape(self.B, 2).copy()
+        _check(load().xe_stream_release(self.h, r.handle), "xe_stream_release")
+        meta = {k: getattr(r, k) for k, _ in Result._fields_ if k != "vis"}
+        return meta, vis
+
+    def stats(self):
+        v = [ctypes.c_int64() for _ in range(4)]
+        _check(load().xe_stream_stats(self.h, *[ctypes.byref(x) for x in v]), "xe_stream_stats")
+        return dict(zip(("admitted", "frames", "integrations", "dropped"), [x.value for x in v]))
+
+    def close(self):
+        if self.h:
+            load().xe_stream_close(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()

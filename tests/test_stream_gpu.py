@@ -1,0 +1,132 @@
+"""Streaming server: integrations equal one-shot correlations of the concatenated frames
+(exactly), in every mix of channels; lost frames, admission by HBM budget, backpressure."""
+import time
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_09481_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_09481_gb300 import xe as _xe
+    _xe.load()
+    return _xe
+
+
+def frames_for(N, frame_T, n_frames, seed):
+    return synth.gauss_plane(N, frame_T * n_frames, 1, seed=seed)[0].reshape(n_frames, frame_T, N)
+
+
+def drain(st, want, timeout_s=20.0):
+    out = []
+    t0 = time.time()
+    while len(out) < want and time.time() - t0 < timeout_s:
+        r = st.poll(timeout_ms=100)
+        if r is not None:
+            out.append(r)
+    assert len(out) == want, f"got {len(out)} of {want} integrations"
+    return out
+
+
+@pytest.mark.parametrize("device_source", [False, True])
+def test_integrations_equal_oracle(xe, device_source):
+    N, fT, F, C, n_int = 200, 1024, 4, 3, 2
+    budget = 1 << 30
+    with xe.Stream(N, fT, F * fT, max_chan=8, hbm_budget=budget, ring_frames=3,
+                   device_source=device_source) as st:
+        data = {}
+        for c in range(C):
+            assert st.admit(c) == 0
+            data[c] = frames_for(N, fT, F * n_int, seed=100 + c)
+        for k in range(F * n_int):
+            for c in range(C):
+                fr = torch.from_numpy(data[c][k])
+                fr = fr.cuda() if device_source else fr
+                while st.push(c, fr, k) == xe.XE_EAGAIN:
+                    time.sleep(0.001)
+        res = drain(st, C * n_int)
+    for meta, vis in res:
+        c, q = meta["chan"], meta["integ_index"]
+        assert meta["complete"] == 1 and meta["n_samples"] == F * fT
+        block = data[c][q * F:(q + 1) * F].reshape(1, F * fT, N)
+        np.testing.assert_array_equal(vis, oracle.correlate_dense(block, N, F * fT, 1)[0])
+        assert meta["t_ready_ns"] >= meta["t_last_arrival_ns"] >= meta["t_first_arrival_ns"]
+
+
+def test_same_result_alone_and_in_the_mix(xe):
+    # Channel 0's integrations are bit-identical whether it streams alone or among 12
+    # channels whose frames are batched into the same persistent launches.
+    N, fT, F = 256, 2048, 2
+    mine = frames_for(N, fT, 2 * F, seed=7)
+
+    def run(n_other):
+        with xe.Stream(N, fT, F * fT, max_chan=16, hbm_budget=8 << 30, ring_frames=2) as st:
+            for c in range(1 + n_other):
+                assert st.admit(c) == 0
+            others = {c: frames_for(N, fT, 2 * F, seed=200 + c) for c in range(1, 1 + n_other)}
+            for k in range(2 * F):
+                for c in range(1 + n_other):
+                    fr = torch.from_numpy(mine[k] if c == 0 else others[c][k])
+                    while st.push(c, fr, k) == xe.XE_EAGAIN:
+                        time.sleep(0.0005)
+            res = drain(st, 2 * (1 + n_other))
+            return {m["integ_index"]: v for m, v in res if m["chan"] == 0}
+
+    alone, mixed = run(0), run(11)
+    assert alone.keys() == mixed.keys() == {0, 1}
+    for q in (0, 1):
+        np.testing.assert_array_equal(alone[q], mixed[q])
+
+
+def test_lost_frame_marks_integration_incomplete(xe):
+    N, fT, F = 130, 512, 4
+    fr = frames_for(N, fT, 2 * F, seed=3)
+    with xe.Stream(N, fT, F * fT, max_chan=2, hbm_budget=1 << 30, ring_frames=2) as st:
+        assert st.admit(0) == 0
+        for k in range(2 * F):
+            if k == 2:
+                continue                       # frame 2 never arrives
+            while st.push(0, torch.from_numpy(fr[k]), k) == xe.XE_EAGAIN:
+                time.sleep(0.001)
+        res = sorted(drain(st, 2), key=lambda r: r[0]["integ_index"])
+        assert st.stats()["dropped"] == 1
+    (m0, v0), (m1, v1) = res
+    assert m0["complete"] == 0 and m0["n_samples"] == 3 * fT
+    got0 = np.concatenate([fr[0], fr[1], fr[3]])[None]
+    np.testing.assert_array_equal(v0, oracle.correlate_dense(got0, N, 3 * fT, 1)[0])
+    assert m1["complete"] == 1
+    np.testing.assert_array_equal(v1, oracle.correlate_dense(fr[F:].reshape(1, F * fT, N), N, F * fT, 1)[0])
+
+
+def test_admission_by_hbm_budget(xe):
+    N, fT, F = 512, 4096, 2
+    per_chan = N * (N + 1) * 4 + 2 * fT * N + 2 * 512 * fT      # accumulator + ring + staging
+    with xe.Stream(N, fT, F * fT, max_chan=8, hbm_budget=2 * per_chan + 1000, ring_frames=2) as st:
+        assert st.admit(0) == 0 and st.admit(1) == 0
+        assert st.admit(2) == xe.XE_EBUDGET
+        st.evict(1)
+        assert st.admit(2) == 0
+        assert st.stats()["admitted"] == 2
+    with pytest.raises(xe.XeError):
+        xe.Stream(N, fT, F * fT, max_chan=8, hbm_budget=1000)
+
+
+def test_push_errors_and_backpressure(xe):
+    N, fT = 64, 256
+    fr = torch.from_numpy(frames_for(N, fT, 1, seed=1)[0])
+    with xe.Stream(N, fT, 4 * fT, max_chan=2, hbm_budget=1 << 28, ring_frames=2) as st:
+        with pytest.raises(xe.XeError):
+            st.push(1, fr, 0)                  # channel not admitted
+        assert st.admit(0) == 0
+        assert st.push(0, fr, 0) == 0
+        with pytest.raises(xe.XeError):
+            st.push(0, fr, 0)                  # duplicate sequence number
+        st.flush()
