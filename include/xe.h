@@ -126,6 +126,21 @@ int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stre
 int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
                   int64_t *n_tiles, int64_t *n_iters, int64_t *n_split_tiles);
 
+/* Dump the plan the scheduler builds for a batch, for a given CTA count, schedule
+ * (-1 = the default choice; 0 stream-K, 1 equal k-split, 2 full waves + stream-K tail,
+ * 3 longest-first) and tile width (0 = default, 128 or 256).  Writes into out[0..cap):
+ * {n_tiles, n_segments, n_cta, n_partial}, then per tile {job, chan, i0, j0, nj, kblocks},
+ * then per segment {cta, tile, k_lo, k_hi, slot}.  Returns the number of int32 values the
+ * dump needs (nothing is written when cap is smaller), or a negative XE_* code.
+ * Pure host computation. */
+int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
+                     int sched, int tile_n, int32_t *out, int64_t cap);
+
+/* The plan configuration (persistent CTAs, tile width, schedule) that the calling
+ * thread's last correlation used: the autotuned one if option "autotune" was on when the
+ * batch shape was first seen, else the default choice.  XE_EAGAIN if none yet. */
+int xe_last_config(int *n_cta, int *tile_n, int *sched);
+
 /* ---- streaming server (continuous integration of frames) --------------------------- */
 
 typedef struct xe_stream_cfg {
@@ -159,8 +174,10 @@ typedef struct xe_result {
  * channels are admitted.  Returns XE_OK and *out, or XE_EINVAL / XE_EBUDGET / XE_ENOMEM. */
 int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out);
 
-/* Admit a channel slot if the HBM budget allows it.  Returns XE_OK, XE_EBUDGET when the
- * budget is full, XE_EINVAL for a bad channel id. */
+/* Admit a channel slot if the HBM budget allows it.  A slot holds two int32 accumulators
+ * (one filling while the other is exported), ring_frames frame buffers and its share of the
+ * staging memory.  Returns XE_OK, XE_EBUDGET when the budget is full, XE_EINVAL for a bad
+ * channel id. */
 int xe_stream_admit(xe_stream *s, int chan);
 
 /* Release a channel slot (its pending integration is dropped, its memory returned). */
@@ -174,6 +191,14 @@ int xe_stream_evict(xe_stream *s, int chan);
  * older than the open integration, XE_ECLOSED after close. */
 int xe_stream_push(xe_stream *s, int chan, const uint8_t *frame, int64_t seq,
                    int64_t t_arrival_ns);
+
+/* Push n frames at once (typically one frame of every channel that arrived together):
+ * frame k is channel chans[k]'s frame with sequence number seqs[k], bytes at frames[k],
+ * all with arrival time t_arrival_ns.  Per-frame results (XE_OK, XE_EAGAIN, XE_EINVAL) go to
+ * rc_out[k] when rc_out is not NULL.  Host-source bytes are on the device before the call
+ * returns.  Returns the number of frames accepted, or a negative XE_* code. */
+int xe_stream_push_frames(xe_stream *s, int n, const int *chans, const uint8_t *const *frames,
+                          const int64_t *seqs, int64_t t_arrival_ns, int *rc_out);
 
 /* Flush what has been pushed so far: schedule every ready frame now. */
 int xe_stream_flush(xe_stream *s);
@@ -228,6 +253,10 @@ int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_
  *   "exact_chunk_t"  samples summed by one f32 tensor-memory accumulation before the
  *                    partial sum is moved to int32 (64 .. 131072, default 131072);
  *   "n_cta"          persistent CTAs per launch (0 = one per SM, the default);
+ *   "sched"          triangle schedule, -1 = automatic (default), 0..3 as in xe_plan_dump;
+ *   "tile_n"         tile width 0 = automatic (default), 128 or 256;
+ *   "autotune"       1 = time every (tile width, schedule) candidate the first time a
+ *                    batch shape is correlated and keep the fastest for that shape;
  *   "timing"         1 = record device times of each call (see xe_last_timing).
  * Returns XE_OK or XE_EINVAL. */
 int xe_set_option(const char *key, int64_t value);

@@ -1,12 +1,15 @@
 // xe_api.cu -- host runtime behind the C ABI of include/xe.h: argument checks, the
-// triangle-tile plan of the persistent stream-K scheduler, per-stream scratch memory,
-// the exact-chunk split of long integrations, CUDA-graph replay of batches, and timing.
+// triangle-tile plans and their schedules (segment lists per persistent CTA), the
+// autotuner that picks tile width and schedule per batch shape, per-stream scratch memory,
+// the exact-window split of long integrations, CUDA-graph replay of batches, and timing.
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <vector>
 
@@ -44,6 +47,9 @@ struct Options {
     int operand_bytes = 1;                 // 1: e4m3 operands, 2: f16 operands
     int64_t exact_chunk_t = kExactChunkT;  // samples per f32 accumulation window
     int n_cta = 0;                         // 0: one CTA per SM
+    int sched = -1;                        // -1: heuristic / autotuned; else a Sched
+    int tile_n = 0;                        // 0: heuristic / autotuned; else 128 or 256
+    int autotune = 0;                      // 1: time candidate plans on first sight of a shape
     int timing = 0;
 };
 static Options g_opt;
@@ -57,11 +63,20 @@ struct JobShape {
     int C;
 };
 
+struct TuneCfg {
+    int n_cta;
+    int tile_n;
+    int sched;
+};
+
 struct HostPlan {
     std::vector<Tile> tiles;
-    int64_t total_iters = 0;
+    std::vector<Seg> segs;
+    std::vector<int> seg_off;     // n_cta + 1 entries
+    std::vector<int> tile_slots;
     int n_cta = 0;
-    int64_t n_split = 0;
+    int n_partial = 0;
+    int64_t total_iters = 0;
 };
 
 static int n_pad_of(int N) { return (N + kNPad - 1) / kNPad * kNPad; }
@@ -71,47 +86,179 @@ static int64_t kblocks_of(int64_t T, int eb) {
     return (T + ks - 1) / ks;
 }
 
-// Triangle tiles of one job: row blocks of 128 inputs; for each, column tiles of 256 inputs
-// aligned to 256, except a 128-wide half tile when the row block starts in the middle of a
-// 256-aligned column block.  Together they cover every (i, j >= i) exactly once.
-static void build_tiles(const std::vector<JobShape> &jobs, int eb, int n_sm, HostPlan &p) {
-    p.tiles.clear();
-    int64_t it = 0;
+// Triangle tiles of every job and channel: row blocks of 128 inputs; column tiles of width
+// tile_n aligned to tile_n, plus a 128-wide half tile where a row block starts mid-way
+// through a 256-aligned column block.  Together they cover every (i, j >= i) exactly once.
+static void enumerate_tiles(const std::vector<JobShape> &jobs, int eb, int tile_n,
+                            std::vector<Tile> &tiles) {
+    tiles.clear();
     for (int q = 0; q < int(jobs.size()); ++q) {
         const JobShape &js = jobs[q];
         const int kb = int(kblocks_of(js.T, eb));
-        for (int c = 0; c < js.C; ++c) {
+        for (int c = 0; c < js.C; ++c)
             for (int i0 = 0; i0 < js.N; i0 += kBM) {
                 int j0 = i0;
-                if (j0 % kBN != 0) {
-                    p.tiles.push_back(Tile{q, c, i0, j0, kBM, kb, it});
-                    it += kb;
+                if (j0 % tile_n != 0) {
+                    tiles.push_back(Tile{q, c, i0, j0, kBM, kb, 0, 0});
                     j0 += kBM;
                 }
-                for (; j0 < js.N; j0 += kBN) {
-                    p.tiles.push_back(Tile{q, c, i0, j0, kBN, kb, it});
-                    it += kb;
-                }
+                for (; j0 < js.N; j0 += tile_n) tiles.push_back(Tile{q, c, i0, j0, tile_n, kb, 0, 0});
             }
+    }
+}
+
+// Equal contiguous ranges of the concatenated k-iterations of tiles [t_lo, t_hi), dealt to
+// CTAs 0..G-1 (appended to their lists).
+static void stream_k(const std::vector<Tile> &tiles, int t_lo, int t_hi, int G,
+                     std::vector<std::vector<Seg>> &per) {
+    int64_t W = 0;
+    for (int t = t_lo; t < t_hi; ++t) W += tiles[size_t(t)].kblocks;
+    if (W == 0) return;
+    const int64_t g = std::min<int64_t>(G, W);
+    int t = t_lo;
+    int64_t tb = 0;   // first iteration of tile t in the concatenation
+    for (int64_t b = 0; b < g; ++b) {
+        const int64_t r0 = b * W / g, r1 = (b + 1) * W / g;
+        while (t < t_hi && tb + tiles[size_t(t)].kblocks <= r0) { tb += tiles[size_t(t)].kblocks; ++t; }
+        int tt = t;
+        int64_t ttb = tb;
+        while (tt < t_hi && ttb < r1) {
+            const int64_t lo = std::max(r0, ttb) - ttb;
+            const int64_t hi = std::min(r1, ttb + tiles[size_t(tt)].kblocks) - ttb;
+            if (hi > lo) per[size_t(b)].push_back(Seg{tt, int(lo), int(hi), -1});
+            ttb += tiles[size_t(tt)].kblocks;
+            ++tt;
         }
     }
-    p.total_iters = it;
-    int64_t g = n_sm;
-    if (g > it) g = it;
-    if (g < 1) g = 1;
-    p.n_cta = int(g);
-    // Tiles whose iterations are split across CTA ranges.
-    p.n_split = 0;
-    for (const Tile &t : p.tiles) {
-        const int64_t b0 = ((t.iter_begin + 1) * g - 1) / it;
-        const int64_t b1 = ((t.iter_begin + t.kblocks) * g - 1) / it;
-        p.n_split += (b0 != b1) ? 1 : 0;
+}
+
+static void schedule(HostPlan &p, int G, int sched) {
+    const int n = int(p.tiles.size());
+    std::vector<std::vector<Seg>> per(static_cast<size_t>(G));
+    if (sched == kSchedSplit) {
+        int s = n < G ? std::max(1, G / n) : 1;
+        int min_kb = 1 << 30;
+        for (const Tile &t : p.tiles) min_kb = std::min(min_kb, t.kblocks);
+        s = std::min(s, std::max(1, min_kb));
+        int64_t item = 0;
+        const int64_t n_items = int64_t(n) * s;
+        const int64_t g = std::min<int64_t>(G, n_items);
+        for (int t = 0; t < n; ++t)
+            for (int k = 0; k < s; ++k, ++item) {
+                const int kb = p.tiles[size_t(t)].kblocks;
+                const int lo = int(int64_t(k) * kb / s), hi = int(int64_t(k + 1) * kb / s);
+                if (hi > lo) per[size_t(item % g)].push_back(Seg{t, lo, hi, -1});
+            }
+    } else if (sched == kSchedHybrid) {
+        const int full = (n / G) * G;
+        for (int t = 0; t < full; ++t)
+            per[size_t(t % G)].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
+        stream_k(p.tiles, full, n, G, per);
+    } else if (sched == kSchedLPT) {
+        std::vector<int> order(static_cast<size_t>(n));
+        for (int t = 0; t < n; ++t) order[size_t(t)] = t;
+        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+            return p.tiles[size_t(a)].kblocks > p.tiles[size_t(b)].kblocks;
+        });
+        using Load = std::pair<int64_t, int>;
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int b = 0; b < G; ++b) heap.push(Load{0, b});
+        for (int t : order) {
+            Load l = heap.top();
+            heap.pop();
+            per[size_t(l.second)].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
+            l.first += p.tiles[size_t(t)].kblocks;
+            heap.push(l);
+        }
+        for (auto &v : per)
+            std::sort(v.begin(), v.end(), [](const Seg &a, const Seg &b) { return a.tile < b.tile; });
+    } else {
+        stream_k(p.tiles, 0, n, G, per);
     }
+    // Drop trailing CTAs without work; build the CSR lists.
+    int used = G;
+    while (used > 1 && per[size_t(used - 1)].empty()) --used;
+    p.n_cta = used;
+    p.segs.clear();
+    p.seg_off.assign(size_t(used) + 1, 0);
+    for (int b = 0; b < used; ++b) {
+        p.seg_off[size_t(b)] = int(p.segs.size());
+        for (const Seg &s : per[size_t(b)]) p.segs.push_back(s);
+    }
+    p.seg_off[size_t(used)] = int(p.segs.size());
+}
+
+// Mark partial segments, give each a workspace slot, and list the slots of every tile.
+// Returns false if the segments do not partition every tile's k-range exactly.
+static bool finalize_parts(HostPlan &p) {
+    const int n = int(p.tiles.size());
+    std::vector<std::vector<int>> by_tile(static_cast<size_t>(n));
+    for (int q = 0; q < int(p.segs.size()); ++q) by_tile[size_t(p.segs[size_t(q)].tile)].push_back(q);
+    p.tile_slots.clear();
+    p.n_partial = 0;
+    p.total_iters = 0;
+    for (int t = 0; t < n; ++t) {
+        Tile &tl = p.tiles[size_t(t)];
+        std::vector<int> &qs = by_tile[size_t(t)];
+        std::sort(qs.begin(), qs.end(),
+                  [&](int a, int b) { return p.segs[size_t(a)].k_lo < p.segs[size_t(b)].k_lo; });
+        int k = 0;
+        for (int q : qs) {
+            if (p.segs[size_t(q)].k_lo != k) return false;
+            k = p.segs[size_t(q)].k_hi;
+        }
+        if (k != tl.kblocks) return false;
+        p.total_iters += tl.kblocks;
+        tl.n_parts = 0;
+        tl.part_off = int(p.tile_slots.size());
+        if (qs.size() > 1) {
+            for (int q : qs) {
+                p.segs[size_t(q)].slot = p.n_partial;
+                p.tile_slots.push_back(p.n_partial);
+                ++p.n_partial;
+            }
+            tl.n_parts = int(qs.size());
+        }
+    }
+    return true;
+}
+
+static bool uniform_kblocks(const std::vector<Tile> &tiles) {
+    for (const Tile &t : tiles)
+        if (t.kblocks != tiles[0].kblocks) return false;
+    return true;
+}
+
+// The default plan when nothing is tuned: 256-wide tiles; with fewer tiles than CTAs and
+// equal tile lengths, split every tile into the same number of k-parts so that concurrently
+// running CTAs read the same k-blocks (shared in L2); many equal tiles: whole tiles in full
+// waves, the last wave stream-K; uneven tiles: whole tiles, longest first.
+static TuneCfg heuristic(const std::vector<JobShape> &jobs, int eb, int n_sm) {
+    TuneCfg c{g_opt.n_cta > 0 ? g_opt.n_cta : n_sm, g_opt.tile_n > 0 ? g_opt.tile_n : 256, g_opt.sched};
+    if (c.sched < 0) {
+        std::vector<Tile> tiles;
+        enumerate_tiles(jobs, eb, c.tile_n, tiles);
+        if (!uniform_kblocks(tiles)) c.sched = kSchedLPT;
+        else if (int(tiles.size()) < c.n_cta) c.sched = kSchedSplit;
+        else c.sched = kSchedHybrid;
+    }
+    return c;
+}
+
+static bool build_plan(const std::vector<JobShape> &jobs, int eb, const TuneCfg &cfg, HostPlan &p) {
+    enumerate_tiles(jobs, eb, cfg.tile_n, p.tiles);
+    if (p.tiles.empty()) return false;
+    schedule(p, std::max(1, cfg.n_cta), cfg.sched);
+    return finalize_parts(p);
 }
 
 struct DevPlan {
     HostPlan host;
-    Tile *d_tiles = nullptr;
+    void *blob = nullptr;         // tiles | segs | seg_off | tile_slots
+    const Tile *d_tiles = nullptr;
+    const Seg *d_segs = nullptr;
+    const int *d_seg_off = nullptr;
+    const int *d_tile_slots = nullptr;
 };
 
 struct Scratch {
@@ -120,7 +267,7 @@ struct Scratch {
     int32_t *ws = nullptr;
     size_t ws_bytes = 0;
     int *counters = nullptr;
-    size_t n_counters = 0;
+    size_t counters_bytes = 0;
     int *status = nullptr;
     cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
 };
@@ -133,15 +280,31 @@ struct HostIO {
     size_t vis_bytes = 0;
 };
 
+struct LaunchRec {
+    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor
+    int eb;
+    JobTable jt;
+    PlanDev pd;
+};
+
+struct GraphRec {
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    std::vector<cudaGraphNode_t> nodes;
+};
+
 struct Device {
     int id = -1;
     int n_sm = 0;
     HostIO io;
     std::map<std::vector<int64_t>, DevPlan *> plans;
+    std::map<std::vector<int64_t>, TuneCfg> tuned;
     std::map<cudaStream_t, Scratch *> scratch;
+    std::map<std::vector<int64_t>, GraphRec *> graphs;
 };
 
 static std::map<int, Device *> g_devs;
+static thread_local TuneCfg g_last_cfg{0, 0, -1};
 
 static int get_device(Device **out) {
     int dev = 0;
@@ -164,36 +327,58 @@ static int get_device(Device **out) {
     return XE_OK;
 }
 
-static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, DevPlan **out) {
-    const int n_sm = g_opt.n_cta > 0 ? g_opt.n_cta : d->n_sm;
-    std::vector<int64_t> key{eb, n_sm};
+static std::vector<int64_t> shape_key(const std::vector<JobShape> &jobs, int eb) {
+    std::vector<int64_t> key{eb};
     for (const JobShape &j : jobs) {
         key.push_back(j.N);
         key.push_back(j.T);
         key.push_back(j.C);
     }
+    return key;
+}
+
+static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const TuneCfg &cfg,
+                    DevPlan **out) {
+    std::vector<int64_t> key = shape_key(jobs, eb);
+    key.push_back(cfg.n_cta);
+    key.push_back(cfg.tile_n);
+    key.push_back(cfg.sched);
     auto it = d->plans.find(key);
     if (it != d->plans.end()) {
         *out = it->second;
         return XE_OK;
     }
     DevPlan *p = new DevPlan;
-    build_tiles(jobs, eb, n_sm, p->host);
-    if (p->host.tiles.size() > size_t(0x7fffffff)) {
+    if (!build_plan(jobs, eb, cfg, p->host)) {
         delete p;
-        return fail(XE_EINVAL, "too many tiles");
+        return fail(XE_EINVAL, "internal: plan does not cover the triangle");
     }
-    const size_t bytes = p->host.tiles.size() * sizeof(Tile);
-    if (cudaMalloc(&p->d_tiles, bytes) != cudaSuccess) {
+    const HostPlan &h = p->host;
+    const size_t b_t = h.tiles.size() * sizeof(Tile), b_s = h.segs.size() * sizeof(Seg);
+    const size_t b_o = h.seg_off.size() * sizeof(int), b_l = (h.tile_slots.size() + 1) * sizeof(int);
+    const size_t o_s = (b_t + 255) / 256 * 256, o_o = o_s + (b_s + 255) / 256 * 256,
+                 o_l = o_o + (b_o + 255) / 256 * 256, total = o_l + b_l;
+    if (cudaMalloc(&p->blob, total) != cudaSuccess) {
+        cudaGetLastError();
         delete p;
-        return fail(XE_ENOMEM, "cannot allocate %zu bytes for the tile plan", bytes);
+        return fail(XE_ENOMEM, "cannot allocate %zu bytes for a plan", total);
     }
-    cudaError_t e = cudaMemcpy(p->d_tiles, p->host.tiles.data(), bytes, cudaMemcpyHostToDevice);
+    std::vector<uint8_t> host(total, 0);
+    memcpy(host.data(), h.tiles.data(), b_t);
+    memcpy(host.data() + o_s, h.segs.data(), b_s);
+    memcpy(host.data() + o_o, h.seg_off.data(), b_o);
+    if (!h.tile_slots.empty()) memcpy(host.data() + o_l, h.tile_slots.data(), b_l - sizeof(int));
+    cudaError_t e = cudaMemcpy(p->blob, host.data(), total, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
-        cudaFree(p->d_tiles);
+        cudaFree(p->blob);
         delete p;
         return fail(XE_ECUDA, "plan upload failed: %s", cudaGetErrorString(e));
     }
+    uint8_t *base = static_cast<uint8_t *>(p->blob);
+    p->d_tiles = reinterpret_cast<const Tile *>(base);
+    p->d_segs = reinterpret_cast<const Seg *>(base + o_s);
+    p->d_seg_off = reinterpret_cast<const int *>(base + o_o);
+    p->d_tile_slots = reinterpret_cast<const int *>(base + o_l);
     d->plans[key] = p;
     *out = p;
     return XE_OK;
@@ -208,7 +393,7 @@ static int grow(void **ptr, size_t *have, size_t need, bool zero) {
         *ptr = nullptr;
         *have = 0;
     }
-    size_t sz = need + need / 8;
+    size_t sz = need + need / 8 + 256;
     if (cudaMalloc(ptr, sz) != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
@@ -250,21 +435,18 @@ static int check_job(const uint8_t *in, int N, int64_t T, int C, const int32_t *
     return XE_OK;
 }
 
-// Enqueue a batch of jobs (all validated) on stream s with the given algorithm.
-static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, int accumulate = 0) {
-    Device *d = nullptr;
-    int rc = get_device(&d);
-    if (rc) return rc;
-    Scratch *sc = nullptr;
-    rc = get_scratch(d, s, &sc);
-    if (rc) return rc;
-    const bool timing = g_opt.timing != 0;
-    if (timing) XE_CUDA(cudaEventRecord(sc->ev[0], s));
-
+// Build the launch sequence for a batch (allocating scratch and plans as needed), without
+// enqueuing anything.  `forced` overrides the plan configuration (autotuner candidates).
+static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, int algo,
+                          int accumulate, const TuneCfg *forced, std::vector<LaunchRec> &out) {
+    out.clear();
     if (algo == XE_ALGO_IMMA) {
         for (int g0 = 0; g0 < n_jobs; g0 += kMaxJobs) {
-            const int ng = n_jobs - g0 < kMaxJobs ? n_jobs - g0 : kMaxJobs;
-            JobTable jt{};
+            const int ng = std::min(n_jobs - g0, kMaxJobs);
+            LaunchRec r{};
+            r.kind = 2;
+            r.eb = 1;
+            JobTable &jt = r.jt;
             jt.n_jobs = ng;
             jt.accumulate = accumulate ? 1 : 0;
             int64_t blocks = 0;
@@ -274,7 +456,6 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
                 jd.in = j.in;
                 jd.vis = j.vis;
                 jd.T = j.T;
-                jd.t0 = 0;
                 jd.T_in = j.T;
                 jd.N = j.N;
                 jd.C = j.n_chan;
@@ -283,91 +464,253 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
                 blocks += imma_blocks(j.N, j.n_chan);
             }
             jt.total_stage_blocks = blocks;
-            XE_CUDA(launch_imma(jt, s));
+            out.push_back(r);
         }
-        if (timing) {
-            XE_CUDA(cudaEventRecord(sc->ev[1], s));
-            XE_CUDA(cudaEventRecord(sc->ev[2], s));
+        return XE_OK;
+    }
+    const int eb = g_opt.operand_bytes;
+    const int64_t wt = g_opt.exact_chunk_t / samples_per_stage(eb) * samples_per_stage(eb);
+    int64_t max_T = 0;
+    for (int q = 0; q < n_jobs; ++q) max_T = std::max(max_T, jobs[q].T);
+    const int64_t n_win = (max_T + wt - 1) / wt;
+    for (int64_t w = 0; w < n_win; ++w) {
+        std::vector<int> act;
+        for (int q = 0; q < n_jobs; ++q)
+            if (jobs[q].T > w * wt) act.push_back(q);
+        for (size_t g0 = 0; g0 < act.size(); g0 += kMaxJobs) {
+            const int ng = int(std::min(act.size() - g0, size_t(kMaxJobs)));
+            std::vector<JobShape> shapes;
+            LaunchRec st{};
+            st.kind = 0;
+            st.eb = eb;
+            JobTable &jt = st.jt;
+            jt.n_jobs = ng;
+            jt.accumulate = (w > 0 || accumulate) ? 1 : 0;
+            size_t plane_off = 0;
+            int64_t blocks = 0;
+            for (int k = 0; k < ng; ++k) {
+                const xe_job &j = jobs[act[g0 + size_t(k)]];
+                const int64_t Tw = std::min(j.T - w * wt, wt);
+                shapes.push_back(JobShape{j.N, Tw, j.n_chan});
+                JobDev &jd = jt.jobs[k];
+                jd.in = j.in;
+                jd.vis = j.vis;
+                jd.T = Tw;
+                jd.t0 = w * wt;
+                jd.T_in = j.T;
+                jd.N = j.N;
+                jd.n_pad = n_pad_of(j.N);
+                jd.C = j.n_chan;
+                jd.kblocks = int(kblocks_of(Tw, eb));
+                jd.plane_chan_bytes = int64_t(jd.kblocks) * 2 * jd.n_pad * kRowBytes;
+                jd.vis_chan_elems = int64_t(j.N) * (j.N + 1);
+                jd.stage_block0 = blocks;
+                blocks += int64_t(j.n_chan) * jd.kblocks * (jd.n_pad / 256);
+                plane_off += size_t(jd.plane_chan_bytes) * size_t(j.n_chan);
+            }
+            jt.total_stage_blocks = blocks;
+            int rc = grow(reinterpret_cast<void **>(&sc->planes), &sc->planes_bytes, plane_off, false);
+            if (rc) return rc;
+            size_t off = 0;
+            for (int k = 0; k < ng; ++k) {
+                jt.jobs[k].planes = sc->planes + off;
+                off += size_t(jt.jobs[k].plane_chan_bytes) * size_t(jt.jobs[k].C);
+            }
+            TuneCfg cfg;
+            if (forced) {
+                cfg = *forced;
+            } else {
+                auto it = d->tuned.find(shape_key(shapes, eb));
+                cfg = it != d->tuned.end() ? it->second : heuristic(shapes, eb, d->n_sm);
+            }
+            g_last_cfg = cfg;
+            DevPlan *p = nullptr;
+            rc = get_plan(d, shapes, eb, cfg, &p);
+            if (rc) return rc;
+            const size_t ws_need =
+                size_t(std::max(1, p->host.n_partial)) * size_t(kWsSlotElems) * sizeof(int32_t);
+            rc = grow(reinterpret_cast<void **>(&sc->ws), &sc->ws_bytes, ws_need, false);
+            if (rc) return rc;
+            rc = grow(reinterpret_cast<void **>(&sc->counters), &sc->counters_bytes,
+                      p->host.tiles.size() * sizeof(int), true);
+            if (rc) return rc;
+            LaunchRec tc = st;
+            tc.kind = 1;
+            PlanDev &pd = tc.pd;
+            pd.tiles = p->d_tiles;
+            pd.segs = p->d_segs;
+            pd.seg_off = p->d_seg_off;
+            pd.tile_slots = p->d_tile_slots;
+            pd.n_tiles = int(p->host.tiles.size());
+            pd.n_cta = p->host.n_cta;
+            pd.ws = sc->ws;
+            pd.counters = sc->counters;
+            pd.status = sc->status;
+            out.push_back(st);
+            out.push_back(tc);
         }
-    } else {
-        const int eb = g_opt.operand_bytes;
-        const int64_t wt = g_opt.exact_chunk_t / samples_per_stage(eb) * samples_per_stage(eb);
-        int64_t max_T = 0;
-        for (int q = 0; q < n_jobs; ++q) max_T = jobs[q].T > max_T ? jobs[q].T : max_T;
-        const int64_t n_win = (max_T + wt - 1) / wt;
-        bool stage_marked = false;
-        for (int64_t w = 0; w < n_win; ++w) {
-            // Jobs that still have samples in window w, in groups of kMaxJobs.
-            std::vector<int> act;
-            for (int q = 0; q < n_jobs; ++q)
-                if (jobs[q].T > w * wt) act.push_back(q);
-            for (size_t g0 = 0; g0 < act.size(); g0 += kMaxJobs) {
-                const int ng = int(act.size() - g0 < size_t(kMaxJobs) ? act.size() - g0 : kMaxJobs);
-                std::vector<JobShape> shapes;
-                JobTable jt{};
-                jt.n_jobs = ng;
-                jt.accumulate = (w > 0 || accumulate) ? 1 : 0;
-                size_t plane_off = 0;
-                int64_t blocks = 0;
-                for (int k = 0; k < ng; ++k) {
-                    const xe_job &j = jobs[act[g0 + k]];
-                    const int64_t Tw = (j.T - w * wt) < wt ? (j.T - w * wt) : wt;
-                    shapes.push_back(JobShape{j.N, Tw, j.n_chan});
-                    JobDev &jd = jt.jobs[k];
-                    jd.in = j.in;
-                    jd.vis = j.vis;
-                    jd.T = Tw;
-                    jd.t0 = w * wt;
-                    jd.T_in = j.T;
-                    jd.N = j.N;
-                    jd.n_pad = n_pad_of(j.N);
-                    jd.C = j.n_chan;
-                    jd.kblocks = int(kblocks_of(Tw, eb));
-                    jd.plane_chan_bytes = int64_t(jd.kblocks) * 2 * jd.n_pad * kRowBytes;
-                    jd.vis_chan_elems = int64_t(j.N) * (j.N + 1);
-                    jd.stage_block0 = blocks;
-                    blocks += int64_t(j.n_chan) * jd.kblocks * (jd.n_pad / 256);
-                    plane_off += size_t(jd.plane_chan_bytes) * j.n_chan;
-                }
-                jt.total_stage_blocks = blocks;
-                rc = grow(reinterpret_cast<void **>(&sc->planes), &sc->planes_bytes, plane_off, false);
-                if (rc) return rc;
-                size_t off = 0;
-                for (int k = 0; k < ng; ++k) {
-                    jt.jobs[k].planes = sc->planes + off;
-                    off += size_t(jt.jobs[k].plane_chan_bytes) * jt.jobs[k].C;
-                }
-                DevPlan *p = nullptr;
-                rc = get_plan(d, shapes, eb, &p);
-                if (rc) return rc;
-                const size_t ws_need = size_t(2) * p->host.n_cta * kWsSlotElems * sizeof(int32_t);
-                rc = grow(reinterpret_cast<void **>(&sc->ws), &sc->ws_bytes, ws_need, false);
-                if (rc) return rc;
-                size_t cnt_have = sc->n_counters * sizeof(int);
-                rc = grow(reinterpret_cast<void **>(&sc->counters), &cnt_have,
-                          p->host.tiles.size() * sizeof(int), true);
-                if (rc) return rc;
-                sc->n_counters = cnt_have / sizeof(int);
+    }
+    return XE_OK;
+}
 
-                PlanDev pd{};
-                pd.tiles = p->d_tiles;
-                pd.n_tiles = int(p->host.tiles.size());
-                pd.n_cta = p->host.n_cta;
-                pd.total_iters = p->host.total_iters;
-                pd.ws = sc->ws;
-                pd.counters = sc->counters;
-                pd.status = sc->status;
-                XE_CUDA(launch_stage(jt, eb, s));
-                if (timing && !stage_marked) {
-                    XE_CUDA(cudaEventRecord(sc->ev[1], s));
-                    stage_marked = true;
-                }
-                XE_CUDA(launch_tc(jt, pd, eb, s));
+static cudaError_t enqueue(const LaunchRec &r, cudaStream_t s) {
+    if (r.kind == 0) return launch_stage(r.jt, r.eb, s);
+    if (r.kind == 1) return launch_tc(r.jt, r.pd, r.eb, s);
+    return launch_imma(r.jt, s);
+}
+
+static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
+    cudaKernelNodeParams p{};
+    args[0] = const_cast<JobTable *>(&r.jt);
+    args[1] = const_cast<PlanDev *>(&r.pd);
+    p.kernelParams = args;
+    p.extra = nullptr;
+    if (r.kind == 0) {
+        p.func = const_cast<void *>(stage_kernel_fn(r.eb));
+        p.gridDim = dim3(unsigned(r.jt.total_stage_blocks));
+        p.blockDim = dim3(256);
+        p.sharedMemBytes = 0;
+    } else if (r.kind == 1) {
+        p.func = const_cast<void *>(tc_kernel_fn(r.eb));
+        p.gridDim = dim3(unsigned(r.pd.n_cta));
+        p.blockDim = dim3(kTcThreads);
+        p.sharedMemBytes = unsigned(tc_smem_bytes());
+    } else {
+        p.func = const_cast<void *>(imma_kernel_fn());
+        p.gridDim = dim3(unsigned(r.jt.total_stage_blocks));
+        p.blockDim = dim3(128);
+        p.sharedMemBytes = 0;
+    }
+    return p;
+}
+
+// Time one launch sequence (median of `reps` runs after one warm-up) on stream s.
+static float time_launches(const std::vector<LaunchRec> &recs, cudaStream_t s, Scratch *sc, int reps) {
+    std::vector<float> t;
+    for (int k = 0; k < reps + 1; ++k) {
+        cudaEventRecord(sc->ev[0], s);
+        for (const LaunchRec &r : recs) enqueue(r, s);
+        cudaEventRecord(sc->ev[2], s);
+        cudaEventSynchronize(sc->ev[2]);
+        float ms = 0;
+        cudaEventElapsedTime(&ms, sc->ev[0], sc->ev[2]);
+        if (k > 0) t.push_back(ms);
+    }
+    std::sort(t.begin(), t.end());
+    return t.empty() ? 1e30f : t[t.size() / 2];
+}
+
+// Pick tile width and schedule for a batch shape by timing the candidates (each candidate
+// overwrites the batch's own outputs, so only non-accumulating calls tune).
+static int autotune(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, cudaStream_t s) {
+    const int eb = g_opt.operand_bytes;
+    if (n_jobs > kMaxJobs || n_jobs < 1) return XE_OK;
+    std::vector<JobShape> shapes;
+    for (int q = 0; q < n_jobs; ++q) {
+        if (jobs[q].T > g_opt.exact_chunk_t) return XE_OK;  // windowed: keep the heuristic
+        shapes.push_back(JobShape{jobs[q].N, jobs[q].T, jobs[q].n_chan});
+    }
+    for (JobShape &j : shapes) j.T = std::min<int64_t>(j.T, g_opt.exact_chunk_t);
+    const std::vector<int64_t> key = shape_key(shapes, eb);
+    if (d->tuned.count(key)) return XE_OK;
+    const int n_cta = g_opt.n_cta > 0 ? g_opt.n_cta : d->n_sm;
+    TuneCfg best = heuristic(shapes, eb, d->n_sm);
+    float best_ms = 1e30f;
+    const int widths[2] = {256, 128};
+    for (int wi = 0; wi < 2; ++wi) {
+        if (g_opt.tile_n > 0 && widths[wi] != g_opt.tile_n) continue;
+        for (int si = 0; si < kNumSched; ++si) {
+            if (g_opt.sched >= 0 && si != g_opt.sched) continue;
+            TuneCfg c{n_cta, widths[wi], si};
+            std::vector<LaunchRec> recs;
+            int rc = build_launches(d, sc, jobs, n_jobs, XE_ALGO_TC, 0, &c, recs);
+            if (rc) return rc;
+            const float ms = time_launches(recs, s, sc, 3);
+            if (ms < best_ms) {
+                best_ms = ms;
+                best = c;
             }
         }
-        if (timing) XE_CUDA(cudaEventRecord(sc->ev[2], s));
+    }
+    XE_CUDA(cudaGetLastError());
+    d->tuned[key] = best;
+    return XE_OK;
+}
+
+// Enqueue a batch of jobs (all validated) on stream s.
+static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, int accumulate = 0,
+                    int use_graph = 0) {
+    Device *d = nullptr;
+    int rc = get_device(&d);
+    if (rc) return rc;
+    Scratch *sc = nullptr;
+    rc = get_scratch(d, s, &sc);
+    if (rc) return rc;
+    if (algo == XE_ALGO_TC && g_opt.autotune && !accumulate) {
+        rc = autotune(d, sc, jobs, n_jobs, s);
+        if (rc) return rc;
+    }
+    std::vector<LaunchRec> recs;
+    rc = build_launches(d, sc, jobs, n_jobs, algo, accumulate, nullptr, recs);
+    if (rc) return rc;
+    const bool timing = g_opt.timing != 0;
+    if (timing) XE_CUDA(cudaEventRecord(sc->ev[0], s));
+
+    if (use_graph && algo == XE_ALGO_TC) {
+        // One CUDA graph per (stream, batch shape, launch geometry); the kernel arguments
+        // (pointers) are refreshed in place on every replay.
+        std::vector<int64_t> key{reinterpret_cast<int64_t>(s), accumulate};
+        for (int q = 0; q < n_jobs; ++q) {
+            key.push_back(jobs[q].N);
+            key.push_back(jobs[q].T);
+            key.push_back(jobs[q].n_chan);
+        }
+        for (const LaunchRec &r : recs) {
+            key.push_back(r.kind);
+            key.push_back(r.kind == 1 ? int64_t(r.pd.n_cta) : r.jt.total_stage_blocks);
+            key.push_back(reinterpret_cast<int64_t>(r.kind == 1 ? static_cast<const void *>(r.pd.segs)
+                                                                : nullptr));
+        }
+        GraphRec *g = nullptr;
+        auto it = d->graphs.find(key);
+        if (it == d->graphs.end()) {
+            XE_CUDA(tc_prepare());
+            g = new GraphRec;
+            XE_CUDA(cudaGraphCreate(&g->graph, 0));
+            cudaGraphNode_t prev = nullptr;
+            for (const LaunchRec &r : recs) {
+                void *args[2];
+                cudaKernelNodeParams kp = node_params(r, args);
+                cudaGraphNode_t node;
+                XE_CUDA(cudaGraphAddKernelNode(&node, g->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
+                g->nodes.push_back(node);
+                prev = node;
+            }
+            XE_CUDA(cudaGraphInstantiate(&g->exec, g->graph, 0));
+            d->graphs[key] = g;
+        } else {
+            g = it->second;
+            for (size_t k = 0; k < recs.size(); ++k) {
+                void *args[2];
+                cudaKernelNodeParams kp = node_params(recs[k], args);
+                XE_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->nodes[k], &kp));
+            }
+        }
+        if (timing) XE_CUDA(cudaEventRecord(sc->ev[1], s));
+        XE_CUDA(cudaGraphLaunch(g->exec, s));
+    } else {
+        bool marked = false;
+        for (const LaunchRec &r : recs) {
+            if (timing && !marked && r.kind != 0) {
+                XE_CUDA(cudaEventRecord(sc->ev[1], s));   // staging done (or none)
+                marked = true;
+            }
+            XE_CUDA(enqueue(r, s));
+        }
+        if (timing && !marked) XE_CUDA(cudaEventRecord(sc->ev[1], s));
     }
     if (timing) {
+        XE_CUDA(cudaEventRecord(sc->ev[2], s));
         for (int k = 0; k < 3; ++k) g_last_ev[k] = sc->ev[k];
     }
     return XE_OK;
@@ -376,6 +719,25 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
 int run_jobs_accumulate(const xe_job *jobs, int n_jobs, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     return run_jobs(jobs, n_jobs, XE_ALGO_TC, s, 1);
+}
+
+static int plan_from_args(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
+                          int sched, int tile_n, HostPlan &p) {
+    if (!N || !T || !n_chan || n_jobs < 1 || n_cta < 1) return fail(XE_EINVAL, "bad plan query");
+    if (sched < -1 || sched >= kNumSched) return fail(XE_EINVAL, "bad schedule");
+    if (tile_n != 0 && tile_n != 128 && tile_n != 256) return fail(XE_EINVAL, "bad tile width");
+    std::vector<JobShape> shapes;
+    for (int q = 0; q < n_jobs; ++q) {
+        if (N[q] < 1 || T[q] < 1 || n_chan[q] < 1) return fail(XE_EINVAL, "bad job %d", q);
+        shapes.push_back(JobShape{N[q], T[q], n_chan[q]});
+    }
+    TuneCfg c = heuristic(shapes, g_opt.operand_bytes, n_cta);
+    c.n_cta = n_cta;
+    if (sched >= 0) c.sched = sched;
+    if (tile_n > 0) c.tile_n = tile_n;
+    if (!build_plan(shapes, g_opt.operand_bytes, c, p))
+        return fail(XE_EINVAL, "plan does not cover the triangle");
+    return XE_OK;
 }
 
 }  // namespace xe
@@ -421,6 +783,16 @@ int xe_set_option(const char *key, int64_t value) {
     } else if (!strcmp(key, "n_cta")) {
         if (value < 0 || value > 4096) return fail(XE_EINVAL, "n_cta must lie in [0, 4096]");
         g_opt.n_cta = int(value);
+    } else if (!strcmp(key, "sched")) {
+        if (value < -1 || value >= kNumSched)
+            return fail(XE_EINVAL, "sched must lie in [-1, %d]", kNumSched - 1);
+        g_opt.sched = int(value);
+    } else if (!strcmp(key, "tile_n")) {
+        if (value != 0 && value != 128 && value != 256)
+            return fail(XE_EINVAL, "tile_n must be 0, 128 or 256");
+        g_opt.tile_n = int(value);
+    } else if (!strcmp(key, "autotune")) {
+        g_opt.autotune = value ? 1 : 0;
     } else if (!strcmp(key, "timing")) {
         g_opt.timing = value ? 1 : 0;
     } else {
@@ -441,6 +813,13 @@ int xe_last_timing(float *stage_ms, float *correlate_ms) {
     if (stage_ms) *stage_ms = a;
     if (correlate_ms) *correlate_ms = b;
     return XE_OK;
+}
+
+int xe_last_config(int *n_cta, int *tile_n, int *sched) {
+    if (n_cta) *n_cta = g_last_cfg.n_cta;
+    if (tile_n) *tile_n = g_last_cfg.tile_n;
+    if (sched) *sched = g_last_cfg.sched;
+    return g_last_cfg.sched < 0 ? XE_EAGAIN : XE_OK;
 }
 
 int xe_correlate_async(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis, int algo,
@@ -487,30 +866,58 @@ int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int3
 }
 
 int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stream) {
-    (void)use_graph;
     if (!jobs || n_jobs < 1) return fail(XE_EINVAL, "empty batch");
     for (int q = 0; q < n_jobs; ++q) {
         int rc = check_job(jobs[q].in, jobs[q].N, jobs[q].T, jobs[q].n_chan, jobs[q].vis);
         if (rc) return rc;
     }
     std::lock_guard<std::mutex> lk(g_mu);
-    return run_jobs(jobs, n_jobs, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream));
+    return run_jobs(jobs, n_jobs, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream), 0, use_graph);
 }
 
 int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
                   int64_t *n_tiles, int64_t *n_iters, int64_t *n_split_tiles) {
-    if (!N || !T || !n_chan || n_jobs < 1 || n_cta < 1) return fail(XE_EINVAL, "bad plan query");
-    std::vector<JobShape> shapes;
-    for (int q = 0; q < n_jobs; ++q) {
-        if (N[q] < 1 || T[q] < 1 || n_chan[q] < 1) return fail(XE_EINVAL, "bad job %d", q);
-        shapes.push_back(JobShape{N[q], T[q], n_chan[q]});
-    }
     HostPlan p;
-    build_tiles(shapes, g_opt.operand_bytes, n_cta, p);
+    int rc = plan_from_args(N, T, n_chan, n_jobs, n_cta, -1, 0, p);
+    if (rc) return rc;
+    int64_t split = 0;
+    for (const Tile &t : p.tiles) split += t.n_parts > 0 ? 1 : 0;
     if (n_tiles) *n_tiles = int64_t(p.tiles.size());
     if (n_iters) *n_iters = p.total_iters;
-    if (n_split_tiles) *n_split_tiles = p.n_split;
+    if (n_split_tiles) *n_split_tiles = split;
     return XE_OK;
+}
+
+int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
+                     int sched, int tile_n, int32_t *out, int64_t cap) {
+    HostPlan p;
+    int rc = plan_from_args(N, T, n_chan, n_jobs, n_cta, sched, tile_n, p);
+    if (rc) return rc;
+    const int64_t need = 4 + 6 * int64_t(p.tiles.size()) + 5 * int64_t(p.segs.size());
+    if (!out || cap < need) return need;
+    int64_t k = 0;
+    out[k++] = int32_t(p.tiles.size());
+    out[k++] = int32_t(p.segs.size());
+    out[k++] = p.n_cta;
+    out[k++] = p.n_partial;
+    for (const Tile &t : p.tiles) {
+        out[k++] = t.job;
+        out[k++] = t.chan;
+        out[k++] = t.i0;
+        out[k++] = t.j0;
+        out[k++] = t.nj;
+        out[k++] = t.kblocks;
+    }
+    for (int b = 0; b < p.n_cta; ++b)
+        for (int q = p.seg_off[size_t(b)]; q < p.seg_off[size_t(b) + 1]; ++q) {
+            const Seg &s = p.segs[size_t(q)];
+            out[k++] = b;
+            out[k++] = s.tile;
+            out[k++] = s.k_lo;
+            out[k++] = s.k_hi;
+            out[k++] = s.slot;
+        }
+    return need;
 }
 
 // Read and clear the device status word of the scratch bound to `stream` (synchronises it).
@@ -527,7 +934,7 @@ int xe_device_status(void *stream) {
     if (st != 0) {
         XE_CUDA(cudaMemset(it->second->status, 0, sizeof(int)));
         if (it->second->counters)
-            XE_CUDA(cudaMemset(it->second->counters, 0, it->second->n_counters * sizeof(int)));
+            XE_CUDA(cudaMemset(it->second->counters, 0, it->second->counters_bytes));
         return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
     }
     return XE_OK;

@@ -150,6 +150,8 @@ int64_t imma_blocks(int N, int C) {
     return int64_t(C) * nb * (nb + 1) / 2;
 }
 
+const void *imma_kernel_fn() { return reinterpret_cast<const void *>(imma_kernel); }
+
 cudaError_t launch_imma(const JobTable &jt, cudaStream_t s) {
     if (jt.total_stage_blocks <= 0) return cudaSuccess;
     if (jt.total_stage_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;

@@ -60,20 +60,41 @@ struct Tile {
     int chan;
     int i0;
     int j0;
-    int nj;                   // 256, or 128 on half tiles next to the diagonal
+    int nj;                   // 256 or 128
     int kblocks;              // k-iterations (pipeline stages) of this tile
-    int64_t iter_begin;       // prefix sum of kblocks over the tile list
+    int n_parts;              // segments that each cover part of the tile (0: one whole segment)
+    int part_off;             // their workspace slots: tile_slots[part_off .. part_off + n_parts)
 };
 
-// Device-resident plan of one persistent launch.
+// A contiguous k-range of one tile processed by one CTA.
+struct Seg {
+    int tile;
+    int k_lo;
+    int k_hi;
+    int slot;                 // workspace slot if the segment is partial, else -1
+};
+
+// Device-resident plan of one persistent launch: CTA b processes segs[seg_off[b] ..
+// seg_off[b+1]) in order.
 struct PlanDev {
     const Tile *tiles;
+    const Seg *segs;
+    const int *seg_off;
+    const int *tile_slots;
     int n_tiles;
     int n_cta;
-    int64_t total_iters;
-    int32_t *ws;              // partial-tile workspace: 2 slots per CTA
+    int32_t *ws;              // partial-tile workspace, one slot per partial segment
     int *counters;            // one arrival counter per tile, zero between launches
     int *status;              // device status word (0 = ok)
+};
+
+// Triangle schedules (host-side choice; the kernel just follows the segment lists).
+enum Sched : int {
+    kSchedStreamK = 0,        // equal contiguous ranges of the concatenated k-iterations
+    kSchedSplit = 1,          // each tile split into s equal k-parts, parts dealt round-robin
+    kSchedHybrid = 2,         // whole tiles in full waves, the last partial wave stream-K
+    kSchedLPT = 3,            // whole tiles, longest first, to the least-loaded CTA
+    kNumSched = 4,
 };
 
 constexpr int64_t kWsSlotElems = 2LL * kBN * kBM;  // re and im planes, [col][row] int32
@@ -91,6 +112,10 @@ cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, c
 cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
+const void *stage_kernel_fn(int elem_bytes);
+const void *tc_kernel_fn(int elem_bytes);
+const void *imma_kernel_fn();
+cudaError_t tc_prepare();
 
 // Enqueue jobs on stream s in accumulate mode (vis += V), tensor-core path; takes the
 // runtime lock.  Used by the streaming server.  Returns an XE_* code.

@@ -30,10 +30,14 @@ namespace xe {
 
 static __device__ __align__(256) uint8_t g_noalloc_scratch[XE_NOALLOC_SCRATCH_BYTES];
 
-// Layout of the array: [status | pad][tile table][planes].
+// Layout of the array: [status | pad][tiles][segments][segment offsets][planes].
 constexpr size_t kNaStatusBytes = 256;
 constexpr size_t kNaTileBytes = size_t(XE_NOALLOC_MAX_TILES) * sizeof(Tile);
-constexpr size_t kNaPlaneOffset = (kNaStatusBytes + kNaTileBytes + 1023) / 1024 * 1024;
+constexpr size_t kNaSegOffset = kNaStatusBytes + kNaTileBytes;
+constexpr size_t kNaSegBytes = size_t(XE_NOALLOC_MAX_TILES) * sizeof(Seg);
+constexpr size_t kNaOffOffset = kNaSegOffset + kNaSegBytes;
+constexpr size_t kNaOffBytes = size_t(XE_NOALLOC_MAX_TILES + 1) * sizeof(int);
+constexpr size_t kNaPlaneOffset = (kNaOffOffset + kNaOffBytes + 1023) / 1024 * 1024;
 constexpr size_t kNaPlaneBytes = size_t(XE_NOALLOC_SCRATCH_BYTES) - kNaPlaneOffset;
 static_assert(kNaPlaneOffset < size_t(XE_NOALLOC_SCRATCH_BYTES), "scratch layout");
 
@@ -44,26 +48,31 @@ static int na_fail(int code, const char *msg) { return record_error(code, msg); 
 
 // Enumerate the triangle tiles of one job (same cover and order as the allocating path:
 // row blocks of 128, 256-wide column tiles aligned to 256, a 128-wide half tile where a row
-// block starts mid-way through a column block) straight into the scratch tile table.
-// One thread: at most XE_NOALLOC_MAX_TILES entries.
-__global__ void na_tiles_kernel(Tile *tiles, int N, int C, int kb, int *status) {
+// block starts mid-way through a column block) straight into the scratch tile table, with
+// one whole-tile segment per CTA.  One thread: at most XE_NOALLOC_MAX_TILES entries.
+__global__ void na_tiles_kernel(Tile *tiles, Seg *segs, int *seg_off, int N, int C, int kb,
+                                int *status) {
     if (threadIdx.x != 0 || blockIdx.x != 0) return;
     *status = 0;
-    int64_t it = 0;
     int k = 0;
     for (int c = 0; c < C; ++c)
         for (int i0 = 0; i0 < N; i0 += kBM) {
             int j0 = i0;
             if (j0 % kBN != 0) {
-                tiles[k++] = Tile{0, c, i0, j0, kBM, kb, it};
-                it += kb;
+                tiles[k] = Tile{0, c, i0, j0, kBM, kb, 0, 0};
+                segs[k] = Seg{k, 0, kb, -1};
+                seg_off[k] = k;
+                ++k;
                 j0 += kBM;
             }
             for (; j0 < N; j0 += kBN) {
-                tiles[k++] = Tile{0, c, i0, j0, kBN, kb, it};
-                it += kb;
+                tiles[k] = Tile{0, c, i0, j0, kBN, kb, 0, 0};
+                segs[k] = Seg{k, 0, kb, -1};
+                seg_off[k] = k;
+                ++k;
             }
         }
+    seg_off[k] = k;
 }
 
 static int64_t na_tile_count(int N, int C) {
@@ -129,6 +138,8 @@ int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_
     cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     int *status = reinterpret_cast<int *>(base);
     Tile *tiles = reinterpret_cast<Tile *>(base + kNaStatusBytes);
+    Seg *segs = reinterpret_cast<Seg *>(base + kNaSegOffset);
+    int *seg_off = reinterpret_cast<int *>(base + kNaOffOffset);
     uint8_t *planes = base + kNaPlaneOffset;
 
     JobTable jt{};
@@ -154,14 +165,16 @@ int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_
     // split-tile workspace and arrival counters of the allocating path are never touched.
     PlanDev pd{};
     pd.tiles = tiles;
+    pd.segs = segs;
+    pd.seg_off = seg_off;
+    pd.tile_slots = seg_off;      // never read: no tile has partial segments
     pd.n_tiles = int(n_tiles);
     pd.n_cta = int(n_tiles);
-    pd.total_iters = n_tiles * kb;
     pd.ws = nullptr;
     pd.counters = nullptr;
     pd.status = status;
 
-    na_tiles_kernel<<<1, 32, 0, s>>>(tiles, N, n_chan, int(kb), status);
+    na_tiles_kernel<<<1, 32, 0, s>>>(tiles, segs, seg_off, N, n_chan, int(kb), status);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return na_fail(XE_ECUDA, cudaGetErrorString(e));
     e = launch_stage(jt, eb, s);

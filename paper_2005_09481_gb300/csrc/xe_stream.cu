@@ -3,15 +3,16 @@
 // The CHIME X-engine integrates visibilities on the GPU and exports them at a fixed cadence
 // (Denman et al. 2020, sections 2.1 and 3.2: per-block GPU processing, time integration,
 // export of correlated visibilities, Table tab:data-flow).  Here each admitted channel owns
-// a device-resident int32 accumulator and a ring of device frame slots.  Producers push
-// frames (host or device memory); one scheduler thread gathers, every pass, the next
-// in-order ready frame of every channel and correlates all of them in batched persistent
-// launches that ADD into the accumulators (continuous batching: frames that arrive while a
-// batch runs join the next one).  When a channel's integration is complete its accumulator
-// is copied to a pinned host buffer and cleared, and the result is handed to xe_stream_poll
-// with its arrival and ready times (frame-to-visibility latency).
+// two device-resident int32 accumulators (one filling, one being exported) and a ring of
+// device frame slots.  Producers push frames (host or device memory).  One scheduler thread
+// gathers, every pass, the next in-order ready frame of every channel and correlates all of
+// them in batched persistent launches that ADD into the accumulators (continuous batching:
+// frames that arrive while a batch runs join the next one).  When a channel's integration is
+// complete, the channel switches to its other accumulator and the finished one is copied to
+// a pinned host buffer on a separate copy stream (overlapping the next batches), cleared,
+// and handed to xe_stream_poll with its arrival and ready times (frame-to-visibility latency).
 //
-// Admission is by HBM budget: a channel is admitted only if its accumulator, frame ring and
+// Admission is by HBM budget: a channel is admitted only if its accumulators, frame ring and
 // share of staging memory fit the stream's budget.  Lost frames (sequence gaps) are counted
 // and mark their integration incomplete; nothing shifts integration boundaries.
 #include <atomic>
@@ -45,7 +46,7 @@ enum SlotState { kFree = 0, kCopying = 1, kReady = 2, kQueued = 3 };
 struct Slot {
     uint8_t *dev = nullptr;
     cudaEvent_t copy_ev = nullptr;   // the frame's bytes have landed in the slot
-    cudaEvent_t ev = nullptr;        // the launch that read the slot has finished
+    int pass_ev = -1;                // index of the event of the pass that read the slot
     int state = kFree;
 };
 
@@ -57,9 +58,13 @@ struct Entry {          // one frame of a channel, in sequence order
 
 struct Chan {
     bool admitted = false;
-    int32_t *acc = nullptr;
+    int32_t *acc[2] = {nullptr, nullptr};
+    cudaEvent_t acc_free_ev[2] = {nullptr, nullptr};  // export of that accumulator done
+    bool acc_wait[2] = {false, false};                // compute must wait on acc_free_ev
+    int cur = 0;                                      // accumulator being filled
     std::vector<Slot> ring;
     std::deque<Entry> fifo;
+    int n_copying = 0;
     int64_t expected_push = 0;     // next sequence number a push may carry
     int64_t integ_index = 0;
     int64_t frames_in_integ = 0;
@@ -72,12 +77,17 @@ struct Chan {
 struct ResultBuf {
     int32_t *host = nullptr;
     int chan = -1;
-    bool busy = false;             // between D2H enqueue and xe_stream_release
+    bool busy = false;             // between export and xe_stream_release
 };
 
 struct Pending {
     xe_result r;
     cudaEvent_t ev;
+};
+
+struct PassEvent {
+    cudaEvent_t ev = nullptr;
+    int refs = 0;
 };
 
 }  // namespace
@@ -89,12 +99,14 @@ struct xe_stream {
     int64_t B = 0;
     size_t frame_bytes = 0, acc_bytes = 0, per_chan_bytes = 0;
     int64_t frames_per_integ = 0;
-    cudaStream_t copy_s = nullptr, comp_s = nullptr;
+    cudaStream_t copy_s = nullptr, comp_s = nullptr, d2h_s = nullptr;
     std::vector<xe::Chan> chans;
     std::vector<xe::ResultBuf> bufs;
     std::deque<xe::Pending> pending;
     std::deque<xe_result> ready;
     std::vector<cudaEvent_t> spare_events;
+    std::vector<xe::PassEvent> pass_events;
+    std::vector<int> queued_slots;   // (chan << 8 | slot) of slots read by launched passes
     std::mutex mu;
     std::condition_variable cv_work, cv_ready;
     std::thread sched;
@@ -121,58 +133,91 @@ cudaEvent_t take_event(xe_stream *s) {
     return e;
 }
 
-// Close the channel's current integration: copy its accumulator to a free result buffer
-// of the channel, clear the accumulator, and queue the result for completion.  Called with
-// s->mu held, after the launches that fed the integration were enqueued on comp_s.
-void finish_integration(xe_stream *s, int c) {
-    Chan &ch = s->chans[c];
+int take_pass_event(xe_stream *s) {
+    for (int k = 0; k < int(s->pass_events.size()); ++k)
+        if (s->pass_events[size_t(k)].refs == 0) return k;
+    PassEvent pe;
+    cudaEventCreateWithFlags(&pe.ev, cudaEventDisableTiming);
+    s->pass_events.push_back(pe);
+    return int(s->pass_events.size()) - 1;
+}
+
+bool has_free_buf(xe_stream *s, int c) {
+    for (int k : s->chans[size_t(c)].bufs)
+        if (!s->bufs[size_t(k)].busy) return true;
+    return false;
+}
+
+struct Export {
+    int chan;
+    int acc_idx;
+    int buf;
+    xe_result r;
+};
+
+// Close channel c's integration (s->mu held): pick a result buffer, switch the channel to its
+// other accumulator, and describe the export to enqueue after the pass's launches.
+Export close_integration(xe_stream *s, int c) {
+    Chan &ch = s->chans[size_t(c)];
     int b = -1;
     for (int k : ch.bufs)
-        if (!s->bufs[k].busy) { b = k; break; }
-    // A buffer is always free here: the scheduler only completes an integration when one is.
-    ResultBuf &rb = s->bufs[b];
-    rb.busy = true;
-    cudaMemcpyAsync(rb.host, ch.acc, s->acc_bytes, cudaMemcpyDeviceToHost, s->comp_s);
-    cudaMemsetAsync(ch.acc, 0, s->acc_bytes, s->comp_s);
-    Pending p{};
-    p.r.chan = c;
-    p.r.integ_index = ch.integ_index;
-    p.r.n_samples = ch.samples_in_integ;
-    p.r.complete = (!ch.lost && ch.samples_in_integ == s->cfg.integ_T) ? 1 : 0;
-    p.r.vis = rb.host;
-    p.r.t_first_arrival_ns = ch.t_first;
-    p.r.t_last_arrival_ns = ch.t_last;
-    p.r.handle = b;
-    p.ev = take_event(s);
-    cudaEventRecord(p.ev, s->comp_s);
-    s->pending.push_back(p);
+        if (!s->bufs[size_t(k)].busy) { b = k; break; }
+    s->bufs[size_t(b)].busy = true;   // a free buffer is guaranteed by the caller
+    Export ex{};
+    ex.chan = c;
+    ex.acc_idx = ch.cur;
+    ex.buf = b;
+    ex.r.chan = c;
+    ex.r.integ_index = ch.integ_index;
+    ex.r.n_samples = ch.samples_in_integ;
+    ex.r.complete = (!ch.lost && ch.samples_in_integ == s->cfg.integ_T) ? 1 : 0;
+    ex.r.vis = s->bufs[size_t(b)].host;
+    ex.r.t_first_arrival_ns = ch.t_first;
+    ex.r.t_last_arrival_ns = ch.t_last;
+    ex.r.handle = b;
+    ch.cur ^= 1;
+    ch.acc_wait[ch.cur] = true;
     ch.integ_index += 1;
     ch.frames_in_integ = 0;
     ch.samples_in_integ = 0;
     ch.lost = false;
     ch.t_first = ch.t_last = 0;
-}
-
-bool has_free_buf(xe_stream *s, int c) {
-    for (int k : s->chans[c].bufs)
-        if (!s->bufs[k].busy) return true;
-    return false;
+    return ex;
 }
 
 // One scheduler pass.  Returns true if it did any work.
 bool pass(xe_stream *s) {
     std::vector<xe_job> jobs;
-    std::vector<std::pair<int, int>> used;   // (channel, slot) consumed by this pass
-    std::vector<int> finishing;
+    std::vector<int> used;             // (chan << 8 | slot) read by this pass
+    std::vector<cudaEvent_t> waits;    // accumulator exports the launches must follow
+    std::vector<Export> exports;
     bool work = false;
     {
         std::unique_lock<std::mutex> lk(s->mu);
+        // Frames whose copies landed; slots whose readers finished.
         for (size_t c = 0; c < s->chans.size(); ++c) {
             Chan &ch = s->chans[c];
-            if (!ch.admitted) continue;
-            for (Slot &sl : ch.ring) {
-                if (sl.state == kCopying && cudaEventQuery(sl.copy_ev) == cudaSuccess) sl.state = kReady;
-                else if (sl.state == kQueued && cudaEventQuery(sl.ev) == cudaSuccess) sl.state = kFree;
+            if (!ch.admitted || ch.n_copying == 0) continue;
+            for (Slot &sl : ch.ring)
+                if (sl.state == kCopying && cudaEventQuery(sl.copy_ev) == cudaSuccess) {
+                    sl.state = kReady;
+                    --ch.n_copying;
+                }
+        }
+        for (size_t k = 0; k < s->queued_slots.size();) {
+            const int code = s->queued_slots[k];
+            Chan &ch = s->chans[size_t(code >> 8)];
+            Slot &sl = ch.ring[size_t(code & 255)];
+            PassEvent &pe = s->pass_events[size_t(sl.pass_ev)];
+            if (cudaEventQuery(pe.ev) == cudaSuccess) {
+                sl.state = kFree;
+                pe.refs -= 1;
+                sl.pass_ev = -1;
+                s->queued_slots[k] = s->queued_slots.back();
+                s->queued_slots.pop_back();
+                work = true;
+            } else {
+                ++k;
             }
         }
         while (!s->pending.empty() && cudaEventQuery(s->pending.front().ev) == cudaSuccess) {
@@ -200,35 +245,68 @@ bool pass(xe_stream *s) {
                     ch.t_last = e.t_arrival;
                     ch.lost = true;
                     ch.frames_in_integ += 1;
-                    if (closes) finishing.push_back(int(c));
-                    if (closes) break;
+                    if (closes) {
+                        exports.push_back(close_integration(s, int(c)));
+                        break;
+                    }
                     continue;
                 }
-                Slot &sl = ch.ring[e.slot];
+                Slot &sl = ch.ring[size_t(e.slot)];
                 if (sl.state != kReady) break;
                 ch.fifo.pop_front();
                 sl.state = kQueued;
-                jobs.push_back(xe_job{sl.dev, ch.acc, s->cfg.N, 1, s->cfg.frame_T});
-                used.emplace_back(int(c), e.slot);
+                if (ch.acc_wait[ch.cur]) {
+                    waits.push_back(ch.acc_free_ev[ch.cur]);
+                    ch.acc_wait[ch.cur] = false;
+                }
+                jobs.push_back(xe_job{sl.dev, ch.acc[ch.cur], s->cfg.N, 1, s->cfg.frame_T});
+                used.push_back(int(c) << 8 | e.slot);
                 if (ch.frames_in_integ == 0) ch.t_first = e.t_arrival;
                 ch.t_last = e.t_arrival;
                 ch.frames_in_integ += 1;
                 ch.samples_in_integ += s->cfg.frame_T;
-                if (closes) finishing.push_back(int(c));
+                if (closes) exports.push_back(close_integration(s, int(c)));
                 break;
             }
         }
-        if (!jobs.empty()) {
-            int rc = run_jobs_accumulate(jobs.data(), int(jobs.size()), s->comp_s);
-            if (rc != XE_OK) s->last_error = rc;
-            for (auto &u : used) cudaEventRecord(s->chans[u.first].ring[u.second].ev, s->comp_s);
-            s->n_frames += int64_t(jobs.size());
-            work = true;
-        }
-        for (int c : finishing) finish_integration(s, c);
-        if (!finishing.empty()) work = true;
     }
-    return work;
+    if (jobs.empty() && exports.empty()) return work;
+
+    // Launch outside the lock; pushes and polls proceed meanwhile.
+    for (cudaEvent_t e : waits) cudaStreamWaitEvent(s->comp_s, e, 0);
+    int rc = XE_OK;
+    if (!jobs.empty()) rc = run_jobs_accumulate(jobs.data(), int(jobs.size()), s->comp_s);
+    cudaEvent_t done = nullptr;
+    std::vector<Pending> pend;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (rc != XE_OK) s->last_error = rc;
+        const int pe = take_pass_event(s);
+        done = s->pass_events[size_t(pe)].ev;
+        cudaEventRecord(done, s->comp_s);
+        for (int code : used) {
+            Slot &sl = s->chans[size_t(code >> 8)].ring[size_t(code & 255)];
+            sl.pass_ev = pe;
+            s->pass_events[size_t(pe)].refs += 1;
+            s->queued_slots.push_back(code);
+        }
+        s->n_frames += int64_t(jobs.size());
+        // Exports run on their own stream after this pass's launches.
+        if (!exports.empty()) cudaStreamWaitEvent(s->d2h_s, done, 0);
+        for (const Export &ex : exports) {
+            Chan &ch = s->chans[size_t(ex.chan)];
+            int32_t *acc = ch.acc[ex.acc_idx];
+            cudaMemcpyAsync(s->bufs[size_t(ex.buf)].host, acc, s->acc_bytes, cudaMemcpyDeviceToHost, s->d2h_s);
+            Pending p{};
+            p.r = ex.r;
+            p.ev = take_event(s);
+            cudaEventRecord(p.ev, s->d2h_s);
+            cudaMemsetAsync(acc, 0, s->acc_bytes, s->d2h_s);
+            cudaEventRecord(ch.acc_free_ev[ex.acc_idx], s->d2h_s);
+            s->pending.push_back(p);
+        }
+    }
+    return true;
 }
 
 void scheduler_main(xe_stream *s) {
@@ -242,6 +320,37 @@ void scheduler_main(xe_stream *s) {
 }
 
 int sfail(int code, const char *msg) { return record_error(code, msg); }
+
+// Queue one frame (s->mu held).  Returns XE_OK, XE_EAGAIN (ring full) or an error.
+int push_locked(xe_stream *s, int chan, const uint8_t *frame, int64_t seq, int64_t t,
+                cudaEvent_t *copy_ev) {
+    if (chan < 0 || chan >= int(s->chans.size()) || !s->chans[size_t(chan)].admitted)
+        return sfail(XE_EINVAL, "channel not admitted");
+    if (!frame) return sfail(XE_EINVAL, "null frame");
+    Chan &ch = s->chans[size_t(chan)];
+    if (seq < ch.expected_push) return sfail(XE_EINVAL, "frame is older than the open integration or a duplicate");
+    if (seq - ch.expected_push > 1000000) return sfail(XE_EINVAL, "sequence gap too large");
+    int slot = -1;
+    for (int k = 0; k < int(ch.ring.size()); ++k)
+        if (ch.ring[size_t(k)].state == kFree) { slot = k; break; }
+    if (slot < 0) return XE_EAGAIN;
+    for (int64_t q = ch.expected_push; q < seq; ++q) {     // frames that never came
+        ch.fifo.push_back(Entry{q, -1, t});
+        s->n_dropped += 1;
+    }
+    Slot &sl = ch.ring[size_t(slot)];
+    cudaError_t e = cudaMemcpyAsync(sl.dev, frame, s->frame_bytes,
+                                    s->cfg.device_source ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                                    s->copy_s);
+    if (e != cudaSuccess) return sfail(XE_ECUDA, cudaGetErrorString(e));
+    cudaEventRecord(sl.copy_ev, s->copy_s);
+    sl.state = kCopying;
+    ch.n_copying += 1;
+    ch.fifo.push_back(Entry{seq, slot, t});
+    ch.expected_push = seq + 1;
+    if (copy_ev) *copy_ev = sl.copy_ev;
+    return XE_OK;
+}
 
 }  // namespace
 }  // namespace xe
@@ -272,14 +381,15 @@ int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
     s->frames_per_integ = c.integ_T / c.frame_T;
     const size_t n_pad = size_t((c.N + kNPad - 1) / kNPad * kNPad);
     const size_t stage_bytes = 2 * n_pad * size_t((c.frame_T + 63) / 64 * 64);
-    s->per_chan_bytes = s->acc_bytes + size_t(c.ring_frames) * s->frame_bytes + stage_bytes;
+    s->per_chan_bytes = 2 * s->acc_bytes + size_t(c.ring_frames) * s->frame_bytes + stage_bytes;
     if (c.hbm_budget < int64_t(s->per_chan_bytes)) {
         delete s;
         return sfail(XE_EBUDGET, "the HBM budget does not fit one channel slot");
     }
     s->chans.resize(size_t(c.max_chan));
     if (cudaStreamCreateWithFlags(&s->copy_s, cudaStreamNonBlocking) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&s->comp_s, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaStreamCreateWithFlags(&s->comp_s, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&s->d2h_s, cudaStreamNonBlocking) != cudaSuccess) {
         delete s;
         return sfail(XE_ECUDA, "stream creation failed");
     }
@@ -297,33 +407,42 @@ int xe_stream_admit(xe_stream *s, int chan) {
     if (ch.admitted) return XE_OK;
     if (s->used_bytes + int64_t(s->per_chan_bytes) > s->cfg.hbm_budget)
         return sfail(XE_EBUDGET, "HBM budget full");
+    if (int(s->cfg.ring_frames) > 255) return sfail(XE_EINVAL, "ring too large");
     cudaSetDevice(s->dev);
-    if (cudaMalloc(&ch.acc, s->acc_bytes) != cudaSuccess) {
-        cudaGetLastError();
-        return sfail(XE_ENOMEM, "accumulator allocation failed");
+    for (int a = 0; a < 2; ++a) {
+        if (cudaMalloc(&ch.acc[a], s->acc_bytes) != cudaSuccess) {
+            cudaGetLastError();
+            return sfail(XE_ENOMEM, "accumulator allocation failed");
+        }
+        cudaMemset(ch.acc[a], 0, s->acc_bytes);
+        cudaEventCreateWithFlags(&ch.acc_free_ev[a], cudaEventDisableTiming);
+        ch.acc_wait[a] = false;
     }
-    cudaMemset(ch.acc, 0, s->acc_bytes);
+    ch.cur = 0;
     ch.ring.assign(size_t(s->cfg.ring_frames), Slot{});
     for (Slot &sl : ch.ring) {
         if (cudaMalloc(&sl.dev, s->frame_bytes) != cudaSuccess) {
             cudaGetLastError();
             return sfail(XE_ENOMEM, "frame ring allocation failed");
         }
-        cudaEventCreateWithFlags(&sl.ev, cudaEventDisableTiming);
         cudaEventCreateWithFlags(&sl.copy_ev, cudaEventDisableTiming);
     }
-    for (int k = 0; k < kBufsPerChan; ++k) {
-        ResultBuf rb;
-        if (cudaHostAlloc(reinterpret_cast<void **>(&rb.host), s->acc_bytes, cudaHostAllocDefault) !=
-            cudaSuccess) {
-            cudaGetLastError();
-            return sfail(XE_ENOMEM, "pinned result buffer allocation failed");
+    if (ch.bufs.empty()) {
+        for (int k = 0; k < kBufsPerChan; ++k) {
+            ResultBuf rb;
+            if (cudaHostAlloc(reinterpret_cast<void **>(&rb.host), s->acc_bytes, cudaHostAllocDefault) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                return sfail(XE_ENOMEM, "pinned result buffer allocation failed");
+            }
+            rb.chan = chan;
+            ch.bufs.push_back(int(s->bufs.size()));
+            s->bufs.push_back(rb);
         }
-        rb.chan = chan;
-        ch.bufs.push_back(int(s->bufs.size()));
-        s->bufs.push_back(rb);
     }
+    cudaDeviceSynchronize();
     ch.fifo.clear();
+    ch.n_copying = 0;
     ch.expected_push = 0;
     ch.integ_index = ch.frames_in_integ = ch.samples_in_integ = 0;
     ch.lost = false;
@@ -341,16 +460,29 @@ int xe_stream_evict(xe_stream *s, int chan) {
     Chan &ch = s->chans[size_t(chan)];
     cudaStreamSynchronize(s->copy_s);
     cudaStreamSynchronize(s->comp_s);
-    // Results of this channel still queued keep their buffers until released.
+    cudaStreamSynchronize(s->d2h_s);
+    for (size_t k = 0; k < s->queued_slots.size();) {
+        if ((s->queued_slots[k] >> 8) == chan) {
+            Slot &sl = ch.ring[size_t(s->queued_slots[k] & 255)];
+            s->pass_events[size_t(sl.pass_ev)].refs -= 1;
+            s->queued_slots[k] = s->queued_slots.back();
+            s->queued_slots.pop_back();
+        } else {
+            ++k;
+        }
+    }
     for (Slot &sl : ch.ring) {
         cudaFree(sl.dev);
-        cudaEventDestroy(sl.ev);
         cudaEventDestroy(sl.copy_ev);
     }
     ch.ring.clear();
     ch.fifo.clear();
-    cudaFree(ch.acc);
-    ch.acc = nullptr;
+    for (int a = 0; a < 2; ++a) {
+        cudaFree(ch.acc[a]);
+        cudaEventDestroy(ch.acc_free_ev[a]);
+        ch.acc[a] = nullptr;
+        ch.acc_free_ev[a] = nullptr;
+    }
     ch.admitted = false;
     s->used_bytes -= int64_t(s->per_chan_bytes);
     s->n_admitted -= 1;
@@ -358,41 +490,42 @@ int xe_stream_evict(xe_stream *s, int chan) {
 }
 
 int xe_stream_push(xe_stream *s, int chan, const uint8_t *frame, int64_t seq, int64_t t_arrival_ns) {
-    if (!s || !frame) return sfail(XE_EINVAL, "null stream or frame");
+    if (!s) return sfail(XE_EINVAL, "null stream");
     cudaEvent_t wait_ev = nullptr;
     {
         std::lock_guard<std::mutex> lk(s->mu);
         if (s->closed) return sfail(XE_ECLOSED, "stream closed");
-        if (chan < 0 || chan >= int(s->chans.size()) || !s->chans[size_t(chan)].admitted)
-            return sfail(XE_EINVAL, "channel not admitted");
-        Chan &ch = s->chans[size_t(chan)];
-        if (seq < ch.expected_push) return sfail(XE_EINVAL, "frame is older than the open integration or a duplicate");
-        if (seq - ch.expected_push > 1000000) return sfail(XE_EINVAL, "sequence gap too large");
-        int slot = -1;
-        for (int k = 0; k < int(ch.ring.size()); ++k)
-            if (ch.ring[size_t(k)].state == kFree) { slot = k; break; }
-        if (slot < 0) return XE_EAGAIN;
-        const int64_t t = t_arrival_ns > 0 ? t_arrival_ns : now_ns();
-        for (int64_t q = ch.expected_push; q < seq; ++q) {     // frames that never came
-            ch.fifo.push_back(Entry{q, -1, t});
-            s->n_dropped += 1;
-        }
-        Slot &sl = ch.ring[size_t(slot)];
-        cudaError_t e = cudaMemcpyAsync(sl.dev, frame, s->frame_bytes,
-                                        s->cfg.device_source ? cudaMemcpyDeviceToDevice
-                                                             : cudaMemcpyHostToDevice,
-                                        s->copy_s);
-        if (e != cudaSuccess) return sfail(XE_ECUDA, cudaGetErrorString(e));
-        cudaEventRecord(sl.copy_ev, s->copy_s);
-        sl.state = kCopying;
-        ch.fifo.push_back(Entry{seq, slot, t});
-        ch.expected_push = seq + 1;
-        if (!s->cfg.device_source) wait_ev = sl.copy_ev;
+        const int rc = push_locked(s, chan, frame, seq, t_arrival_ns > 0 ? t_arrival_ns : now_ns(), &wait_ev);
+        if (rc != XE_OK) return rc;
     }
     // Host source: the caller's bytes are on the device before the call returns.
-    if (wait_ev) cudaEventSynchronize(wait_ev);
+    if (!s->cfg.device_source) cudaEventSynchronize(wait_ev);
     s->cv_work.notify_one();
     return XE_OK;
+}
+
+int xe_stream_push_frames(xe_stream *s, int n, const int *chans, const uint8_t *const *frames,
+                          const int64_t *seqs, int64_t t_arrival_ns, int *rc_out) {
+    if (!s || n < 0 || (n > 0 && (!chans || !frames || !seqs))) return sfail(XE_EINVAL, "bad frame batch");
+    cudaEvent_t last = nullptr;
+    int n_ok = 0;
+    {
+        std::lock_guard<std::mutex> lk(s->mu);
+        if (s->closed) return sfail(XE_ECLOSED, "stream closed");
+        const int64_t t = t_arrival_ns > 0 ? t_arrival_ns : now_ns();
+        for (int k = 0; k < n; ++k) {
+            cudaEvent_t ev = nullptr;
+            const int rc = push_locked(s, chans[k], frames[k], seqs[k], t, &ev);
+            if (rc_out) rc_out[k] = rc;
+            if (rc == XE_OK) {
+                last = ev;
+                ++n_ok;
+            }
+        }
+    }
+    if (!s->cfg.device_source && last) cudaStreamSynchronize(s->copy_s);
+    s->cv_work.notify_one();
+    return n_ok;
 }
 
 int xe_stream_flush(xe_stream *s) {
@@ -462,19 +595,24 @@ void xe_stream_close(xe_stream *s) {
     cudaSetDevice(s->dev);
     cudaStreamSynchronize(s->copy_s);
     cudaStreamSynchronize(s->comp_s);
+    cudaStreamSynchronize(s->d2h_s);
     for (Chan &ch : s->chans) {
         for (Slot &sl : ch.ring) {
             cudaFree(sl.dev);
-            cudaEventDestroy(sl.ev);
             cudaEventDestroy(sl.copy_ev);
         }
-        if (ch.acc) cudaFree(ch.acc);
+        for (int a = 0; a < 2; ++a) {
+            if (ch.acc[a]) cudaFree(ch.acc[a]);
+            if (ch.acc_free_ev[a]) cudaEventDestroy(ch.acc_free_ev[a]);
+        }
     }
     for (ResultBuf &rb : s->bufs) cudaFreeHost(rb.host);
     for (Pending &p : s->pending) cudaEventDestroy(p.ev);
     for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
+    for (PassEvent &pe : s->pass_events) cudaEventDestroy(pe.ev);
     cudaStreamDestroy(s->copy_s);
     cudaStreamDestroy(s->comp_s);
+    cudaStreamDestroy(s->d2h_s);
     delete s;
 }
 

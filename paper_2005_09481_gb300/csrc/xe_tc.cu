@@ -17,13 +17,15 @@
 //   stage_kernel  packed 4+4-bit bytes [T][N] -> per-stage operand planes [kb][re|im][n][64 B]
 //                 in the exact shared-memory image the MMA reads (64-byte swizzle), so the
 //                 correlation kernel fetches each plane tile with one bulk copy.
-//   tc_kernel     persistent, one CTA per SM, stream-K over all triangle tiles of all jobs:
+//   tc_kernel     persistent, at most one CTA per SM; each CTA follows its list of
+//                 segments (a k-range of one triangle tile of one job) from the host plan:
 //                 warp 4 streams planes into a 4-stage shared-memory ring with bulk copies,
 //                 warp 5 issues tcgen05.mma (M=128, N=256/128, K=32 bytes) into two f32
 //                 accumulators in tensor memory (Re: columns 0-255, Im: 256-511),
 //                 warps 0-3 drain them (tcgen05.ld), convert to int32 and store the packed
-//                 upper triangle.  A tile split between CTAs is summed exactly through a
-//                 workspace by the last CTA to finish it (arrival counter, no spinning).
+//                 upper triangle.  A tile split into several segments is summed exactly
+//                 through a workspace by the last segment to finish (arrival counter, no
+//                 spinning on other CTAs).
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -167,29 +169,11 @@ cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s) {
 
 // ---- persistent tensor-core correlation kernel -----------------------------------------------
 
-__device__ __forceinline__ int find_tile(const PlanDev &p, int64_t it) {
-    int lo = 0, hi = p.n_tiles - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (p.tiles[mid].iter_begin <= it) lo = mid; else hi = mid - 1;
-    }
-    return lo;
-}
-
-__device__ __forceinline__ int64_t range_start(int64_t b, int64_t W, int64_t G) {
-    return b * W / G;
-}
-
-// The CTA whose iteration range holds iteration x (all ranges are non-empty: G <= W).
-__device__ __forceinline__ int64_t cta_of(int64_t x, int64_t W, int64_t G) {
-    return ((x + 1) * G - 1) / W;
-}
-
 __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: "memory"); }
 
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
 
-// Store (or add) one row run of final visibilities: row i, columns j0+col0 .. +31.
+// Store (or add) one row run of final visibilities: row i, columns jbase .. jbase+31.
 __device__ __forceinline__ void store_run(const JobDev &jb, int chan, int i, int jbase,
                                           const int (&re)[32], const int (&im)[32], int acc) {
     if (i >= jb.N) return;
@@ -248,12 +232,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_after();
     const uint32_t tmem = *tmem_slot;
 
-    const int64_t G = plan.n_cta;
-    const int64_t W = plan.total_iters;
-    const int64_t b = blockIdx.x;
-    const int64_t r_start = range_start(b, W, G);
-    const int64_t r_end = range_start(b + 1, W, G);
-    const int t_first = find_tile(plan, r_start);
+    // This CTA's work: segments [q0, q1) of the plan, each a k-range of one tile.
+    const int q0 = plan.seg_off[blockIdx.x];
+    const int q1 = plan.seg_off[blockIdx.x + 1];
     constexpr uint32_t kFmt = 0;  // E4M3 for kind::f8f6f4, F16 for kind::f16
 
     if (warp == 4) {
@@ -263,15 +244,13 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t ph = 0;
             int64_t fills = 0;
             bool ok = true;
-            for (int t = t_first; ok && t < plan.n_tiles && plan.tiles[t].iter_begin < r_end; ++t) {
-                const Tile tl = plan.tiles[t];
+            for (int q = q0; ok && q < q1; ++q) {
+                const Seg sg = plan.segs[q];
+                const Tile tl = plan.tiles[sg.tile];
                 const JobDev &jb = jt.jobs[tl.job];
-                const int64_t lo = (r_start > tl.iter_begin ? r_start : tl.iter_begin) - tl.iter_begin;
-                const int64_t te = tl.iter_begin + tl.kblocks;
-                const int64_t hi = (r_end < te ? r_end : te) - tl.iter_begin;
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
-                for (int64_t k = lo; k < hi; ++k) {
+                for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
                         set_status(plan.status, kStatusTimeoutProducer);
                         ok = false;
@@ -295,7 +274,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 const int64_t n = fills < kStages ? fills : kStages;
                 int s = stage;
                 uint32_t p = ph;
-                for (int64_t q = 0; q < n; ++q) {
+                for (int64_t r = 0; r < n; ++r) {
                     if (--s < 0) { s = kStages - 1; p ^= 1u; }
                     const long long t0 = clock64();
                     while (!mbar_try_wait(&full[s], p) && clock64() - t0 < kWaitBudgetCycles) {}
@@ -309,11 +288,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t ph = 0, acc_ph = 0;
             bool ok = true;
             const uint32_t d_re = tmem, d_im = tmem + 256;
-            for (int t = t_first; ok && t < plan.n_tiles && plan.tiles[t].iter_begin < r_end; ++t) {
-                const Tile tl = plan.tiles[t];
-                const int64_t lo = (r_start > tl.iter_begin ? r_start : tl.iter_begin) - tl.iter_begin;
-                const int64_t te = tl.iter_begin + tl.kblocks;
-                const int64_t hi = (r_end < te ? r_end : te) - tl.iter_begin;
+            for (int q = q0; ok && q < q1; ++q) {
+                const Seg sg = plan.segs[q];
+                const Tile tl = plan.tiles[sg.tile];
                 const uint32_t idesc = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, false);
                 const uint32_t idesc_neg = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, true);
                 if (!mbar_wait(acc_empty, acc_ph ^ 1u, status)) {
@@ -323,7 +300,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 acc_ph ^= 1u;
                 tc_fence_after();
-                for (int64_t k = lo; k < hi; ++k) {
+                for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
                     if (!mbar_wait(&full[stage], ph, status)) {
                         set_status(plan.status, kStatusTimeoutMma);
                         ok = false;
@@ -338,7 +315,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         const uint64_t a_im = sdesc_k_sw64(base + kAPlane + off);
                         const uint64_t b_re = sdesc_k_sw64(base + 2 * kAPlane + off);
                         const uint64_t b_im = sdesc_k_sw64(base + 2 * kAPlane + kBPlane + off);
-                        const uint32_t acc = (k > lo || s > 0) ? 1u : 0u;
+                        const uint32_t acc = (k > sg.k_lo || s > 0) ? 1u : 0u;
                         if (EB == 1) {
                             mma_f8f6f4(d_re, a_re, b_re, idesc, acc);      // + A_I A_J^T
                             mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);       // + B_I B_J^T
@@ -368,11 +345,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         uint32_t acc_ph = 0;
         const int r = warp * 32 + lane;
         const uint32_t lane_base = uint32_t(warp * 32) << 16;
-        for (int t = t_first; t < plan.n_tiles && plan.tiles[t].iter_begin < r_end; ++t) {
-            const Tile tl = plan.tiles[t];
+        for (int q = q0; q < q1; ++q) {
+            const Seg sg = plan.segs[q];
+            const Tile tl = plan.tiles[sg.tile];
             const JobDev &jb = jt.jobs[tl.job];
-            const int64_t tb = tl.iter_begin;
-            const int64_t te = tb + tl.kblocks;
             if (threadIdx.x == 0) {
                 const bool ok = mbar_wait(acc_full, acc_ph, status);
                 if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
@@ -384,8 +360,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             tc_fence_after();
 
             const int i = tl.i0 + r;
-            const bool whole = r_start <= tb && r_end >= te;
-            if (whole) {
+            if (sg.slot < 0) {
                 for (int cc = 0; cc < tl.nj; cc += 32) {
                     uint32_t fre[32], fim[32];
                     tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
@@ -400,9 +375,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                     store_run(jb, tl.chan, i, tl.j0 + cc, re, im, jt.accumulate);
                 }
             } else {
-                // Partial tile: publish this CTA's share, the last contributor sums all.
-                const int64_t slot = 2 * b + (r_start < tb ? 1 : 0);
-                int32_t *ws = plan.ws + slot * kWsSlotElems;
+                // Partial tile: publish this segment's share; the last one to arrive sums all.
+                int32_t *ws = plan.ws + int64_t(sg.slot) * kWsSlotElems;
                 for (int cc = 0; cc < tl.nj; cc += 32) {
                     uint32_t fre[32], fim[32];
                     tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
@@ -417,26 +391,21 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 __threadfence();
                 epi_bar();
-                const int64_t b_first = cta_of(tb, W, G);
-                const int64_t b_last = cta_of(te - 1, W, G);
                 if (threadIdx.x == 0) {
-                    const int n_contrib = int(b_last - b_first + 1);
-                    const int old = atomicAdd(&plan.counters[t], 1);
-                    const bool last = old == n_contrib - 1;
-                    if (last) plan.counters[t] = 0;  // ready for the next launch
+                    const int old = atomicAdd(&plan.counters[sg.tile], 1);
+                    const bool last = old == tl.n_parts - 1;
+                    if (last) plan.counters[sg.tile] = 0;  // ready for the next launch
                     *epi_flag = last ? 2 : 1;
                 }
                 epi_bar();
                 if (*epi_flag == 2) {
                     __threadfence();
-                    const bool first_split = range_start(b_first, W, G) < tb;
                     for (int cc = 0; cc < tl.nj; cc += 32) {
                         int re[32], im[32];
 #pragma unroll
                         for (int k = 0; k < 32; ++k) { re[k] = 0; im[k] = 0; }
-                        for (int64_t bb = b_first; bb <= b_last; ++bb) {
-                            const int64_t sl = 2 * bb + ((bb == b_first && first_split) ? 1 : 0);
-                            const int32_t *w = plan.ws + sl * kWsSlotElems;
+                        for (int p = 0; p < tl.n_parts; ++p) {
+                            const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + p]) * kWsSlotElems;
 #pragma unroll
                             for (int k = 0; k < 32; ++k) {
                                 re[k] += __ldcg(w + int64_t(cc + k) * kBM + r);
@@ -462,25 +431,37 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
 int tc_smem_bytes() { return kTcSmem; }
 
+const void *stage_kernel_fn(int elem_bytes) {
+    return elem_bytes == 1 ? reinterpret_cast<const void *>(stage_kernel<1>)
+                           : reinterpret_cast<const void *>(stage_kernel<2>);
+}
+
+const void *tc_kernel_fn(int elem_bytes) {
+    return elem_bytes == 1 ? reinterpret_cast<const void *>(tc_kernel<1>)
+                           : reinterpret_cast<const void *>(tc_kernel<2>);
+}
+
+// Opt the correlation kernels into their dynamic shared memory (once per process/device).
+cudaError_t tc_prepare() {
+    static int done_dev[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done_dev[dev] = 1;
+    return cudaSuccess;
+}
+
 cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s) {
-    if (plan.n_cta <= 0 || plan.total_iters <= 0) return cudaSuccess;
-    static bool attr_set[3] = {false, false, false};
-    cudaError_t e = cudaSuccess;
-    if (elem_bytes == 1) {
-        if (!attr_set[1]) {
-            e = cudaFuncSetAttribute(tc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-            if (e != cudaSuccess) return e;
-            attr_set[1] = true;
-        }
-        tc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
-    } else {
-        if (!attr_set[2]) {
-            e = cudaFuncSetAttribute(tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-            if (e != cudaSuccess) return e;
-            attr_set[2] = true;
-        }
-        tc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
-    }
+    if (plan.n_cta <= 0 || plan.n_tiles <= 0) return cudaSuccess;
+    cudaError_t e = tc_prepare();
+    if (e != cudaSuccess) return e;
+    if (elem_bytes == 1) tc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+    else tc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
     return cudaGetLastError();
 }
 

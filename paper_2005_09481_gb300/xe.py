@@ -62,10 +62,13 @@ def load():
             "xe_last_timing": ([p, p], i32),
             "xe_device_status": ([p], i32),
             "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
+            "xe_plan_dump": ([p, p, p, i32, i32, i32, i32, p, i64], i64),
+            "xe_last_config": ([p, p, p], i32),
             "xe_stream_open": ([p, p], i32),
             "xe_stream_admit": ([p, i32], i32),
             "xe_stream_evict": ([p, i32], i32),
             "xe_stream_push": ([p, i32, p, i64, i64], i32),
+            "xe_stream_push_frames": ([p, i32, p, p, p, i64, p], i32),
             "xe_stream_flush": ([p], i32),
             "xe_stream_poll": ([p, p, i32], i32),
             "xe_stream_release": ([p, i64], i32),
@@ -132,6 +135,37 @@ def plan_stats(shapes, n_cta: int):
     a, b, c = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int64()
     _check(load().xe_plan_stats(Ns, Ts, Cs, n, n_cta, ctypes.byref(a), ctypes.byref(b),
                                 ctypes.byref(c)), "xe_plan_stats")
+    return a.value, b.value, c.value
+
+
+SCHEDULES = {"stream_k": 0, "split": 1, "hybrid": 2, "lpt": 3}
+
+
+def plan_dump(shapes, n_cta: int, sched: int = -1, tile_n: int = 0):
+    """Host-side plan for shapes [(N, T, C), ...]: dict with 'tiles' (job, chan, i0, j0, nj,
+    kblocks) rows, 'segs' (cta, tile, k_lo, k_hi, slot) rows, 'n_cta', 'n_partial'."""
+    import numpy as np
+    n = len(shapes)
+    Ns = (ctypes.c_int * n)(*[s[0] for s in shapes])
+    Ts = (ctypes.c_int64 * n)(*[s[1] for s in shapes])
+    Cs = (ctypes.c_int * n)(*[s[2] for s in shapes])
+    L = load()
+    need = L.xe_plan_dump(Ns, Ts, Cs, n, n_cta, sched, tile_n, None, 0)
+    if need < 0:
+        _check(int(need), "xe_plan_dump")
+    buf = np.zeros(need, np.int32)
+    got = L.xe_plan_dump(Ns, Ts, Cs, n, n_cta, sched, tile_n, buf.ctypes.data, need)
+    _check(0 if got == need else int(got), "xe_plan_dump")
+    nt, ns = int(buf[0]), int(buf[1])
+    tiles = buf[4:4 + 6 * nt].reshape(nt, 6)
+    segs = buf[4 + 6 * nt:4 + 6 * nt + 5 * ns].reshape(ns, 5)
+    return {"tiles": tiles, "segs": segs, "n_cta": int(buf[2]), "n_partial": int(buf[3])}
+
+
+def last_config():
+    """(n_cta, tile_n, schedule) of the last plan this thread launched."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    load().xe_last_config(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
     return a.value, b.value, c.value
 
 
@@ -254,19 +288,39 @@ class Stream:
             _check(rc, "xe_stream_push")
         return rc
 
+    def push_frames(self, chans, frames, seqs, t_arrival_ns: int = 0):
+        """Push several frames in one call; returns the per-frame codes (numpy int32)."""
+        import numpy as np
+        n = len(chans)
+        for f in frames:
+            if f.numel() != self.frame_T * self.N or bool(f.is_cuda) != self.device_source:
+                raise ValueError("bad frame")
+        c = np.ascontiguousarray(chans, np.int32)
+        q = np.ascontiguousarray(seqs, np.int64)
+        ptrs = (ctypes.c_void_p * n)(*[f.data_ptr() for f in frames])
+        rc = np.zeros(n, np.int32)
+        got = load().xe_stream_push_frames(self.h, n, c.ctypes.data, ptrs, q.ctypes.data,
+                                           t_arrival_ns, rc.ctypes.data)
+        if got < 0:
+            _check(got, "xe_stream_push_frames")
+        return rc
+
     def flush(self):
         _check(load().xe_stream_flush(self.h), "xe_stream_flush")
 
-    def poll(self, timeout_ms: int = 0):
-        """Next completed integration as (meta dict, int32 numpy [B, 2] copy), or None."""
+    def poll(self, timeout_ms: int = 0, copy: bool = True):
+        """Next completed integration as (meta dict, int32 numpy [B, 2] copy or None), or
+        None if nothing is ready.  The result buffer is handed back to the stream."""
         import numpy as np
         r = Result()
         rc = load().xe_stream_poll(self.h, ctypes.byref(r), timeout_ms)
         if rc == XE_EAGAIN:
             return None
         _check(rc, "xe_stream_poll")
-        buf = (ctypes.c_int32 * (2 * self.B)).from_address(r.vis)
-        vis = np.frombuffer(buf, dtype=np.int32).reshape(self.B, 2).copy()
+        vis = None
+        if copy:
+            buf = (ctypes.c_int32 * (2 * self.B)).from_address(r.vis)
+            vis = np.frombuffer(buf, dtype=np.int32).reshape(self.B, 2).copy()
         _check(load().xe_stream_release(self.h, r.handle), "xe_stream_release")
         meta = {k: getattr(r, k) for k, _ in Result._fields_ if k != "vis"}
         return meta, vis

@@ -142,3 +142,61 @@ def test_plan_stats_batch_and_split():
     assert xe.plan_stats([(2048, 32768, 1)], 1)[2] == 0
     t2, i2, _ = xe.plan_stats([(256, 4096, 2), (512, 8192, 1)], 152)
     assert t2 == 2 * 2 + 6 and i2 == 4 * 64 + 6 * 128
+
+
+def _check_plan(shapes, n_cta, sched, tile_n):
+    d = xe.plan_dump(shapes, n_cta, sched, tile_n)
+    tiles, segs = d["tiles"], d["segs"]
+    # tiles: cover every (i, j >= i) of every job/channel exactly once
+    for q, (N, T, C) in enumerate(shapes):
+        for c in range(C):
+            cover = np.zeros((N, N), np.int32)
+            for (job, ch, i0, j0, nj, kb) in tiles:
+                if job != q or ch != c:
+                    continue
+                assert kb == (T + 63) // 64
+                for i in range(i0, min(i0 + 128, N)):
+                    lo = max(j0, i)
+                    if lo < min(j0 + nj, N):
+                        cover[i, lo:min(j0 + nj, N)] += 1
+            iu = np.triu_indices(N)
+            assert (cover[iu] == 1).all() and cover.sum() == N * (N + 1) // 2
+    # segments: every k of every tile exactly once; partial segments own distinct slots
+    seen = {t: np.zeros(int(tiles[t][5]), np.int32) for t in range(len(tiles))}
+    slots = []
+    per_tile = {}
+    for (cta, t, lo, hi, slot) in segs:
+        assert 0 <= cta < d["n_cta"] <= n_cta and lo < hi
+        seen[int(t)][lo:hi] += 1
+        per_tile.setdefault(int(t), []).append(int(slot))
+    for t, v in seen.items():
+        assert (v == 1).all(), f"tile {t} k-cover {v.min()}..{v.max()}"
+        sl = per_tile[t]
+        if len(sl) == 1:
+            assert sl == [-1]
+        else:
+            assert min(sl) >= 0
+            slots += sl
+    assert len(slots) == len(set(slots)) == d["n_partial"]
+    return d
+
+
+@pytest.mark.parametrize("sched", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_schedules_cover_every_tile_and_k_once(sched, tile_n):
+    for shapes, n_cta in [([(2048, 32768, 1)], 152), ([(300, 1000, 3)], 7), ([(100, 64, 1)], 152),
+                          ([(256, 4096, 2), (512, 8192, 1), (130, 700, 1)], 19),
+                          ([(1024, 8192, 1)] * 4, 152)]:
+        _check_plan(shapes, n_cta, sched, tile_n)
+
+
+def test_split_schedule_aligns_parts_for_the_headline():
+    d = _check_plan([(2048, 32768, 1)], 152, 1, 256)
+    assert d["n_cta"] == 144                       # 72 tiles x 2 equal k-parts
+    assert set(map(tuple, d["segs"][:, 2:4].tolist())) == {(0, 256), (256, 512)}
+
+
+def test_hybrid_schedule_full_waves_whole():
+    d = _check_plan([(2048, 16384, 16)], 152, 2, 256)
+    whole = (d["segs"][:, 4] == -1).sum()
+    assert whole >= (1152 // 152) * 152            # full waves are whole tiles

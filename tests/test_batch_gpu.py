@@ -1,0 +1,144 @@
+"""Batched persistent launches: every job of a batch equals its solo launch and the oracle
+(exactly), for uneven N and T, every schedule and tile width, CUDA-graph replay with fresh
+pointers, the autotuner, and the full-size 16-channel and 64-instance workloads."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_09481_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def xe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_09481_gb300 import xe as _xe
+    _xe.load()
+    return _xe
+
+
+@pytest.fixture(autouse=True)
+def _reset(xe):
+    yield
+    for k, v in (("sched", -1), ("tile_n", 0), ("autotune", 0), ("n_cta", 0)):
+        xe.set_option(k, v)
+
+
+def make_batch(shapes, seed=0):
+    host = [synth.uniform(N, T, C, seed=seed + 17 * q) for q, (N, T, C) in enumerate(shapes)]
+    dev = [torch.from_numpy(h).cuda() for h in host]
+    return host, dev
+
+
+def run_batch(xe, shapes, dev, use_graph=False):
+    outs = [xe.empty_vis(N, C) for (N, T, C) in shapes]
+    xe.correlate_batch([(d, o, N, T, C) for d, o, (N, T, C) in zip(dev, outs, shapes)], use_graph=use_graph)
+    torch.cuda.synchronize()
+    xe.device_status()
+    return [o.cpu().numpy() for o in outs]
+
+
+UNEVEN = [(64, 100, 1), (200, 1000, 2), (256, 4096, 1), (512, 64, 3), (130, 3000, 1),
+          (700, 777, 1), (1, 5, 2), (257, 2048, 1)]
+
+
+def test_uneven_batch_equals_oracle_and_solo(xe):
+    host, dev = make_batch(UNEVEN, seed=1)
+    got = run_batch(xe, UNEVEN, dev)
+    for (N, T, C), h, g, d in zip(UNEVEN, host, got, dev):
+        np.testing.assert_array_equal(g, oracle.correlate_dense(h, N, T, C))
+        solo = xe.correlate(d, N, T, C)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(g, solo.cpu().numpy())
+
+
+@pytest.mark.parametrize("sched", [0, 1, 2, 3])
+@pytest.mark.parametrize("tile_n", [128, 256])
+def test_every_schedule_and_tile_width_is_exact(xe, sched, tile_n):
+    shapes = [(300, 1000, 2), (520, 2000, 1), (64, 64, 1)]
+    host, dev = make_batch(shapes, seed=2)
+    xe.set_option("sched", sched)
+    xe.set_option("tile_n", tile_n)
+    got = run_batch(xe, shapes, dev)
+    for (N, T, C), h, g in zip(shapes, host, got):
+        np.testing.assert_array_equal(g, oracle.correlate_dense(h, N, T, C))
+
+
+def test_graph_replay_with_new_pointers(xe):
+    shapes = [(256, 2048, 2), (384, 1000, 1)]
+    host_a, dev_a = make_batch(shapes, seed=3)
+    host_b, dev_b = make_batch(shapes, seed=4)
+    for host, dev in ((host_a, dev_a), (host_b, dev_b), (host_a, dev_a)):
+        got = run_batch(xe, shapes, dev, use_graph=True)
+        for (N, T, C), h, g in zip(shapes, host, got):
+            np.testing.assert_array_equal(g, oracle.correlate_dense(h, N, T, C))
+
+
+def test_autotune_picks_a_plan_and_stays_exact(xe):
+    shapes = [(640, 4096, 3)]
+    host, dev = make_batch(shapes, seed=5)
+    xe.set_option("autotune", 1)
+    got = run_batch(xe, shapes, dev)
+    n_cta, tile_n, sched = xe.last_config()
+    assert tile_n in (128, 256) and 0 <= sched <= 3 and n_cta > 0
+    np.testing.assert_array_equal(got[0], oracle.correlate_dense(host[0], 640, 4096, 3))
+
+
+def _sample_pairs(rng, N, n):
+    i = rng.integers(0, N, n)
+    j = np.array([rng.integers(a, N) for a in i])
+    # always include the corners and tile edges
+    extra_i = np.array([0, 0, N - 1, min(127, N - 1), min(128, N - 1), min(255, N - 1)])
+    extra_j = np.array([0, N - 1, N - 1, min(128, N - 1), min(255, N - 1), N - 1])
+    return np.concatenate([i, extra_i]), np.concatenate([j, np.maximum(extra_i, extra_j)])
+
+
+def test_config3_sixteen_channels_batched(xe):
+    # 16 channels x N=2048 x T=16384, quantised Gaussian + plane wave, one persistent launch
+    # (channels as one 16-channel job, and as 16 jobs in a graph): equal to each other, to
+    # per-channel solo launches, and to the oracle on sampled baselines.
+    N, T, C = 2048, 16384, 16
+    host = synth.gauss_plane(N, T, C)
+    d = torch.from_numpy(host).cuda()
+    out_a = xe.correlate(d, N, T, C)
+    jobs = [(d[c], xe.empty_vis(N, 1), N, T, 1) for c in range(C)]
+    xe.correlate_batch(jobs, use_graph=True)
+    torch.cuda.synchronize()
+    a = out_a.cpu().numpy()
+    for c in range(C):
+        np.testing.assert_array_equal(a[c], jobs[c][1].cpu().numpy()[0])
+    rng = np.random.default_rng(0)
+    for c in (0, 7, 15):
+        solo = xe.correlate(d[c].contiguous(), N, T, 1)
+        torch.cuda.synchronize()
+        np.testing.assert_array_equal(a[c], solo.cpu().numpy()[0])
+        ii, jj = _sample_pairs(rng, N, 150)
+        want = oracle.pairs(host, N, T, C, np.full(ii.size, c), ii, jj)
+        idx = ii * N - ii * (ii - 1) // 2 + (jj - ii)
+        np.testing.assert_array_equal(a[c][idx], want)
+
+
+def test_config4_uneven_64_instances_batched(xe):
+    # 64 instances, N in {256..2048}, T in {4096..65536} (seeded), one persistent launch,
+    # against 64 plain launches (exact) and the oracle on sampled baselines.
+    shapes = synth.uneven_shapes(64)
+    host = [synth.uniform(N, T, 1, seed=synth.BASE_SEED + 1 + q) for q, (N, T) in enumerate(shapes)]
+    dev = [torch.from_numpy(h).cuda() for h in host]
+    outs = [xe.empty_vis(N, 1) for (N, T) in shapes]
+    xe.correlate_batch([(d, o, N, T, 1) for d, o, (N, T) in zip(dev, outs, shapes)])
+    torch.cuda.synchronize()
+    xe.device_status()
+    rng = np.random.default_rng(1)
+    for q, ((N, T), h, d, o) in enumerate(zip(shapes, host, dev, outs)):
+        solo = xe.correlate(d, N, T, 1)
+        torch.cuda.synchronize()
+        g = o.cpu().numpy()
+        np.testing.assert_array_equal(g, solo.cpu().numpy())
+        if q % 8 == 0:
+            ii, jj = _sample_pairs(rng, N, 40)
+            want = oracle.pairs(h, N, T, 1, np.zeros(ii.size, np.int64), ii, jj)
+            idx = ii * N - ii * (ii - 1) // 2 + (jj - ii)
+            np.testing.assert_array_equal(g[0][idx], want)

@@ -108,7 +108,7 @@ def test_lost_frame_marks_integration_incomplete(xe):
 
 def test_admission_by_hbm_budget(xe):
     N, fT, F = 512, 4096, 2
-    per_chan = N * (N + 1) * 4 + 2 * fT * N + 2 * 512 * fT      # accumulator + ring + staging
+    per_chan = 2 * N * (N + 1) * 4 + 2 * fT * N + 2 * 512 * fT  # 2 accumulators + ring + staging
     with xe.Stream(N, fT, F * fT, max_chan=8, hbm_budget=2 * per_chan + 1000, ring_frames=2) as st:
         assert st.admit(0) == 0 and st.admit(1) == 0
         assert st.admit(2) == xe.XE_EBUDGET
@@ -130,3 +130,25 @@ def test_push_errors_and_backpressure(xe):
         with pytest.raises(xe.XeError):
             st.push(0, fr, 0)                  # duplicate sequence number
         st.flush()
+
+
+def test_push_frames_batch_matches_single_pushes(xe):
+    N, fT, F, C = 160, 512, 2, 5
+    data = {c: frames_for(N, fT, 2 * F, seed=300 + c) for c in range(C)}
+    with xe.Stream(N, fT, F * fT, max_chan=C, hbm_budget=1 << 30, ring_frames=3,
+                   device_source=True) as st:
+        for c in range(C):
+            assert st.admit(c) == 0
+        dev = {c: [torch.from_numpy(data[c][k]).cuda() for k in range(2 * F)] for c in range(C)}
+        for k in range(2 * F):
+            todo = list(range(C))
+            while todo:
+                rc = st.push_frames(todo, [dev[c][k] for c in todo], [k] * len(todo))
+                todo = [c for c, r in zip(todo, rc) if r == xe.XE_EAGAIN]
+                if todo:
+                    time.sleep(0.001)
+        res = drain(st, C * 2)
+    for meta, vis in res:
+        c, q = meta["chan"], meta["integ_index"]
+        block = data[c][q * F:(q + 1) * F].reshape(1, F * fT, N)
+        np.testing.assert_array_equal(vis, oracle.correlate_dense(block, N, F * fT, 1)[0])
