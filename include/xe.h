@@ -118,6 +118,11 @@ typedef struct xe_job {
  * shape (pointers are refreshed in place).  Returns as xe_correlate_async. */
 int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stream);
 
+/* As xe_correlate_batch without graphs, but ADDS each job's visibilities into its vis
+ * (vis += V): callers integrate consecutive blocks of samples into their own int32
+ * accumulators (time integration, section 2.1).  The caller keeps |sum| < 2^31. */
+int xe_correlate_accumulate(const xe_job *jobs, int n_jobs, void *stream);
+
 /* ---- host-side planning (no GPU needed; exposed for tests and tooling) ------------ */
 
 /* Work plan the persistent scheduler would use for a batch: number of triangle tiles,
@@ -213,6 +218,12 @@ int xe_stream_release(xe_stream *s, int64_t handle);
 /* Counters: admitted channels, frames processed, integrations completed, frames dropped. */
 int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *integrations,
                     int64_t *dropped);
+
+/* Scheduler counters, written to out[0 .. min(n, 8)): admitted channels, frames processed,
+ * integrations completed, frames dropped, scheduler passes that launched work, launch groups,
+ * passes that held back to fill a batch, host nanoseconds spent enqueuing launches.
+ * Returns the number of values written or a negative XE_* code. */
+int xe_stream_counters(xe_stream *s, int64_t *out, int n);
 
 /* Close the stream: stops its threads, waits (bounded) for in-flight work and frees all
  * of its memory.  Results not yet released become invalid. */

@@ -51,6 +51,7 @@ struct Options {
     int tile_n = 0;                        // 0: heuristic / autotuned; else 128 or 256
     int autotune = 0;                      // 1: time candidate plans on first sight of a shape
     int timing = 0;
+    int inject_stall = 0;                  // test hook for the bounded-wait path (next call only)
 };
 static Options g_opt;
 static std::mutex g_mu;
@@ -423,6 +424,7 @@ static int get_scratch(Device *d, cudaStream_t s, Scratch **out) {
 }
 
 static thread_local cudaEvent_t g_last_ev[3] = {nullptr, nullptr, nullptr};
+static thread_local const int *g_job_acc = nullptr;   // per-job accumulate flags (stream server)
 
 static int check_job(const uint8_t *in, int N, int64_t T, int C, const int32_t *vis) {
     if (!in || !vis) return fail(XE_EINVAL, "null input or output pointer");
@@ -491,6 +493,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             for (int k = 0; k < ng; ++k) {
                 const xe_job &j = jobs[act[g0 + size_t(k)]];
                 const int64_t Tw = std::min(j.T - w * wt, wt);
+                jt.jobs[k].accumulate = g_job_acc ? g_job_acc[act[g0 + size_t(k)]] : 0;
                 shapes.push_back(JobShape{j.N, Tw, j.n_chan});
                 JobDev &jd = jt.jobs[k];
                 jd.in = j.in;
@@ -546,6 +549,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             pd.ws = sc->ws;
             pd.counters = sc->counters;
             pd.status = sc->status;
+            pd.inject_stall = g_opt.inject_stall;
             out.push_back(st);
             out.push_back(tc);
         }
@@ -567,7 +571,7 @@ static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
     p.extra = nullptr;
     if (r.kind == 0) {
         p.func = const_cast<void *>(stage_kernel_fn(r.eb));
-        p.gridDim = dim3(unsigned(r.jt.total_stage_blocks));
+        p.gridDim = dim3(stage_grid(r.jt, r.eb));
         p.blockDim = dim3(256);
         p.sharedMemBytes = 0;
     } else if (r.kind == 1) {
@@ -652,6 +656,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
     }
     std::vector<LaunchRec> recs;
     rc = build_launches(d, sc, jobs, n_jobs, algo, accumulate, nullptr, recs);
+    g_opt.inject_stall = 0;
     if (rc) return rc;
     const bool timing = g_opt.timing != 0;
     if (timing) XE_CUDA(cudaEventRecord(sc->ev[0], s));
@@ -719,6 +724,14 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
 int run_jobs_accumulate(const xe_job *jobs, int n_jobs, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     return run_jobs(jobs, n_jobs, XE_ALGO_TC, s, 1);
+}
+
+int run_jobs_mixed(const xe_job *jobs, const int *accumulate, int n_jobs, cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_job_acc = accumulate;
+    const int rc = run_jobs(jobs, n_jobs, XE_ALGO_TC, s, 0);
+    g_job_acc = nullptr;
+    return rc;
 }
 
 static int plan_from_args(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
@@ -795,6 +808,8 @@ int xe_set_option(const char *key, int64_t value) {
         g_opt.autotune = value ? 1 : 0;
     } else if (!strcmp(key, "timing")) {
         g_opt.timing = value ? 1 : 0;
+    } else if (!strcmp(key, "inject_stall")) {
+        g_opt.inject_stall = value ? 1 : 0;
     } else {
         return fail(XE_EINVAL, "unknown option '%s'", key);
     }
@@ -873,6 +888,16 @@ int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stre
     }
     std::lock_guard<std::mutex> lk(g_mu);
     return run_jobs(jobs, n_jobs, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream), 0, use_graph);
+}
+
+int xe_correlate_accumulate(const xe_job *jobs, int n_jobs, void *stream) {
+    if (!jobs || n_jobs < 1) return fail(XE_EINVAL, "empty batch");
+    for (int q = 0; q < n_jobs; ++q) {
+        int rc = check_job(jobs[q].in, jobs[q].N, jobs[q].T, jobs[q].n_chan, jobs[q].vis);
+        if (rc) return rc;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    return run_jobs(jobs, n_jobs, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream), 1, 0);
 }
 
 int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,

@@ -134,7 +134,7 @@ __global__ void __launch_bounds__(128) imma_kernel(const __grid_constant__ JobTa
                 if (i < N && j < N && j >= i) {
                     const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
                     int2 *p = reinterpret_cast<int2 *>(vis + 2 * k);
-                    if (jt.accumulate) {
+                    if (jt.accumulate | jb.accumulate) {
                         const int2 o = *p;
                         *p = make_int2(o.x + acc_re[mt][nt][e], o.y + acc_im[mt][nt][e]);
                     } else {

@@ -17,8 +17,9 @@ constexpr int kAPlane = kBM * kRowBytes;              // 8 KB
 constexpr int kBPlane = kBN * kRowBytes;              // 16 KB
 constexpr int kStageBytes = 2 * kAPlane + 2 * kBPlane;  // 48 KB
 constexpr int kTcThreads = 192;    // 4 epilogue warps, 1 producer warp, 1 MMA warp
-constexpr int kTcSmem = kStages * kStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kMaxJobs = 128;      // jobs per launch (passed by value)
+constexpr int kEpiStageBytes = 4 * 32 * 33 * 8;  // per epilogue warp: 32 x 33 int2 transpose buffer
+constexpr int kTcSmem = kStages * kStageBytes + kEpiStageBytes + 1024 /*align*/ + 256 /*barriers*/;
+constexpr int kMaxJobs = 256;      // jobs per launch (passed by value)
 
 // Samples per stage: 64 with 1-byte (e4m3) operands, 32 with 2-byte (f16) operands.
 __host__ __device__ constexpr int samples_per_stage(int elem_bytes) {
@@ -44,6 +45,7 @@ struct JobDev {
     int n_pad;
     int C;
     int kblocks;              // ceil(T / samples_per_stage)
+    int accumulate;           // 1: this job adds into vis (vis += V) even if the launch overwrites
     int64_t stage_block0;     // first block of this job in the stage (or anchor) grid
 };
 
@@ -86,6 +88,7 @@ struct PlanDev {
     int32_t *ws;              // partial-tile workspace, one slot per partial segment
     int *counters;            // one arrival counter per tile, zero between launches
     int *status;              // device status word (0 = ok)
+    int inject_stall;         // test hook: 1 = the producer issues no copies, so waits time out
 };
 
 // Triangle schedules (host-side choice; the kernel just follows the segment lists).
@@ -113,6 +116,7 @@ cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
 const void *stage_kernel_fn(int elem_bytes);
+unsigned stage_grid(const JobTable &jt, int elem_bytes);
 const void *tc_kernel_fn(int elem_bytes);
 const void *imma_kernel_fn();
 cudaError_t tc_prepare();
@@ -120,6 +124,8 @@ cudaError_t tc_prepare();
 // Enqueue jobs on stream s in accumulate mode (vis += V), tensor-core path; takes the
 // runtime lock.  Used by the streaming server.  Returns an XE_* code.
 int run_jobs_accumulate(const struct ::xe_job *jobs, int n_jobs, cudaStream_t s);
+// Same, with a per-job choice: accumulate[k] = 1 adds into job k's vis, 0 overwrites it.
+int run_jobs_mixed(const struct ::xe_job *jobs, const int *accumulate, int n_jobs, cudaStream_t s);
 
 // Record a failure for xe_last_error() on this thread; returns `code`.
 int record_error(int code, const char *msg);

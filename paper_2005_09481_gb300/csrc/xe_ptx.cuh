@@ -7,8 +7,8 @@
 
 namespace xe {
 
-// Give up on any single barrier wait after this many SM clock cycles (~2 s at 2 GHz).
-constexpr long long kWaitBudgetCycles = 4000000000LL;
+// Give up on any single barrier wait after this many SM clock cycles (~1 s at 2 GHz).
+constexpr long long kWaitBudgetCycles = 2000000000LL;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));

@@ -61,6 +61,7 @@ struct Chan {
     int32_t *acc[2] = {nullptr, nullptr};
     cudaEvent_t acc_free_ev[2] = {nullptr, nullptr};  // export of that accumulator done
     bool acc_wait[2] = {false, false};                // compute must wait on acc_free_ev
+    bool fresh[2] = {true, true};                     // next frame overwrites (no stale sums)
     int cur = 0;                                      // accumulator being filled
     std::vector<Slot> ring;
     std::deque<Entry> fifo;
@@ -115,12 +116,17 @@ struct xe_stream {
     int64_t used_bytes = 0;
     int64_t n_admitted = 0, n_frames = 0, n_integ = 0, n_dropped = 0;
     int last_error = XE_OK;
+    int64_t hold_since = 0;          // first pass that held back a partial batch
+    bool flush_req = false;
+    int64_t n_launch_groups = 0, n_launch_passes = 0, n_held = 0, launch_ns = 0;
 };
 
 namespace xe {
 namespace {
 
 constexpr int kBufsPerChan = 2;
+constexpr int kMaxGroups = 4;                 // frames of one channel per scheduler pass
+constexpr int64_t kHoldNs = 1500000;          // longest wait for a fuller batch
 
 cudaEvent_t take_event(xe_stream *s) {
     if (!s->spare_events.empty()) {
@@ -187,7 +193,9 @@ Export close_integration(xe_stream *s, int c) {
 
 // One scheduler pass.  Returns true if it did any work.
 bool pass(xe_stream *s) {
-    std::vector<xe_job> jobs;
+    std::vector<std::vector<xe_job>> groups(static_cast<size_t>(kMaxGroups));
+    std::vector<std::vector<int>> group_acc(static_cast<size_t>(kMaxGroups));
+    size_t n_jobs = 0;
     std::vector<int> used;             // (chan << 8 | slot) read by this pass
     std::vector<cudaEvent_t> waits;    // accumulator exports the launches must follow
     std::vector<Export> exports;
@@ -230,12 +238,35 @@ bool pass(xe_stream *s) {
             s->cv_ready.notify_all();
             work = true;
         }
-        // At most one frame per channel per pass: two frames of one channel in one launch
-        // would add into the same accumulator concurrently.
+        // Batching: while frames are still being copied in and fewer than all waiting
+        // channels are ready, hold the launch for up to kHoldNs so one launch carries them.
+        int n_ready = 0, n_copying = 0;
+        for (size_t c = 0; c < s->chans.size(); ++c) {
+            const Chan &ch = s->chans[c];
+            if (!ch.admitted || ch.fifo.empty()) continue;
+            const Entry &e = ch.fifo.front();
+            if (e.slot < 0 || ch.ring[size_t(e.slot)].state == kReady) ++n_ready;
+            else ++n_copying;
+        }
+        const int64_t t_now = now_ns();
+        if (n_ready == 0) {
+            s->hold_since = 0;
+        } else if (n_copying > 0) {
+            if (s->hold_since == 0) s->hold_since = t_now;
+            if (t_now - s->hold_since < kHoldNs && !s->flush_req) {
+                ++s->n_held;
+                return work;
+            }
+        }
+        s->hold_since = 0;
+        // Up to kMaxGroups frames per channel: the g-th frame of every channel goes to launch
+        // group g (frames of one channel never share a launch: they add into the same
+        // accumulator).  A channel stops at its first closed integration in the pass.
         for (size_t c = 0; c < s->chans.size(); ++c) {
             Chan &ch = s->chans[c];
             if (!ch.admitted) continue;
-            while (!ch.fifo.empty()) {
+            int g = 0;
+            while (!ch.fifo.empty() && g < kMaxGroups) {
                 const Entry e = ch.fifo.front();
                 const bool closes = ch.frames_in_integ + 1 == s->frames_per_integ;
                 if (closes && !has_free_buf(s, int(c))) break;       // consumer is behind
@@ -259,23 +290,38 @@ bool pass(xe_stream *s) {
                     waits.push_back(ch.acc_free_ev[ch.cur]);
                     ch.acc_wait[ch.cur] = false;
                 }
-                jobs.push_back(xe_job{sl.dev, ch.acc[ch.cur], s->cfg.N, 1, s->cfg.frame_T});
+                groups[size_t(g)].push_back(xe_job{sl.dev, ch.acc[ch.cur], s->cfg.N, 1, s->cfg.frame_T});
+                group_acc[size_t(g)].push_back(ch.fresh[ch.cur] ? 0 : 1);
+                ch.fresh[ch.cur] = false;
                 used.push_back(int(c) << 8 | e.slot);
                 if (ch.frames_in_integ == 0) ch.t_first = e.t_arrival;
                 ch.t_last = e.t_arrival;
                 ch.frames_in_integ += 1;
                 ch.samples_in_integ += s->cfg.frame_T;
-                if (closes) exports.push_back(close_integration(s, int(c)));
-                break;
+                ++g;
+                if (closes) {
+                    exports.push_back(close_integration(s, int(c)));
+                    break;
+                }
             }
         }
+        s->flush_req = false;
+        n_jobs = 0;
+        for (auto &gr : groups) n_jobs += gr.size();
     }
-    if (jobs.empty() && exports.empty()) return work;
+    if (n_jobs == 0 && exports.empty()) return work;
 
     // Launch outside the lock; pushes and polls proceed meanwhile.
     for (cudaEvent_t e : waits) cudaStreamWaitEvent(s->comp_s, e, 0);
     int rc = XE_OK;
-    if (!jobs.empty()) rc = run_jobs_accumulate(jobs.data(), int(jobs.size()), s->comp_s);
+    const int64_t t_l0 = now_ns();
+    int n_groups = 0;
+    for (size_t gi = 0; gi < groups.size(); ++gi)
+        if (!groups[gi].empty() && rc == XE_OK) {
+            rc = run_jobs_mixed(groups[gi].data(), group_acc[gi].data(), int(groups[gi].size()), s->comp_s);
+            ++n_groups;
+        }
+    const int64_t t_l1 = now_ns();
     cudaEvent_t done = nullptr;
     std::vector<Pending> pend;
     {
@@ -290,19 +336,24 @@ bool pass(xe_stream *s) {
             s->pass_events[size_t(pe)].refs += 1;
             s->queued_slots.push_back(code);
         }
-        s->n_frames += int64_t(jobs.size());
+        s->n_frames += int64_t(n_jobs);
+        s->n_launch_groups += n_groups;
+        s->n_launch_passes += n_groups > 0 ? 1 : 0;
+        s->launch_ns += t_l1 - t_l0;
         // Exports run on their own stream after this pass's launches.
         if (!exports.empty()) cudaStreamWaitEvent(s->d2h_s, done, 0);
         for (const Export &ex : exports) {
             Chan &ch = s->chans[size_t(ex.chan)];
             int32_t *acc = ch.acc[ex.acc_idx];
+            // An integration whose frames were all lost never wrote its accumulator.
+            if (ch.fresh[ex.acc_idx]) cudaMemsetAsync(acc, 0, s->acc_bytes, s->d2h_s);
             cudaMemcpyAsync(s->bufs[size_t(ex.buf)].host, acc, s->acc_bytes, cudaMemcpyDeviceToHost, s->d2h_s);
             Pending p{};
             p.r = ex.r;
             p.ev = take_event(s);
             cudaEventRecord(p.ev, s->d2h_s);
-            cudaMemsetAsync(acc, 0, s->acc_bytes, s->d2h_s);
             cudaEventRecord(ch.acc_free_ev[ex.acc_idx], s->d2h_s);
+            ch.fresh[ex.acc_idx] = true;        // its next frame overwrites it
             s->pending.push_back(p);
         }
     }
@@ -417,6 +468,7 @@ int xe_stream_admit(xe_stream *s, int chan) {
         cudaMemset(ch.acc[a], 0, s->acc_bytes);
         cudaEventCreateWithFlags(&ch.acc_free_ev[a], cudaEventDisableTiming);
         ch.acc_wait[a] = false;
+        ch.fresh[a] = true;
     }
     ch.cur = 0;
     ch.ring.assign(size_t(s->cfg.ring_frames), Slot{});
@@ -539,6 +591,7 @@ int xe_stream_flush(xe_stream *s) {
             for (const Chan &ch : s->chans)
                 if (ch.admitted && !ch.fifo.empty()) { any = true; break; }
             if (!any) return XE_OK;
+            s->flush_req = true;
         }
         s->cv_work.notify_one();
         std::this_thread::sleep_for(std::chrono::microseconds(100));
@@ -581,6 +634,15 @@ int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *i
     if (integrations) *integrations = s->n_integ;
     if (dropped) *dropped = s->n_dropped;
     return XE_OK;
+}
+
+int xe_stream_counters(xe_stream *s, int64_t *out, int n) {
+    if (!s || !out || n < 1) return sfail(XE_EINVAL, "bad counter query");
+    std::lock_guard<std::mutex> lk(s->mu);
+    const int64_t v[8] = {s->n_admitted, s->n_frames, s->n_integ, s->n_dropped,
+                          s->n_launch_passes, s->n_launch_groups, s->n_held, s->launch_ns};
+    for (int k = 0; k < n && k < 8; ++k) out[k] = v[k];
+    return n < 8 ? n : 8;
 }
 
 void xe_stream_close(xe_stream *s) {

@@ -64,6 +64,27 @@ __host__ __device__ constexpr NibbleCodes make_codes(int elem_bytes) {
 __constant__ NibbleCodes c_codes_e4m3 = make_codes(1);
 __constant__ NibbleCodes c_codes_f16 = make_codes(2);
 
+// Four e4m3 codes packed little-endian into one word: nibble values lo..lo+3.
+__host__ __device__ constexpr uint32_t pack_codes(int lo) {
+    return encode_small_int(nibble_value(lo), 1) | (encode_small_int(nibble_value(lo + 1), 1) << 8) |
+           (encode_small_int(nibble_value(lo + 2), 1) << 16) | (encode_small_int(nibble_value(lo + 3), 1) << 24);
+}
+
+// Four two's-complement nibbles (one in the low 4 bits of each byte) -> four e4m3 codes.
+// A byte permute looks each nibble up in the 16-entry code table (held in four words:
+// values 0..3, 4..7, -8..-5, -4..-1): the low 3 bits select within the non-negative or the
+// negative half, bit 3 chooses the half.
+__device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t x) {
+    constexpr uint32_t P0 = pack_codes(0), P1 = pack_codes(4), N0 = pack_codes(8), N1 = pack_codes(12);
+    const uint32_t y = x & 0x07070707u;
+    const uint32_t z = y | (y >> 4);
+    const uint32_t sel = __byte_perm(z, 0, 0x0020);
+    const uint32_t pos = __byte_perm(P0, P1, sel);
+    const uint32_t neg = __byte_perm(N0, N1, sel);
+    const uint32_t m = ((x >> 3) & 0x01010101u) * 0xFFu;
+    return (pos & ~m) | (neg & m);
+}
+
 // ---- staging kernel ----------------------------------------------------------------------
 
 __device__ __forceinline__ int find_job(const JobTable &jt, int64_t blk) {
@@ -121,29 +142,47 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ JobT
     }
     __syncthreads();
 
-    // Row n0+tid of both planes: 4 chunks of 16 bytes each, 64-byte swizzle.
-    const int row = n0 + tid;
-    uint8_t *pre = const_cast<uint8_t *>(jb.planes) + int64_t(c) * jb.plane_chan_bytes +
-                   ((int64_t(kb) * 2 + 0) * jb.n_pad + row) * kRowBytes;
-    uint8_t *pim = pre + int64_t(jb.n_pad) * kRowBytes;
-    const int sw = (tid >> 1) & 3;
+    uint8_t *plane0 = const_cast<uint8_t *>(jb.planes) + int64_t(c) * jb.plane_chan_bytes +
+                      (int64_t(kb) * 2 * jb.n_pad + n0) * kRowBytes;
+    const int64_t im_off = int64_t(jb.n_pad) * kRowBytes;
+    if (EB == 1) {
+        // Thread: rows n0 + 4g .. +3 (g = tid % 64), 16-sample chunk q = tid / 64 of each.
+        // Four 32-bit shared loads give a 4x4 byte block (4 samples x 4 inputs); a byte
+        // transpose turns it into 4 samples of each input, and the nibble -> e4m3 table
+        // (held in registers) converts them.
+        const int g = tid & 63, q = tid >> 6;
+        uint32_t re[4][4], im[4][4];                 // [input][word of the 16-byte chunk]
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        uint32_t wr[4], wi[4];
-        if (EB == 1) {
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t w[4];
 #pragma unroll
-            for (int w = 0; w < 4; ++w) {
-                uint32_t xr = 0, xi = 0;
+            for (int r = 0; r < 4; ++r)
+                w[r] = *reinterpret_cast<const uint32_t *>(&raw[q * 16 + kk * 4 + r][4 * g]);
+            const uint32_t a = __byte_perm(w[0], w[1], 0x5140), b = __byte_perm(w[2], w[3], 0x5140);
+            const uint32_t cc = __byte_perm(w[0], w[1], 0x7362), d = __byte_perm(w[2], w[3], 0x7362);
+            const uint32_t v[4] = {__byte_perm(a, b, 0x5410), __byte_perm(a, b, 0x7632),
+                                   __byte_perm(cc, d, 0x5410), __byte_perm(cc, d, 0x7632)};
 #pragma unroll
-                for (int b = 0; b < 4; ++b) {
-                    const uint32_t code = lut[raw[q * 16 + w * 4 + b][tid]];
-                    xr |= (code & 0xFFu) << (8 * b);
-                    xi |= ((code >> 16) & 0xFFu) << (8 * b);
-                }
-                wr[w] = xr;
-                wi[w] = xi;
+            for (int i = 0; i < 4; ++i) {
+                re[i][kk] = e4m3_of_nibbles((v[i] >> 4) & 0x0F0F0F0Fu);
+                im[i][kk] = e4m3_of_nibbles(v[i] & 0x0F0F0F0Fu);
             }
-        } else {
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = 4 * g + i;
+            uint8_t *pre = plane0 + int64_t(row) * kRowBytes + ((q ^ ((row >> 1) & 3)) << 4);
+            *reinterpret_cast<uint4 *>(pre) = make_uint4(re[i][0], re[i][1], re[i][2], re[i][3]);
+            *reinterpret_cast<uint4 *>(pre + im_off) = make_uint4(im[i][0], im[i][1], im[i][2], im[i][3]);
+        }
+    } else {
+        // f16 operands: row n0+tid of both planes, 4 chunks of 8 samples each.
+        const int row = tid;
+        uint8_t *pre = plane0 + int64_t(row) * kRowBytes;
+        const int sw = (row >> 1) & 3;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            uint32_t wr[4], wi[4];
 #pragma unroll
             for (int w = 0; w < 4; ++w) {
                 const uint32_t c0 = lut[raw[q * 8 + w * 2 + 0][tid]];
@@ -151,18 +190,158 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ JobT
                 wr[w] = (c0 & 0xFFFFu) | (c1 << 16);
                 wi[w] = (c0 >> 16) | (c1 & 0xFFFF0000u);
             }
+            const int off = ((q ^ sw) << 4);
+            *reinterpret_cast<uint4 *>(pre + off) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
+            *reinterpret_cast<uint4 *>(pre + im_off + off) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
         }
-        const int off = ((q ^ sw) << 4);
-        *reinterpret_cast<uint4 *>(pre + off) = make_uint4(wr[0], wr[1], wr[2], wr[3]);
-        *reinterpret_cast<uint4 *>(pim + off) = make_uint4(wi[0], wi[1], wi[2], wi[3]);
     }
+}
+
+// Persistent e4m3 staging kernel: each block walks the (job, channel, k-block, 256-input)
+// items with a grid stride; the packed [64][256] input tile of the next item streams into
+// the other half of a double buffer (cp.async, zero-filled outside [0,T) x [0,N)) while
+// the current one is converted, so HBM reads, conversion and plane writes overlap.
+constexpr int kStageBlocksPerSm = 4;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_u32(dst)), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+
+struct StageItem {
+    const JobDev *jb;
+    int c, kb, n0;
+};
+
+__device__ __forceinline__ StageItem stage_item(const JobTable &jt, int64_t blk) {
+    const JobDev &jb = jt.jobs[find_job(jt, blk)];
+    const int64_t local = blk - jb.stage_block0;
+    const int nblk = jb.n_pad / 256;
+    StageItem it;
+    it.jb = &jb;
+    it.n0 = int(local % nblk) * 256;
+    const int64_t rest = local / nblk;
+    it.kb = int(rest % jb.kblocks);
+    it.c = int(rest / jb.kblocks);
+    return it;
+}
+
+// Shared layout of one packed input tile: sample t of the 64 is stored at row
+// 4 * (t % 16) + t / 16, rows 288 bytes apart, so that the four 16-sample chunks read by the
+// four lanes of one input group fall in distinct banks.
+constexpr int kRawStride = 288;
+__device__ __forceinline__ int raw_row(int t) { return 4 * (t & 15) + (t >> 4); }
+
+__global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__ JobTable jt) {
+    constexpr int KS = 64;
+    __shared__ __align__(16) uint8_t raw[2][KS][kRawStride];
+    const int tid = threadIdx.x;
+    const int64_t total = jt.total_stage_blocks;
+
+    // Issue the loads of one item into buffer b (vector path: N % 16 == 0, aligned input).
+    auto issue = [&](int64_t blk, int b) {
+        const StageItem it = stage_item(jt, blk);
+        const JobDev &jb = *it.jb;
+        const uint8_t *src = jb.in + (int64_t(it.c) * jb.T_in + jb.t0) * jb.N;
+        const int seg = tid & 15;
+        const int n = it.n0 + seg * 16;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int r = (tid >> 4) + 16 * j;
+            const int64_t t = int64_t(it.kb) * KS + r;
+            const bool ok = t < jb.T && n < jb.N;
+            cp_async16(&raw[b][raw_row(r)][seg * 16], ok ? static_cast<const void *>(src + t * jb.N + n)
+                                                 : static_cast<const void *>(jb.in), ok ? 16u : 0u);
+        }
+    };
+    auto vec_ok = [&](const JobDev &jb) {
+        return (jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0;
+    };
+
+    int b = 0;
+    int64_t blk = blockIdx.x;
+    if (blk < total && vec_ok(*stage_item(jt, blk).jb)) issue(blk, b);
+    cp_async_commit();
+    for (; blk < total; blk += gridDim.x) {
+        const StageItem it = stage_item(jt, blk);
+        const JobDev &jb = *it.jb;
+        const int64_t next = blk + gridDim.x;
+        if (next < total && vec_ok(*stage_item(jt, next).jb)) issue(next, b ^ 1);
+        cp_async_commit();
+        if (!vec_ok(jb)) {
+            // Scalar path (N not a multiple of 16 or unaligned input): byte loads.
+            const uint8_t *src = jb.in + (int64_t(it.c) * jb.T_in + jb.t0) * jb.N;
+            for (int r = 0; r < KS; ++r) {
+                const int64_t t = int64_t(it.kb) * KS + r;
+                const int n = it.n0 + tid;
+                raw[b][raw_row(r)][tid] = (t < jb.T && n < jb.N) ? src[t * jb.N + n] : uint8_t(0);
+            }
+        }
+        cp_async_wait1();
+        __syncthreads();
+
+        uint8_t *plane0 = const_cast<uint8_t *>(jb.planes) + int64_t(it.c) * jb.plane_chan_bytes +
+                          (int64_t(it.kb) * 2 * jb.n_pad + it.n0) * kRowBytes;
+        const int64_t im_off = int64_t(jb.n_pad) * kRowBytes;
+        // Lane l of warp w: input group g = 8w + l/4 (inputs 4g..4g+3), 16-sample chunk q = l%4;
+        // the four lanes of a group write the four chunks of a row together (full sectors).
+        const int g = (tid >> 5) * 8 + ((tid & 31) >> 2), q = tid & 3;
+        uint32_t re[4][4], im[4][4];
+#pragma unroll
+        for (int kk = 0; kk < 4; ++kk) {
+            uint32_t w[4];
+#pragma unroll
+            for (int r = 0; r < 4; ++r)
+                w[r] = *reinterpret_cast<const uint32_t *>(&raw[b][raw_row(q * 16 + kk * 4 + r)][4 * g]);
+            const uint32_t a = __byte_perm(w[0], w[1], 0x5140), bb = __byte_perm(w[2], w[3], 0x5140);
+            const uint32_t cc = __byte_perm(w[0], w[1], 0x7362), d = __byte_perm(w[2], w[3], 0x7362);
+            const uint32_t v[4] = {__byte_perm(a, bb, 0x5410), __byte_perm(a, bb, 0x7632),
+                                   __byte_perm(cc, d, 0x5410), __byte_perm(cc, d, 0x7632)};
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                re[i][kk] = e4m3_of_nibbles((v[i] >> 4) & 0x0F0F0F0Fu);
+                im[i][kk] = e4m3_of_nibbles(v[i] & 0x0F0F0F0Fu);
+            }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int row = 4 * g + i;
+            uint8_t *pre = plane0 + int64_t(row) * kRowBytes + ((q ^ ((row >> 1) & 3)) << 4);
+            *reinterpret_cast<uint4 *>(pre) = make_uint4(re[i][0], re[i][1], re[i][2], re[i][3]);
+            *reinterpret_cast<uint4 *>(pre + im_off) = make_uint4(im[i][0], im[i][1], im[i][2], im[i][3]);
+        }
+        __syncthreads();   // raw[b] is refilled two iterations from now
+        b ^= 1;
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+}
+
+static int sm_count() {
+    static int n = 0;
+    if (n == 0) {
+        int dev = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+        if (n <= 0) n = 148;
+    }
+    return n;
+}
+
+// Grid of the staging launch (also used when the launch is placed in a CUDA graph).
+unsigned stage_grid(const JobTable &jt, int elem_bytes) {
+    if (elem_bytes == 2) return unsigned(jt.total_stage_blocks);
+    const int64_t cap = int64_t(sm_count()) * kStageBlocksPerSm;
+    return unsigned(jt.total_stage_blocks < cap ? jt.total_stage_blocks : cap);
 }
 
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s) {
     if (jt.total_stage_blocks <= 0) return cudaSuccess;
     if (jt.total_stage_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const dim3 grid(unsigned(jt.total_stage_blocks));
-    if (elem_bytes == 1) stage_kernel<1><<<grid, 256, 0, s>>>(jt);
+    const dim3 grid(stage_grid(jt, elem_bytes));
+    if (elem_bytes == 1) stage_e4m3_kernel<<<grid, 256, 0, s>>>(jt);
     else stage_kernel<2><<<grid, 256, 0, s>>>(jt);
     return cudaGetLastError();
 }
@@ -173,26 +352,51 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
 
-// Store (or add) one row run of final visibilities: row i, columns jbase .. jbase+31.
-__device__ __forceinline__ void store_run(const JobDev &jb, int chan, int i, int jbase,
-                                          const int (&re)[32], const int (&im)[32], int acc) {
-    if (i >= jb.N) return;
-    const int64_t N = jb.N;
-    int32_t *rowp = jb.vis + int64_t(chan) * jb.vis_chan_elems +
-                    2 * (int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 - i);
+// Store (or add) a 32 x 32 block of final visibilities held by one warp (lane = row
+// i0 + lane, register k = column jbase + k).  The block is transposed through the warp's
+// shared buffer so that each global access covers 32 consecutive baselines of one row
+// (256 contiguous bytes); in accumulate mode all 32 row loads are issued before any add.
+__device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, int jbase,
+                                            const int (&re)[32], const int (&im)[32], int acc,
+                                            int2 *stage) {
+    const int lane = threadIdx.x & 31;
 #pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        const int j = jbase + k;
-        if (j >= i && j < jb.N) {
-            int2 *p = reinterpret_cast<int2 *>(rowp + 2 * int64_t(j));
-            if (acc) {
-                const int2 o = *p;
-                *p = make_int2(o.x + re[k], o.y + im[k]);
-            } else {
-                *p = make_int2(re[k], im[k]);
+    for (int k = 0; k < 32; ++k) stage[lane * 33 + k] = make_int2(re[k], im[k]);
+    __syncwarp();
+    const int64_t N = jb.N;
+    int32_t *vis = jb.vis + int64_t(chan) * jb.vis_chan_elems;
+    const int j = jbase + lane;
+    if (acc) {
+        int2 old[32];
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int i = i0 + r;
+            old[r] = make_int2(0, 0);
+            if (i < jb.N && j >= i && j < jb.N) {
+                const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
+                old[r] = __ldcg(reinterpret_cast<const int2 *>(vis + 2 * k));
+            }
+        }
+#pragma unroll
+        for (int r = 0; r < 32; ++r) {
+            const int i = i0 + r;
+            if (i < jb.N && j >= i && j < jb.N) {
+                const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
+                const int2 v = stage[r * 33 + lane];
+                *reinterpret_cast<int2 *>(vis + 2 * k) = make_int2(old[r].x + v.x, old[r].y + v.y);
+            }
+        }
+    } else {
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const int i = i0 + r;
+            if (i < jb.N && j >= i && j < jb.N) {
+                const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
+                *reinterpret_cast<int2 *>(vis + 2 * k) = stage[r * 33 + lane];
             }
         }
     }
+    __syncwarp();
 }
 
 template <int EB>
@@ -208,6 +412,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     uint64_t *drain = acc_empty + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *epi_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    int2 *epi_stage = reinterpret_cast<int2 *>(smem + kStages * kStageBytes + 256) + (threadIdx.x >> 5) * 32 * 33;
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -244,7 +449,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             uint32_t ph = 0;
             int64_t fills = 0;
             bool ok = true;
-            for (int q = q0; ok && q < q1; ++q) {
+            // Test hook: issue nothing, so the MMA warp's bounded wait runs out.
+            for (int q = plan.inject_stall ? q1 : q0; ok && q < q1; ++q) {
                 const Seg sg = plan.segs[q];
                 const Tile tl = plan.tiles[sg.tile];
                 const JobDev &jb = jt.jobs[tl.job];
@@ -359,7 +565,6 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             acc_ph ^= 1u;
             tc_fence_after();
 
-            const int i = tl.i0 + r;
             if (sg.slot < 0) {
                 for (int cc = 0; cc < tl.nj; cc += 32) {
                     uint32_t fre[32], fim[32];
@@ -372,7 +577,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         re[k] = __float2int_rn(__uint_as_float(fre[k]));
                         im[k] = __float2int_rn(__uint_as_float(fim[k]));
                     }
-                    store_run(jb, tl.chan, i, tl.j0 + cc, re, im, jt.accumulate);
+                    store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + cc, re, im, jt.accumulate | jb.accumulate, epi_stage);
                 }
             } else {
                 // Partial tile: publish this segment's share; the last one to arrive sums all.
@@ -412,7 +617,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                                 im[k] += __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
                             }
                         }
-                        store_run(jb, tl.chan, i, tl.j0 + cc, re, im, jt.accumulate);
+                        store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + cc, re, im, jt.accumulate | jb.accumulate, epi_stage);
                     }
                 }
             }
@@ -432,7 +637,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 int tc_smem_bytes() { return kTcSmem; }
 
 const void *stage_kernel_fn(int elem_bytes) {
-    return elem_bytes == 1 ? reinterpret_cast<const void *>(stage_kernel<1>)
+    return elem_bytes == 1 ? reinterpret_cast<const void *>(stage_e4m3_kernel)
                            : reinterpret_cast<const void *>(stage_kernel<2>);
 }
 

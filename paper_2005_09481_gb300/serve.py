@@ -87,6 +87,7 @@ def run_realtime(n_chan: int, seconds: float, N: int = 2048, frame_T: int = 8192
         th.join(timeout=10.0)
         t_end = time.monotonic()
         stats = st.stats()
+        counters = st.counters()
     lat = sorted(lat_ns)
     pct = (lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] / 1e6) if lat else (lambda q: None)
     cmac_frame = N * (N + 1) / 2 * frame_T
@@ -103,6 +104,6 @@ def run_realtime(n_chan: int, seconds: float, N: int = 2048, frame_T: int = 8192
         "cmac_per_s": stats["frames"] * cmac_frame / span,
         "p50_latency_ms": pct(0.50), "p99_latency_ms": pct(0.99),
         "max_latency_ms": (lat[-1] / 1e6) if lat else None,
-        "drain_s": t_end - t_last_push, "device_source": device_source,
+        "drain_s": t_end - t_last_push, "device_source": device_source, "counters": counters,
         "frame_T": frame_T, "integ_T": integ_T, "N": N, "rate": rate,
     }

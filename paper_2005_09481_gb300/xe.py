@@ -56,6 +56,7 @@ def load():
             "xe_correlate_host": ([p, i32, i64, i32, p, i32], i32),
             "xe_correlate_batch": ([p, i32, i32, p], i32),
             "xe_correlate_noalloc": ([p, i32, i64, i32, p, p], i32),
+            "xe_correlate_accumulate": ([p, i32, p], i32),
             "xe_plan_stats": ([p, p, p, i32, i32, p, p, p], i32),
             "xe_set_option": ([ctypes.c_char_p, i64], i32),
             "xe_set_timing": ([i32], i32),
@@ -74,6 +75,7 @@ def load():
             "xe_stream_release": ([p, i64], i32),
             "xe_stream_stats": ([p, p, p, p, p], i32),
             "xe_stream_close": ([p], None),
+            "xe_stream_counters": ([p, p, i32], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -224,6 +226,17 @@ def correlate_batch(jobs, use_graph: bool = False, stream=None):
     return [j[1] for j in jobs]
 
 
+def correlate_accumulate(jobs, stream=None):
+    """jobs: list of (input, out, N, T, C); adds each job's visibilities into its out."""
+    arr = (Job * len(jobs))()
+    for k, (inp, out, N, T, C) in enumerate(jobs):
+        _shape(inp, N, T, C)
+        arr[k] = Job(inp.data_ptr(), out.data_ptr(), N, C, T)
+    _check(load().xe_correlate_accumulate(arr, len(jobs), _stream_handle(stream)),
+           "xe_correlate_accumulate")
+    return [j[1] for j in jobs]
+
+
 def correlate_noalloc(inp, N: int, T: int, C: int = 1, out=None, stream=None):
     """As correlate(algo="tc"), through the entry point that allocates nothing (its scratch
     is a fixed array inside the library; see include/xe.h for the limits)."""
@@ -329,6 +342,16 @@ class Stream:
         v = [ctypes.c_int64() for _ in range(4)]
         _check(load().xe_stream_stats(self.h, *[ctypes.byref(x) for x in v]), "xe_stream_stats")
         return dict(zip(("admitted", "frames", "integrations", "dropped"), [x.value for x in v]))
+
+    def counters(self):
+        import numpy as np
+        v = np.zeros(8, np.int64)
+        n = load().xe_stream_counters(self.h, v.ctypes.data, 8)
+        if n < 0:
+            _check(n, "xe_stream_counters")
+        keys = ("admitted", "frames", "integrations", "dropped", "launch_passes",
+                "launch_groups", "held_passes", "launch_host_ns")
+        return dict(zip(keys, v.tolist()))
 
     def close(self):
         if self.h:

@@ -142,3 +142,16 @@ def test_config4_uneven_64_instances_batched(xe):
             want = oracle.pairs(h, N, T, 1, np.zeros(ii.size, np.int64), ii, jj)
             idx = ii * N - ii * (ii - 1) // 2 + (jj - ii)
             np.testing.assert_array_equal(g[0][idx], want)
+
+
+def test_accumulate_adds_into_outputs(xe):
+    shapes = [(300, 1000, 2), (520, 640, 1)]
+    host_a, dev_a = make_batch(shapes, seed=8)
+    host_b, dev_b = make_batch(shapes, seed=9)
+    outs = [xe.empty_vis(N, C) for (N, T, C) in shapes]
+    xe.correlate_batch([(d, o, N, T, C) for d, o, (N, T, C) in zip(dev_a, outs, shapes)])
+    xe.correlate_accumulate([(d, o, N, T, C) for d, o, (N, T, C) in zip(dev_b, outs, shapes)])
+    torch.cuda.synchronize()
+    for (N, T, C), ha, hb, o in zip(shapes, host_a, host_b, outs):
+        both = np.concatenate([ha, hb], axis=1)
+        np.testing.assert_array_equal(o.cpu().numpy(), oracle.correlate_dense(both, N, 2 * T, C))

@@ -164,3 +164,21 @@ def test_host_buffers_entry_point(xe):
     p = synth.uniform(N, T, 2, seed=12)
     got = xe.correlate_host(torch.from_numpy(p).pin_memory(), N, T, 2)
     assert_exact(got.numpy(), oracle.correlate_dense(p, N, T, 2), "host")
+
+
+def test_bounded_wait_times_out_and_context_survives(xe):
+    # Test hook: the producer warp issues no copies, so the MMA warp's bounded wait on the
+    # pipeline barrier runs out (about a second); the kernel sets the status word, every
+    # role exits, and the next call on the same context is exact again.
+    N, T = 256, 1024
+    p = synth.uniform(N, T, 1, seed=31)
+    dev = torch.from_numpy(p).cuda()
+    xe.set_option("inject_stall", 1)
+    xe.correlate(dev, N, T, 1)
+    with pytest.raises(xe.XeError) as ei:
+        xe.device_status()
+    assert ei.value.code == xe.XE_ETIMEOUT
+    out = xe.correlate(dev, N, T, 1)
+    torch.cuda.synchronize()
+    xe.device_status()
+    assert_exact(out.cpu().numpy(), oracle.correlate(p, N, T, 1), "after timeout")
