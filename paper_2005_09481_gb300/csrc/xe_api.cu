@@ -573,7 +573,7 @@ static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
         p.func = const_cast<void *>(stage_kernel_fn(r.eb));
         p.gridDim = dim3(stage_grid(r.jt, r.eb));
         p.blockDim = dim3(256);
-        p.sharedMemBytes = 0;
+        p.sharedMemBytes = unsigned(stage_smem_bytes(r.eb));
     } else if (r.kind == 1) {
         p.func = const_cast<void *>(tc_kernel_fn(r.eb));
         p.gridDim = dim3(unsigned(r.pd.n_cta));
@@ -680,6 +680,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
         auto it = d->graphs.find(key);
         if (it == d->graphs.end()) {
             XE_CUDA(tc_prepare());
+            XE_CUDA(stage_prepare());
             g = new GraphRec;
             XE_CUDA(cudaGraphCreate(&g->graph, 0));
             cudaGraphNode_t prev = nullptr;

@@ -117,6 +117,8 @@ int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
 const void *stage_kernel_fn(int elem_bytes);
 unsigned stage_grid(const JobTable &jt, int elem_bytes);
+int stage_smem_bytes(int elem_bytes);
+cudaError_t stage_prepare();
 const void *tc_kernel_fn(int elem_bytes);
 const void *imma_kernel_fn();
 cudaError_t tc_prepare();

@@ -209,7 +209,7 @@ __device__ __forceinline__ void cp_async16(void *dst, const void *src, uint32_t 
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 struct StageItem {
     const JobDev *jb;
@@ -235,9 +235,12 @@ __device__ __forceinline__ StageItem stage_item(const JobTable &jt, int64_t blk)
 constexpr int kRawStride = 288;
 __device__ __forceinline__ int raw_row(int t) { return 4 * (t & 15) + (t >> 4); }
 
+constexpr int kStageSmem = 3 * 64 * kRawStride;   // three packed input tiles (dynamic smem)
+
 __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__ JobTable jt) {
     constexpr int KS = 64;
-    __shared__ __align__(16) uint8_t raw[2][KS][kRawStride];
+    extern __shared__ __align__(16) uint8_t stage_smem[];
+    auto raw = reinterpret_cast<uint8_t (*)[KS][kRawStride]>(stage_smem);
     const int tid = threadIdx.x;
     const int64_t total = jt.total_stage_blocks;
 
@@ -261,15 +264,19 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
         return (jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0;
     };
 
+    // Three buffers: the tiles of the next two items are in flight while one is converted.
     int b = 0;
     int64_t blk = blockIdx.x;
-    if (blk < total && vec_ok(*stage_item(jt, blk).jb)) issue(blk, b);
-    cp_async_commit();
+    for (int a = 0; a < 2; ++a) {
+        const int64_t pre = blk + int64_t(a) * gridDim.x;
+        if (pre < total && vec_ok(*stage_item(jt, pre).jb)) issue(pre, a);
+        cp_async_commit();
+    }
     for (; blk < total; blk += gridDim.x) {
         const StageItem it = stage_item(jt, blk);
         const JobDev &jb = *it.jb;
-        const int64_t next = blk + gridDim.x;
-        if (next < total && vec_ok(*stage_item(jt, next).jb)) issue(next, b ^ 1);
+        const int64_t next = blk + 2 * int64_t(gridDim.x);
+        if (next < total && vec_ok(*stage_item(jt, next).jb)) issue(next, b == 0 ? 2 : b - 1);
         cp_async_commit();
         if (!vec_ok(jb)) {
             // Scalar path (N not a multiple of 16 or unaligned input): byte loads.
@@ -280,7 +287,7 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
                 raw[b][raw_row(r)][tid] = (t < jb.T && n < jb.N) ? src[t * jb.N + n] : uint8_t(0);
             }
         }
-        cp_async_wait1();
+        cp_async_wait2();
         __syncthreads();
 
         uint8_t *plane0 = const_cast<uint8_t *>(jb.planes) + int64_t(it.c) * jb.plane_chan_bytes +
@@ -313,8 +320,8 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
             *reinterpret_cast<uint4 *>(pre) = make_uint4(re[i][0], re[i][1], re[i][2], re[i][3]);
             *reinterpret_cast<uint4 *>(pre + im_off) = make_uint4(im[i][0], im[i][1], im[i][2], im[i][3]);
         }
-        __syncthreads();   // raw[b] is refilled two iterations from now
-        b ^= 1;
+        __syncthreads();   // raw[b] is refilled by the next iteration's prefetch
+        b = b == 2 ? 0 : b + 1;
     }
     asm volatile("cp.async.wait_all;" ::: "memory");
 }
@@ -337,12 +344,31 @@ unsigned stage_grid(const JobTable &jt, int elem_bytes) {
     return unsigned(jt.total_stage_blocks < cap ? jt.total_stage_blocks : cap);
 }
 
+int stage_smem_bytes(int elem_bytes) { return elem_bytes == 1 ? kStageSmem : 0; }
+
+cudaError_t stage_prepare() {
+    static int done_dev[64] = {0};
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
+    e = cudaFuncSetAttribute(stage_e4m3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < 64) done_dev[dev] = 1;
+    return cudaSuccess;
+}
+
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s) {
     if (jt.total_stage_blocks <= 0) return cudaSuccess;
     if (jt.total_stage_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
     const dim3 grid(stage_grid(jt, elem_bytes));
-    if (elem_bytes == 1) stage_e4m3_kernel<<<grid, 256, 0, s>>>(jt);
-    else stage_kernel<2><<<grid, 256, 0, s>>>(jt);
+    if (elem_bytes == 1) {
+        cudaError_t e = stage_prepare();
+        if (e != cudaSuccess) return e;
+        stage_e4m3_kernel<<<grid, 256, kStageSmem, s>>>(jt);
+    } else {
+        stage_kernel<2><<<grid, 256, 0, s>>>(jt);
+    }
     return cudaGetLastError();
 }
 
@@ -604,13 +630,24 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                 }
                 epi_bar();
                 if (*epi_flag == 2) {
+                    // Last share to arrive: its own part is still in tensor memory; add the
+                    // other shares from the workspace.
                     __threadfence();
                     for (int cc = 0; cc < tl.nj; cc += 32) {
+                        uint32_t fre[32], fim[32];
+                        tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
+                        tmem_ld_32x32b_x32(tmem + lane_base + 256 + cc, fim);
+                        tmem_ld_wait();
                         int re[32], im[32];
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) { re[k] = 0; im[k] = 0; }
+                        for (int k = 0; k < 32; ++k) {
+                            re[k] = __float2int_rn(__uint_as_float(fre[k]));
+                            im[k] = __float2int_rn(__uint_as_float(fim[k]));
+                        }
                         for (int p = 0; p < tl.n_parts; ++p) {
-                            const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + p]) * kWsSlotElems;
+                            const int slot = plan.tile_slots[tl.part_off + p];
+                            if (slot == sg.slot) continue;
+                            const int32_t *w = plan.ws + int64_t(slot) * kWsSlotElems;
 #pragma unroll
                             for (int k = 0; k < 32; ++k) {
                                 re[k] += __ldcg(w + int64_t(cc + k) * kBM + r);
