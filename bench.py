@@ -291,7 +291,7 @@ def main():
     ap.add_argument("--workload", default="headline", choices=["headline", "batch16", "uneven64", "stream"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
-    ap.add_argument("--stream-channels", type=int, default=128)
+    ap.add_argument("--stream-channels", type=int, default=256)
     ap.add_argument("--stream-seconds", type=float, default=2.0)
     ap.add_argument("--stream-start", type=int, default=128)
     ap.add_argument("--stream-step", type=int, default=32)
@@ -403,6 +403,12 @@ def main():
         fp8_peak = 2.0 * bf16                  # dense FP8 = 2 x dense bf16 (nominal 4.5 / 2.25)
         kmean = statistics.mean(kern_ms)
         achieved = 8.0 * cm_step / (kmean * 1e-3) / 1e12
+        probes = {}
+        for kind in ("tc_fp8", "imma_s8"):
+            try:
+                probes[kind] = xe.peak_probe(kind)
+            except Exception as e:  # reported, never fatal
+                probes[kind] = f"failed: {e}"
         cpu = None
         if ws == 1 and not args.no_cpu_baseline:
             rate, cores, desc = cpu_oracle_rate(packed[0], N_IN)
@@ -420,7 +426,10 @@ def main():
                          "kernel": "tc_kernel<1> (tcgen05 kind::f8f6f4)",
                          "algorithmic": "8 int ops per cMAC x C*T*N(N+1)/2 cMAC per launch",
                          "peak_source": f"{src}: 2 x bf16_tflops ({bf16}) of MEASURED_PEAKS.json",
-                         "kernel_ms": kmean, "stage_ms": statistics.mean(stage_ms)},
+                         "kernel_ms": kmean, "stage_ms": statistics.mean(stage_ms),
+                         "probe_tflops": probes,
+                         "frac_of_probe": (achieved / probes["tc_fp8"]
+                                           if isinstance(probes.get("tc_fp8"), float) else None)},
             "cpu_baseline": cpu,
             "e2e": {"value": e2e_value, "unit": UNIT,
                     "h2d_bytes_per_step": int(packed.nbytes),

@@ -133,9 +133,10 @@ int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs,
 
 /* Dump the plan the scheduler builds for a batch, for a given CTA count, schedule
  * (-1 = the default choice; 0 stream-K, 1 equal k-split, 2 full waves + stream-K tail,
- * 3 longest-first) and tile width (0 = default, 128 or 256).  Writes into out[0..cap):
+ * 3 longest-first, 4 tile pairs sharing a column block on 2-CTA clusters with equal k-split)
+ * and tile width (0 = default, 128 or 256).  Writes into out[0..cap):
  * {n_tiles, n_segments, n_cta, n_partial}, then per tile {job, chan, i0, j0, nj, kblocks},
- * then per segment {cta, tile, k_lo, k_hi, slot}.  Returns the number of int32 values the
+ * then per segment {cta, tile (-1: partner-only), k_lo, k_hi, slot, multicast}.  Returns the number of int32 values the
  * dump needs (nothing is written when cap is smaller), or a negative XE_* code.
  * Pure host computation. */
 int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
@@ -259,12 +260,21 @@ int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_
 
 /* ---- diagnostics -------------------------------------------------------------------- */
 
+/* Measure a tensor-core ceiling on the current device: kind 0 = tcgen05 kind::f8f6f4
+ * (e4m3, M=128 N=256 K=32, operands resident in shared memory), kind 1 = mma.sync
+ * m16n8k32 s8, kind 2 = kind 0 while bulk copies stream 48 KB rounds into shared memory
+ * as fast as they complete from a 1 MB source, kind 3 = the same from a 64 MB source
+ * (*aux receives that fill rate in GB/s; aux may be NULL).
+ * Writes dense TFLOP/s (2 operations per multiply-accumulate) to *tflops.  Each loop runs
+ * for a few milliseconds.  Returns XE_OK or an XE_* code. */
+int xe_peak_probe(int kind, double *tflops, double *aux);
+
 /* Tuning / diagnostic options (process-wide; take effect on the next call):
  *   "operand_bytes"  1 = FP8 e4m3 tensor-core operands (default), 2 = f16 operands;
  *   "exact_chunk_t"  samples summed by one f32 tensor-memory accumulation before the
  *                    partial sum is moved to int32 (64 .. 131072, default 131072);
  *   "n_cta"          persistent CTAs per launch (0 = one per SM, the default);
- *   "sched"          triangle schedule, -1 = automatic (default), 0..3 as in xe_plan_dump;
+ *   "sched"          triangle schedule, -1 = automatic (default), 0..4 as in xe_plan_dump;
  *   "tile_n"         tile width 0 = automatic (default), 128 or 256;
  *   "autotune"       1 = time every (tile width, schedule) candidate the first time a
  *                    batch shape is correlated and keep the fastest for that shape;
@@ -276,6 +286,10 @@ int xe_set_option(const char *key, int64_t value);
  * to it.  Returns XE_OK, or XE_ETIMEOUT if a kernel gave up on a bounded wait (its output
  * is then invalid). */
 int xe_device_status(void *stream);
+
+/* Streaming multiprocessors of the current device, and how many 2-CTA clusters of the
+ * clustered correlation kernel can be resident at once (0 if none).  Returns an XE_* code. */
+int xe_device_info(int *n_sm, int *max_clusters);
 
 /* Bit pattern of the small integer v in [-16, 16] as an MMA operand: e4m3 when
  * elem_bytes == 1, f16 when elem_bytes == 2.  Host-only; for tests of the encoder. */

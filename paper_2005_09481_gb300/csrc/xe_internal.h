@@ -12,6 +12,7 @@ constexpr int kBM = 128;           // inputs i per tile (MMA M)
 constexpr int kBN = 256;           // inputs j per tile (MMA N; 128 on half tiles)
 constexpr int kRowBytes = 64;      // bytes of one operand row per pipeline stage
 constexpr int kStages = 4;         // shared-memory pipeline depth
+constexpr int kPrefetchStages = 8; // L2 prefetch distance of the plane tiles, in stages
 constexpr int kNPad = 256;         // inputs are padded to a multiple of this (zeros)
 constexpr int kAPlane = kBM * kRowBytes;              // 8 KB
 constexpr int kBPlane = kBN * kRowBytes;              // 16 KB
@@ -68,12 +69,16 @@ struct Tile {
     int part_off;             // their workspace slots: tile_slots[part_off .. part_off + n_parts)
 };
 
-// A contiguous k-range of one tile processed by one CTA.
+// A contiguous k-range of one tile processed by one CTA.  In the clustered kernel the two
+// CTAs of a cluster walk segment lists of equal shape in lockstep: `multicast` segments of
+// the pair share their column block (each CTA fetches one B plane for both), and a segment
+// with tile < 0 only keeps the pipeline handshake going for the partner (k_hi - k_lo stages).
 struct Seg {
     int tile;
     int k_lo;
     int k_hi;
     int slot;                 // workspace slot if the segment is partial, else -1
+    int multicast;            // clustered kernel only: 1 = B planes shared with the partner
 };
 
 // Device-resident plan of one persistent launch: CTA b processes segs[seg_off[b] ..
@@ -97,7 +102,8 @@ enum Sched : int {
     kSchedSplit = 1,          // each tile split into s equal k-parts, parts dealt round-robin
     kSchedHybrid = 2,         // whole tiles in full waves, the last partial wave stream-K
     kSchedLPT = 3,            // whole tiles, longest first, to the least-loaded CTA
-    kNumSched = 4,
+    kSchedPairSplit = 4,      // clustered kernel: tile pairs sharing a column block, k-split
+    kNumSched = 5,
 };
 
 constexpr int64_t kWsSlotElems = 2LL * kBN * kBM;  // re and im planes, [col][row] int32
@@ -111,7 +117,9 @@ enum DeviceStatus : int {
 
 // Kernel launchers (xe_tc.cu, xe_imma.cu).
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s);
-cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s);
+cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
+                      bool clustered = false);
+int tc_max_clusters();
 cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
@@ -119,7 +127,7 @@ const void *stage_kernel_fn(int elem_bytes);
 unsigned stage_grid(const JobTable &jt, int elem_bytes);
 int stage_smem_bytes(int elem_bytes);
 cudaError_t stage_prepare();
-const void *tc_kernel_fn(int elem_bytes);
+const void *tc_kernel_fn(int elem_bytes, bool clustered = false);
 const void *imma_kernel_fn();
 cudaError_t tc_prepare();
 

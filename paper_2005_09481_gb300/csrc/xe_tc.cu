@@ -425,9 +425,14 @@ __device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, 
     __syncwarp();
 }
 
-template <int EB>
-__global__ void __launch_bounds__(kTcThreads, 1)
-    tc_kernel(const __grid_constant__ JobTable jt, const __grid_constant__ PlanDev plan) {
+// MC = the clustered variant: the two CTAs of a cluster walk equally shaped segment lists
+// in lockstep; for `multicast` segments CTA rank r fetches B plane r (re or im) of the shared
+// column block for both CTAs, so each CTA reads 2/3 of the B bytes it would read alone.
+// Each CTA's MMA completion for a stage arrives on the stage's `empty` barrier of BOTH CTAs
+// (multicast commit, barrier count 2), so a producer refills a stage -- its own copies and
+// its multicast into the partner -- only after both tensor cores have finished reading it.
+template <int EB, bool MC>
+__device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
         (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -447,7 +452,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], 1);
+            mbar_init(&empty[s], MC ? 2 : 1);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
@@ -461,7 +466,9 @@ __global__ void __launch_bounds__(kTcThreads, 1)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
+    if (MC) cluster_sync();     // the partner's barriers are initialised before any remote use
     const uint32_t tmem = *tmem_slot;
+    const uint32_t rank = MC ? cluster_ctarank() : 0u;   // which B plane this CTA multicasts
 
     // This CTA's work: segments [q0, q1) of the plan, each a k-range of one tile.
     const int q0 = plan.seg_off[blockIdx.x];
@@ -476,9 +483,10 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             int64_t fills = 0;
             bool ok = true;
             // Test hook: issue nothing, so the MMA warp's bounded wait runs out.
-            for (int q = plan.inject_stall ? q1 : q0; ok && q < q1; ++q) {
+            for (int q = (!MC && plan.inject_stall) ? q1 : q0; ok && q < q1; ++q) {
                 const Seg sg = plan.segs[q];
-                const Tile tl = plan.tiles[sg.tile];
+                const bool null_seg = MC && sg.tile < 0;
+                const Tile tl = plan.tiles[null_seg ? 0 : sg.tile];
                 const JobDev &jb = jt.jobs[tl.job];
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
@@ -488,15 +496,36 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                         ok = false;
                         break;
                     }
+                    if (null_seg) {
+                        mbar_arrive(&full[stage]);     // nothing to load: complete the phase
+                        ++fills;
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                        continue;
+                    }
                     mbar_arrive_expect_tx(&full[stage], 2 * kAPlane + 2 * bbytes);
                     uint8_t *st = smem + stage * kStageBytes;
                     const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
                     const uint8_t *pim = pre + int64_t(jb.n_pad) * kRowBytes;
+                    if (k + kPrefetchStages < sg.k_hi) {
+                        // Bring the plane tiles of a later stage into L2 ahead of their copy.
+                        const uint8_t *fre = pre + int64_t(kPrefetchStages) * 2 * jb.n_pad * kRowBytes;
+                        const uint8_t *fim = fre + int64_t(jb.n_pad) * kRowBytes;
+                        bulk_prefetch_l2(fre + int64_t(tl.i0) * kRowBytes, kAPlane);
+                        bulk_prefetch_l2(fim + int64_t(tl.i0) * kRowBytes, kAPlane);
+                        if (!(MC && sg.multicast) || rank == 0) bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
+                        if (!(MC && sg.multicast) || rank == 1) bulk_prefetch_l2(fim + int64_t(tl.j0) * kRowBytes, bbytes);
+                    }
                     bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
                     bulk_g2s(st + kAPlane, pim + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
-                    bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
-                    bulk_g2s(st + 2 * kAPlane + kBPlane, pim + int64_t(tl.j0) * kRowBytes, bbytes,
-                             &full[stage]);
+                    if (MC && sg.multicast) {
+                        // B plane `rank` of the shared column block, into both CTAs.
+                        const uint8_t *pb = (rank == 0 ? pre : pim) + int64_t(tl.j0) * kRowBytes;
+                        bulk_g2s_multicast(st + 2 * kAPlane + rank * kBPlane, pb, bbytes, &full[stage], 0x3);
+                    } else {
+                        bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
+                        bulk_g2s(st + 2 * kAPlane + kBPlane, pim + int64_t(tl.j0) * kRowBytes, bbytes,
+                                 &full[stage]);
+                    }
                     ++fills;
                     if (++stage == kStages) { stage = 0; ph ^= 1u; }
                 }
@@ -522,6 +551,19 @@ __global__ void __launch_bounds__(kTcThreads, 1)
             const uint32_t d_re = tmem, d_im = tmem + 256;
             for (int q = q0; ok && q < q1; ++q) {
                 const Seg sg = plan.segs[q];
+                if (MC && sg.tile < 0) {
+                    // Partner-only segment: pass each stage straight back to the producer.
+                    for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
+                        if (!mbar_wait(&full[stage], ph, status)) {
+                            set_status(plan.status, kStatusTimeoutMma);
+                            ok = false;
+                            break;
+                        }
+                        mma_commit_multicast(&empty[stage], 0x3);
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                    }
+                    continue;
+                }
                 const Tile tl = plan.tiles[sg.tile];
                 const uint32_t idesc = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, false);
                 const uint32_t idesc_neg = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, true);
@@ -560,7 +602,8 @@ __global__ void __launch_bounds__(kTcThreads, 1)
                             mma_f16(d_im, a_re, b_im, idesc_neg, 1u);
                         }
                     }
-                    mma_commit(&empty[stage]);
+                    if (MC) mma_commit_multicast(&empty[stage], 0x3);
+                    else mma_commit(&empty[stage]);
                     if (++stage == kStages) { stage = 0; ph ^= 1u; }
                 }
                 if (ok) mma_commit(acc_full);
@@ -579,6 +622,7 @@ __global__ void __launch_bounds__(kTcThreads, 1)
         const uint32_t lane_base = uint32_t(warp * 32) << 16;
         for (int q = q0; q < q1; ++q) {
             const Seg sg = plan.segs[q];
+            if (MC && sg.tile < 0) continue;      // partner-only segment: nothing to drain
             const Tile tl = plan.tiles[sg.tile];
             const JobDev &jb = jt.jobs[tl.job];
             if (threadIdx.x == 0) {
@@ -665,10 +709,32 @@ __global__ void __launch_bounds__(kTcThreads, 1)
 
     tc_fence_before();
     __syncthreads();
+    if (MC) {
+        // Both CTAs are done with each other's barriers and shared memory before either exits;
+        // after an abort, give multicast copies already in flight time to land.
+        cluster_sync();
+        if (*status != 0) {
+            const long long t0 = clock64();
+            while (clock64() - t0 < 4000000LL) {}
+            cluster_sync();
+        }
+    }
     if (warp == 5) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
     }
+}
+
+template <int EB>
+__global__ void __launch_bounds__(kTcThreads, 1)
+    tc_kernel(const __grid_constant__ JobTable jt, const __grid_constant__ PlanDev plan) {
+    tc_body<EB, false>(jt, plan);
+}
+
+template <int EB>
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
+    tc_mc_kernel(const __grid_constant__ JobTable jt, const __grid_constant__ PlanDev plan) {
+    tc_body<EB, true>(jt, plan);
 }
 
 int tc_smem_bytes() { return kTcSmem; }
@@ -678,7 +744,10 @@ const void *stage_kernel_fn(int elem_bytes) {
                            : reinterpret_cast<const void *>(stage_kernel<2>);
 }
 
-const void *tc_kernel_fn(int elem_bytes) {
+const void *tc_kernel_fn(int elem_bytes, bool clustered) {
+    if (clustered)
+        return elem_bytes == 1 ? reinterpret_cast<const void *>(tc_mc_kernel<1>)
+                               : reinterpret_cast<const void *>(tc_mc_kernel<2>);
     return elem_bytes == 1 ? reinterpret_cast<const void *>(tc_kernel<1>)
                            : reinterpret_cast<const void *>(tc_kernel<2>);
 }
@@ -694,16 +763,54 @@ cudaError_t tc_prepare() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_mc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(tc_mc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
+    if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done_dev[dev] = 1;
     return cudaSuccess;
 }
 
-cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s) {
+// Clusters of two tensor-core CTAs that can be resident at once (0 if the query fails).
+int tc_max_clusters() {
+    static int cached[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
+    if (tc_prepare() != cudaSuccess) return 0;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * 256);
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = kTcSmem;
+    cudaLaunchAttribute attr;
+    attr.id = cudaLaunchAttributeClusterDimension;
+    attr.val.clusterDim.x = 2;
+    attr.val.clusterDim.y = 1;
+    attr.val.clusterDim.z = 1;
+    cfg.attrs = &attr;
+    cfg.numAttrs = 1;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(tc_mc_kernel<1>), &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    if (dev >= 0 && dev < 64) cached[dev] = n;
+    return n;
+}
+
+cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
+                      bool clustered) {
     if (plan.n_cta <= 0 || plan.n_tiles <= 0) return cudaSuccess;
+    if (clustered && (plan.n_cta & 1)) return cudaErrorInvalidValue;
     cudaError_t e = tc_prepare();
     if (e != cudaSuccess) return e;
-    if (elem_bytes == 1) tc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
-    else tc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+    if (clustered) {
+        if (elem_bytes == 1) tc_mc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+        else tc_mc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+    } else {
+        if (elem_bytes == 1) tc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+        else tc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+    }
     return cudaGetLastError();
 }
 
