@@ -72,6 +72,7 @@ struct TuneCfg {
 
 struct HostPlan {
     bool clustered = false;       // segments are laid out for the 2-CTA clustered kernel
+    bool pair_exchange = false;   // every split tile has 2 parts and every CTA 1 segment
     std::vector<Tile> tiles;
     std::vector<Seg> segs;
     std::vector<int> seg_off;     // n_cta + 1 entries
@@ -308,7 +309,14 @@ static bool build_plan(const std::vector<JobShape> &jobs, int eb, const TuneCfg 
     int G = std::max(1, cfg.n_cta);
     if (cfg.sched == kSchedPairSplit) G = std::max(2, G & ~1);
     schedule(p, G, cfg.sched);
-    return finalize_parts(p);
+    if (!finalize_parts(p)) return false;
+    // The symmetric two-part exchange waits for the partner part, so it is used only when
+    // both parts are the only work of their CTAs (all of them resident at once).
+    bool pe = !p.clustered;
+    for (const Tile &t : p.tiles) pe = pe && (t.n_parts == 0 || t.n_parts == 2);
+    for (int b = 0; b < p.n_cta && pe; ++b) pe = p.seg_off[size_t(b) + 1] - p.seg_off[size_t(b)] == 1;
+    p.pair_exchange = pe;
+    return true;
 }
 
 struct DevPlan {
@@ -615,6 +623,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             pd.counters = sc->counters;
             pd.status = sc->status;
             pd.inject_stall = g_opt.inject_stall;
+            // All CTAs of the launch must be resident together for the exchange's wait.
+            pd.pair_exchange = p->host.pair_exchange && p->host.n_cta <= d->n_sm ? 1 : 0;
             out.push_back(st);
             out.push_back(tc);
         }

@@ -94,6 +94,8 @@ struct PlanDev {
     int *counters;            // one arrival counter per tile, zero between launches
     int *status;              // device status word (0 = ok)
     int inject_stall;         // test hook: 1 = the producer issues no copies, so waits time out
+    int pair_exchange;        // 1: every split tile has 2 parts and every CTA one segment, so the
+                              // two parts swap column halves instead of a last-arriver sum
 };
 
 // Triangle schedules (host-side choice; the kernel just follows the segment lists).

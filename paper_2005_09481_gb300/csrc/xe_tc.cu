@@ -649,6 +649,66 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                     }
                     store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + cc, re, im, jt.accumulate | jb.accumulate, epi_stage);
                 }
+            } else if (!MC && plan.pair_exchange) {
+                // Two-part tile, both parts running now on two CTAs: part p finalises column
+                // half p.  Publish my share of the partner's half, count myself in, wait
+                // (bounded) for the partner's share of mine, then add it to my own sums.
+                const int part = sg.k_lo == 0 ? 0 : 1;
+                const int half = tl.nj / 2;
+                const int mine0 = part * half, theirs0 = (1 - part) * half;
+                int32_t *ws = plan.ws + int64_t(sg.slot) * kWsSlotElems;
+                for (int cc = 0; cc < half; cc += 32) {
+                    uint32_t fre[32], fim[32];
+                    tmem_ld_32x32b_x32(tmem + lane_base + theirs0 + cc, fre);
+                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + theirs0 + cc, fim);
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        __stcg(ws + int64_t(cc + k) * kBM + r, __float2int_rn(__uint_as_float(fre[k])));
+                        __stcg(ws + int64_t(kBN + cc + k) * kBM + r, __float2int_rn(__uint_as_float(fim[k])));
+                    }
+                }
+                __threadfence();
+                epi_bar();
+                if (threadIdx.x == 0) {
+                    atomicAdd(&plan.counters[sg.tile], 1);
+                    volatile int *cnt = plan.counters + sg.tile;
+                    const long long t0 = clock64();
+                    bool ok = true;
+                    while (*cnt < 2) {
+                        if (*status != 0 || clock64() - t0 > kWaitBudgetCycles) { ok = false; break; }
+                    }
+                    if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
+                    *epi_flag = ok ? 1 : 0;
+                }
+                epi_bar();
+                if (*epi_flag == 1) {
+                    __threadfence();
+                    const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + (1 - part)]) * kWsSlotElems;
+                    for (int cc = 0; cc < half; cc += 32) {
+                        uint32_t fre[32], fim[32];
+                        tmem_ld_32x32b_x32(tmem + lane_base + mine0 + cc, fre);
+                        tmem_ld_32x32b_x32(tmem + lane_base + 256 + mine0 + cc, fim);
+                        int re[32], im[32];
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            re[k] = __ldcg(w + int64_t(cc + k) * kBM + r);
+                            im[k] = __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
+                        }
+                        tmem_ld_wait();
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) {
+                            re[k] += __float2int_rn(__uint_as_float(fre[k]));
+                            im[k] += __float2int_rn(__uint_as_float(fim[k]));
+                        }
+                        store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + mine0 + cc, re, im,
+                                    jt.accumulate | jb.accumulate, epi_stage);
+                    }
+                    epi_bar();
+                    // Both parts have read each other's share: the second to finish resets the
+                    // counter for the next launch.
+                    if (threadIdx.x == 0 && atomicAdd(&plan.counters[sg.tile], 1) == 3) plan.counters[sg.tile] = 0;
+                }
             } else {
                 // Partial tile: publish this segment's share; the last one to arrive sums all.
                 int32_t *ws = plan.ws + int64_t(sg.slot) * kWsSlotElems;
