@@ -15,9 +15,16 @@ section 2.2; channels independent, section 2.3):
   floating-point rounding can occur in any summation order.  It exists so that full
   outputs at N=2048 can be checked in seconds; tests pin it to the C loop.
 
-Readings where the paper is silent (listed in the design doc as well): high nibble = real,
-low nibble = imaginary, two's complement, conjugate on the second index, row-major
-packed upper triangle with {Re, Im} interleaved.
+Readings where the paper is silent: high nibble = real, low nibble = imaginary, two's
+complement, conjugate on the second index, row-major packed upper triangle with {Re, Im}
+interleaved.
+
+Flag-masked correlation (flags travel with the data, section 2.2 and Table
+tab:data-flow; RFI excision precedes correlation, Table tab:computing):
+``correlate_masked`` / ``flag_counts`` (C loops) and ``correlate_masked_dense`` /
+``flag_counts_dense`` (library matmuls of the masked voltages and of the 0/1 validity
+matrix).  Readings: one validity bit per (sample, input), bit n%8 of byte n/8, 1 = valid;
+a sample counts only where both inputs are valid; offset-binary nibbles encode u - 8.
 """
 from __future__ import annotations
 
@@ -65,6 +72,10 @@ def _load():
             lib.xe_oracle_cmac.argtypes = [i64, i64, i64]
             lib.xe_oracle_cmac.restype = ctypes.c_double
             lib.xe_oracle_threads.restype = ctypes.c_int
+            lib.xe_oracle_correlate_masked.argtypes = [p, p, i64, i64, i64, ctypes.c_int, p]
+            lib.xe_oracle_correlate_masked.restype = ctypes.c_int
+            lib.xe_oracle_flag_counts.argtypes = [p, i64, i64, i64, p]
+            lib.xe_oracle_flag_counts.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -177,3 +188,85 @@ def unpack_triangle(vis: np.ndarray, N: int) -> np.ndarray:
     V[iu] = vis[:, 0] + 1j * vis[:, 1]
     V[(iu[1], iu[0])] = vis[:, 0] - 1j * vis[:, 1]
     return V
+
+
+def correlate_masked(packed: np.ndarray, flags, N: int, T: int, C: int = 1,
+                     encoding: int = 0) -> np.ndarray:
+    """Flag-masked correlation (plain C loop).  flags: uint8 [C][T][ceil(N/8)] validity
+    bits (bit n%8 of byte n/8, 1 = valid) or None; encoding 0 = two's complement nibbles,
+    1 = offset binary.  Returns int32 [C, N(N+1)/2, 2]."""
+    b = _check_in(packed, N, T, C)
+    f = None
+    if flags is not None:
+        f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
+        if f.size != C * T * ((N + 7) // 8):
+            raise ValueError("flags must hold C*T*ceil(N/8) bytes")
+    out = np.empty((C, n_baselines(N), 2), np.int64)
+    rc = _load().xe_oracle_correlate_masked(_ptr(b), None if f is None else _ptr(f), N, T, C,
+                                            encoding, _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_correlate_masked rejected its arguments")
+    return to_int32(out)
+
+
+def flag_counts(flags, N: int, T: int, C: int = 1) -> np.ndarray:
+    """Valid-sample count of every baseline, n_ij = sum_t f_i(t) f_j(t); int64 [C, B]."""
+    f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(-1)
+    if f.size != C * T * ((N + 7) // 8):
+        raise ValueError("flags must hold C*T*ceil(N/8) bytes")
+    out = np.empty((C, n_baselines(N)), np.int64)
+    rc = _load().xe_oracle_flag_counts(_ptr(f), N, T, C, _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_flag_counts rejected its arguments")
+    return out
+
+
+def valid_bits(flags, N: int, T: int, C: int = 1) -> np.ndarray:
+    """Validity bits uint8 [C][T][ceil(N/8)] -> bool [C, T, N] (bit n%8 of byte n/8)."""
+    f = np.ascontiguousarray(flags, dtype=np.uint8).reshape(C, T, (N + 7) // 8)
+    return np.unpackbits(f, axis=2, bitorder="little")[:, :, :N].astype(bool)
+
+
+def correlate_masked_dense(packed: np.ndarray, flags, N: int, T: int, C: int = 1,
+                           encoding: int = 0, t_chunk: int = 4096) -> np.ndarray:
+    """The masked definition as a matrix product: with f in {0, 1},
+    f_i f_j x_i conj(x_j) = (f_i x_i) conj(f_j x_j), so V = Y Y^H with Y = F * X
+    (complex128 library matmul; exact for the same reason as correlate_dense).
+    Offset-binary samples (encoding 1) decode as nibble - 8.  int32 [C, B, 2]."""
+    b = _check_in(packed, N, T, C).reshape(C, T, N)
+    valid = None if flags is None else valid_bits(flags, N, T, C)
+    iu = np.triu_indices(N)
+    out = np.empty((C, n_baselines(N), 2), np.int64)
+    for c in range(C):
+        V = np.zeros((N, N), np.complex128)
+        for t0 in range(0, T, t_chunk):
+            blk = b[c, t0:t0 + t_chunk]
+            if encoding == 1:
+                re = (blk >> 4).astype(np.int64) - 8
+                im = (blk & 0xF).astype(np.int64) - 8
+            else:
+                re, im = decode(blk)
+            Y = (re + 1j * im).astype(np.complex128)
+            if valid is not None:
+                Y = Y * valid[c, t0:t0 + t_chunk]
+            Y = Y.T
+            V += Y @ Y.conj().T
+        tri = V[iu]
+        out[c, :, 0] = np.rint(tri.real).astype(np.int64)
+        out[c, :, 1] = np.rint(tri.imag).astype(np.int64)
+    return to_int32(out)
+
+
+def flag_counts_dense(flags, N: int, T: int, C: int = 1, t_chunk: int = 8192) -> np.ndarray:
+    """Valid-sample counts as the matrix product F^T F of the 0/1 validity matrix (float64
+    library matmul; exact, every partial sum is an integer <= T < 2**53).  int64 [C, B]."""
+    valid = valid_bits(flags, N, T, C)
+    iu = np.triu_indices(N)
+    out = np.empty((C, n_baselines(N)), np.int64)
+    for c in range(C):
+        M = np.zeros((N, N), np.float64)
+        for t0 in range(0, T, t_chunk):
+            F = valid[c, t0:t0 + t_chunk].astype(np.float64)
+            M += F.T @ F
+        out[c] = np.rint(M[iu]).astype(np.int64)
+    return out

@@ -120,6 +120,89 @@ int xe_oracle_pairs(const uint8_t *in, int64_t N, int64_t T, int64_t n,
     return 0;
 }
 
+/*
+ * Flag-masked correlation, optional offset-binary samples.
+ *
+ * Denman et al. 2020, section 2.2 and Table tab:data-flow: the F-engine sends flags and
+ * metadata with the voltages (644 B per 4096 B of data), and RFI excision runs on the GPU
+ * before the correlation (Table tab:computing).  Readings (the paper gives no format):
+ *   (R10) flags are validity bits per (time sample, input): byte t*ceil(N/8) + n/8 of a
+ *         channel, bit n%8; 1 = valid.  A flagged sample contributes nothing, i.e.
+ *         V_ij = sum_t f_i(t) f_j(t) x_i(t) conj(x_j(t));  flags == NULL means all valid.
+ *   (R11) encoding 1 = offset binary: each nibble u encodes the value u - 8 (encoding 0 is
+ *         the two's complement of R2).
+ */
+static void decode_sample_enc(uint8_t byte, int encoding, int64_t *re, int64_t *im)
+{
+    if (encoding == 1) {
+        *re = (int64_t)((byte >> 4) & 0xF) - 8;
+        *im = (int64_t)(byte & 0xF) - 8;
+    } else {
+        decode_sample(byte, re, im);
+    }
+}
+
+static int flag_valid(const uint8_t *chan_flags, int64_t N, int64_t t, int64_t n)
+{
+    if (!chan_flags) return 1;
+    const int64_t row = (N + 7) / 8;
+    return (chan_flags[t * row + n / 8] >> (n % 8)) & 1;
+}
+
+/* in: uint8 [C][T][N]; flags: uint8 [C][T][ceil(N/8)] or NULL; vis: int64 [C][B][2]. */
+int xe_oracle_correlate_masked(const uint8_t *in, const uint8_t *flags, int64_t N, int64_t T,
+                               int64_t C, int encoding, int64_t *vis)
+{
+    if (N < 1 || T < 0 || C < 1 || !in || !vis || (encoding != 0 && encoding != 1))
+        return -1;
+    const int64_t B = xe_oracle_n_baselines(N);
+    const int64_t frow = (N + 7) / 8;
+    for (int64_t c = 0; c < C; ++c) {
+        const uint8_t *chan = in + c * T * N;
+        const uint8_t *cf = flags ? flags + c * T * frow : NULL;
+        int64_t *out = vis + c * B * 2;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < N; ++i) {
+            for (int64_t j = i; j < N; ++j) {
+                int64_t acc_re = 0, acc_im = 0;
+                for (int64_t t = 0; t < T; ++t) {
+                    if (!flag_valid(cf, N, t, i) || !flag_valid(cf, N, t, j)) continue;
+                    int64_t a, b, p, q;
+                    decode_sample_enc(chan[t * N + i], encoding, &a, &b);
+                    decode_sample_enc(chan[t * N + j], encoding, &p, &q);
+                    acc_re += a * p + b * q;
+                    acc_im += b * p - a * q;
+                }
+                int64_t k = xe_oracle_tri_index(N, i, j);
+                out[2 * k + 0] = acc_re;
+                out[2 * k + 1] = acc_im;
+            }
+        }
+    }
+    return 0;
+}
+
+/* Valid-sample counts per baseline: n_ij = sum_t f_i(t) f_j(t); counts int64 [C][B]. */
+int xe_oracle_flag_counts(const uint8_t *flags, int64_t N, int64_t T, int64_t C, int64_t *counts)
+{
+    if (N < 1 || T < 0 || C < 1 || !flags || !counts)
+        return -1;
+    const int64_t B = xe_oracle_n_baselines(N);
+    const int64_t frow = (N + 7) / 8;
+    for (int64_t c = 0; c < C; ++c) {
+        const uint8_t *cf = flags + c * T * frow;
+#pragma omp parallel for schedule(dynamic, 1)
+        for (int64_t i = 0; i < N; ++i)
+            for (int64_t j = i; j < N; ++j) {
+                int64_t n = 0;
+                for (int64_t t = 0; t < T; ++t)
+                    n += flag_valid(cf, N, t, i) & flag_valid(cf, N, t, j);
+                counts[c * B + xe_oracle_tri_index(N, i, j)] = n;
+            }
+    }
+    return 0;
+}
+
 /* Complex multiply-accumulates of one correlation: C * T * N(N+1)/2 (section 2.2). */
 double xe_oracle_cmac(int64_t N, int64_t T, int64_t C)
 {

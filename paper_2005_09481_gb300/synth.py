@@ -89,3 +89,26 @@ def uneven_batch(n_inst: int = 64, seed: int = BASE_SEED, shapes=None) -> list[n
 def constant(N: int, T: int, re: int, im: int, C: int = 1) -> np.ndarray:
     """Every sample equal to re + i im (extreme-magnitude cases)."""
     return np.full((C, T, N), pack(np.array(re), np.array(im)), np.uint8)
+
+
+def flags(N: int, T: int, C: int = 1, p_bad: float = 0.1, seed: int = BASE_SEED,
+          burst: int = 0) -> np.ndarray:
+    """Validity bits uint8 [C][T][ceil(N/8)] (bit n%8 of byte n/8; 1 = valid): each
+    (sample, input) is flagged independently with probability p_bad; with burst > 0, whole
+    time samples are also flagged in runs of `burst` (RFI-like)."""
+    rng = np.random.default_rng(seed + 7919)
+    valid = rng.random((C, T, N)) >= p_bad
+    if burst > 0 and T > 0:
+        starts = rng.integers(0, T, size=max(1, T // (burst * 20)))
+        for c in range(C):
+            for s in starts:
+                valid[c, s:s + burst, :] = False
+    pad = (-N) % 8
+    if pad:
+        valid = np.concatenate([valid, np.zeros((C, T, pad), bool)], axis=2)
+    return np.packbits(valid, axis=2, bitorder="little")
+
+
+def to_offset_binary(packed: np.ndarray) -> np.ndarray:
+    """The same sample values written with offset-binary nibbles (value = nibble - 8)."""
+    return (np.asarray(packed, np.uint8) ^ np.uint8(0x88)).astype(np.uint8)
