@@ -123,6 +123,53 @@ int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stre
  * accumulators (time integration, section 2.1).  The caller keeps |sum| < 2^31. */
 int xe_correlate_accumulate(const xe_job *jobs, int n_jobs, void *stream);
 
+/* ---- flag-masked correlation, offset-binary input --------------------------------- */
+
+/* Flags and metadata travel with the voltages from the F-engine (section 2.2 and Table
+ * tab:data-flow: 644 B per 4096 B of data), and RFI excision runs on the GPU before the
+ * correlation (Table tab:computing).  The paper fixes no flag format; this library takes
+ * one validity bit per (sample, input):
+ *
+ *   flags  uint8 [C][T][ceil(N/8)]  bit (n % 8) of byte (n / 8) of row (c, t) is 1 when
+ *                                   sample t of input n in channel c is valid.
+ *                                   Bits of inputs >= N in the last byte are ignored.
+ *
+ * The masked correlation sums only samples where both inputs are valid,
+ *
+ *     V_ij = sum_t f_i(t) f_j(t) x_i(t) conj(x_j(t)),
+ *     n_ij = sum_t f_i(t) f_j(t)          (valid-sample count of every baseline),
+ *
+ * with counts int32 [C][B] in the same baseline order as vis.  flags == NULL means every
+ * sample is valid.
+ *
+ * Sample encodings: XE_ENC_TWOS = two's-complement nibbles (the format of every other
+ * entry point); XE_ENC_OFFSET = offset binary, nibble u encodes the value u - 8. */
+#define XE_ENC_TWOS   0
+#define XE_ENC_OFFSET 1
+
+typedef struct xe_masked_job {
+    const uint8_t *in;        /* device, [C][T][N] packed samples in `encoding` */
+    const uint8_t *flags;     /* device, validity bits as above, or NULL (all valid) */
+    int32_t *vis;             /* device, [C][B][2]; 8-byte aligned */
+    int32_t *counts;          /* device, [C][B], 4-byte aligned; or NULL (not computed) */
+    int N;
+    int n_chan;
+    int64_t T;
+    int encoding;             /* XE_ENC_TWOS or XE_ENC_OFFSET */
+    int accumulate;           /* 0: overwrite vis (and counts); 1: vis += V, counts += n */
+} xe_masked_job;
+
+/* Masked correlation of every job of the batch (tensor-core path; the counts are a 1-bit
+ * tensor-core contraction of the flags).  jobs[] is a host array read during the call;
+ * all pointers in it are caller-owned device memory.  Enqueued on `stream`, not
+ * synchronised.  Returns XE_OK, XE_EINVAL (bad sizes, null in/vis, unknown encoding,
+ * misaligned vis or counts), XE_EOVERFLOW, XE_ENOMEM, XE_ECUDA or XE_ENODEV. */
+int xe_correlate_masked_batch(const xe_masked_job *jobs, int n_jobs, void *stream);
+
+/* One masked job (see xe_masked_job for the arguments). */
+int xe_correlate_masked(const uint8_t *in, const uint8_t *flags, int N, int64_t T, int n_chan,
+                        int encoding, int32_t *vis, int32_t *counts, int accumulate, void *stream);
+
 /* ---- host-side planning (no GPU needed; exposed for tests and tooling) ------------ */
 
 /* Work plan the persistent scheduler would use for a batch: number of triangle tiles,
@@ -300,6 +347,9 @@ uint32_t xe_debug_operand_code(int v, int elem_bytes);
  * xe_set_timing(1).  Returns XE_OK or XE_EAGAIN if nothing was recorded. */
 int xe_set_timing(int enable);
 int xe_last_timing(float *stage_ms, float *correlate_ms);
+/* As xe_last_timing, plus the device time of the valid-sample count kernels of a masked
+ * call (0 when the call computed no counts). */
+int xe_last_timing_counts(float *stage_ms, float *correlate_ms, float *count_ms);
 
 #ifdef __cplusplus
 }

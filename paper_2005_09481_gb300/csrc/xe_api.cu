@@ -336,7 +336,9 @@ struct Scratch {
     int *counters = nullptr;
     size_t counters_bytes = 0;
     int *status = nullptr;
-    cudaEvent_t ev[3] = {nullptr, nullptr, nullptr};
+    int32_t *cvis = nullptr;      // outputs of the count jobs of masked calls ([C][B][2] each)
+    size_t cvis_bytes = 0;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
 struct HostIO {
@@ -348,11 +350,13 @@ struct HostIO {
 };
 
 struct LaunchRec {
-    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor
+    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor, 3 counts
     int eb;
     bool clustered;               // kind 1: the 2-CTA clustered kernel
+    bool masked;                  // kind 0: the masking variant of the staging kernel
     JobTable jt;
     PlanDev pd;
+    CountDev cd;                  // kind 3
 };
 
 struct GraphRec {
@@ -490,8 +494,10 @@ static int get_scratch(Device *d, cudaStream_t s, Scratch **out) {
     return XE_OK;
 }
 
-static thread_local cudaEvent_t g_last_ev[3] = {nullptr, nullptr, nullptr};
+static thread_local cudaEvent_t g_last_ev[4] = {nullptr, nullptr, nullptr, nullptr};
 static thread_local const int *g_job_acc = nullptr;   // per-job accumulate flags (stream server)
+// Per-job masking of a masked batch (null for plain batches).
+static thread_local const xe_masked_job *g_job_mask = nullptr;
 
 static int check_job(const uint8_t *in, int N, int64_t T, int C, const int32_t *vis) {
     if (!in || !vis) return fail(XE_EINVAL, "null input or output pointer");
@@ -538,7 +544,24 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
         return XE_OK;
     }
     const int eb = g_opt.operand_bytes;
+    if (g_job_mask && eb != 1) return fail(XE_EINVAL, "masked correlation needs 1-byte operands");
     const int64_t wt = g_opt.exact_chunk_t / samples_per_stage(eb) * samples_per_stage(eb);
+    // Outputs of the count jobs (masked jobs that ask for counts), one region per job.
+    std::vector<size_t> cvis_off(size_t(n_jobs), 0);
+    if (g_job_mask) {
+        size_t elems = 0;
+        for (int q = 0; q < n_jobs; ++q) {
+            cvis_off[size_t(q)] = elems;
+            if (g_job_mask[q].counts)
+                elems += size_t(jobs[q].n_chan) * size_t(jobs[q].N) * size_t(jobs[q].N + 1);
+        }
+        if (elems) {
+            int rc = grow(reinterpret_cast<void **>(&sc->cvis), &sc->cvis_bytes, elems * 4, false);
+            if (rc) return rc;
+        }
+    }
+    // A masked group holds at most half the job slots: each job may add its count job.
+    const size_t group = g_job_mask ? size_t(kMaxJobs / 2) : size_t(kMaxJobs);
     int64_t max_T = 0;
     for (int q = 0; q < n_jobs; ++q) max_T = std::max(max_T, jobs[q].T);
     const int64_t n_win = (max_T + wt - 1) / wt;
@@ -546,8 +569,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
         std::vector<int> act;
         for (int q = 0; q < n_jobs; ++q)
             if (jobs[q].T > w * wt) act.push_back(q);
-        for (size_t g0 = 0; g0 < act.size(); g0 += kMaxJobs) {
-            const int ng = int(std::min(act.size() - g0, size_t(kMaxJobs)));
+        for (size_t g0 = 0; g0 < act.size(); g0 += group) {
+            const int ng = int(std::min(act.size() - g0, group));
             std::vector<JobShape> shapes;
             LaunchRec st{};
             st.kind = 0;
@@ -575,17 +598,47 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 jd.plane_chan_bytes = int64_t(jd.kblocks) * 2 * jd.n_pad * kRowBytes;
                 jd.vis_chan_elems = int64_t(j.N) * (j.N + 1);
                 jd.stage_block0 = blocks;
+                if (g_job_mask) {
+                    const xe_masked_job &mj = g_job_mask[act[g0 + size_t(k)]];
+                    jd.mode = kModeMasked | (mj.encoding == XE_ENC_OFFSET ? kModeOffsetBinary : 0);
+                    jd.flags = mj.flags;
+                    st.masked = true;
+                }
                 blocks += int64_t(j.n_chan) * jd.kblocks * (jd.n_pad / 256);
                 plane_off += size_t(jd.plane_chan_bytes) * size_t(j.n_chan);
+            }
+            // Count jobs after every data job, with no staging blocks of their own (their
+            // planes are written by their masked job's staging): their stage_block0 is the
+            // total, so the staging kernel's job search never lands on them.
+            std::vector<int> count_of(size_t(ng), -1);
+            for (int k = 0; k < ng && g_job_mask; ++k) {
+                const int q = act[g0 + size_t(k)];
+                if (!g_job_mask[q].counts) continue;
+                const int idx = jt.n_jobs++;
+                JobDev &cj = jt.jobs[idx];
+                cj = jt.jobs[k];
+                cj.in = nullptr;
+                cj.flags = nullptr;
+                cj.count_planes = nullptr;
+                cj.mode = kModeCount;
+                cj.accumulate = 0;
+                cj.vis = sc->cvis + cvis_off[size_t(q)];
+                cj.stage_block0 = blocks;
+                count_of[size_t(k)] = idx;
+                shapes.push_back(shapes[size_t(k)]);
+                plane_off += size_t(cj.plane_chan_bytes) * size_t(cj.C);
             }
             jt.total_stage_blocks = blocks;
             int rc = grow(reinterpret_cast<void **>(&sc->planes), &sc->planes_bytes, plane_off, false);
             if (rc) return rc;
             size_t off = 0;
-            for (int k = 0; k < ng; ++k) {
+            for (int k = 0; k < jt.n_jobs; ++k) {
                 jt.jobs[k].planes = sc->planes + off;
                 off += size_t(jt.jobs[k].plane_chan_bytes) * size_t(jt.jobs[k].C);
             }
+            for (int k = 0; k < ng; ++k)
+                if (count_of[size_t(k)] >= 0)
+                    jt.jobs[k].count_planes = const_cast<uint8_t *>(jt.jobs[count_of[size_t(k)]].planes);
             TuneCfg cfg;
             if (forced) {
                 cfg = *forced;
@@ -593,6 +646,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 auto it = d->tuned.find(shape_key(shapes, eb));
                 cfg = it != d->tuned.end() ? it->second : heuristic(shapes, eb, d->n_sm);
             }
+            // Count jobs run in the plain kernel only (its producer loads their re slots alone).
+            if (cfg.sched == kSchedPairSplit && jt.n_jobs > ng) cfg.sched = kSchedSplit;
             if (cfg.sched == kSchedPairSplit) {
                 const int mc = tc_max_clusters();
                 if (mc <= 0) cfg.sched = kSchedSplit;              // clusters unavailable
@@ -629,12 +684,27 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             out.push_back(tc);
         }
     }
+    if (g_job_mask) {
+        for (int q = 0; q < n_jobs; ++q) {
+            const xe_masked_job &mj = g_job_mask[q];
+            if (!mj.counts) continue;
+            LaunchRec cr{};
+            cr.kind = 3;
+            CountDev &cd = cr.cd;
+            cd.src = sc->cvis + cvis_off[size_t(q)];
+            cd.counts = mj.counts;
+            cd.n = int64_t(jobs[q].n_chan) * (int64_t(jobs[q].N) * (jobs[q].N + 1) / 2);
+            cd.accumulate = mj.accumulate ? 1 : 0;
+            out.push_back(cr);
+        }
+    }
     return XE_OK;
 }
 
 static cudaError_t enqueue(const LaunchRec &r, cudaStream_t s) {
-    if (r.kind == 0) return launch_stage(r.jt, r.eb, s);
+    if (r.kind == 0) return launch_stage(r.jt, r.eb, s, r.masked);
     if (r.kind == 1) return launch_tc(r.jt, r.pd, r.eb, s, r.clustered);
+    if (r.kind == 3) return launch_counts(r.cd, s);
     return launch_imma(r.jt, s);
 }
 
@@ -645,10 +715,10 @@ static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
     p.kernelParams = args;
     p.extra = nullptr;
     if (r.kind == 0) {
-        p.func = const_cast<void *>(stage_kernel_fn(r.eb));
-        p.gridDim = dim3(stage_grid(r.jt, r.eb));
+        p.func = const_cast<void *>(stage_kernel_fn(r.eb, r.masked));
+        p.gridDim = dim3(stage_grid(r.jt, r.eb, r.masked));
         p.blockDim = dim3(256);
-        p.sharedMemBytes = unsigned(stage_smem_bytes(r.eb));
+        p.sharedMemBytes = unsigned(stage_smem_bytes(r.eb, r.masked));
     } else if (r.kind == 1) {
         p.func = const_cast<void *>(tc_kernel_fn(r.eb, r.clustered));
         p.gridDim = dim3(unsigned(r.pd.n_cta));
@@ -725,7 +795,8 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
     Scratch *sc = nullptr;
     rc = get_scratch(d, s, &sc);
     if (rc) return rc;
-    if (algo == XE_ALGO_TC && g_opt.autotune && !accumulate) {
+    // Candidates overwrite the jobs' outputs, so calls that add into any output never tune.
+    if (algo == XE_ALGO_TC && g_opt.autotune && !accumulate && !g_job_acc) {
         rc = autotune(d, sc, jobs, n_jobs, s);
         if (rc) return rc;
     }
@@ -736,7 +807,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
     const bool timing = g_opt.timing != 0;
     if (timing) XE_CUDA(cudaEventRecord(sc->ev[0], s));
 
-    if (use_graph && algo == XE_ALGO_TC) {
+    if (use_graph && algo == XE_ALGO_TC && !g_job_mask) {
         // One CUDA graph per (stream, batch shape, launch geometry); the kernel arguments
         // (pointers) are refreshed in place on every replay.
         std::vector<int64_t> key{reinterpret_cast<int64_t>(s), accumulate};
@@ -779,20 +850,26 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
         }
         if (timing) XE_CUDA(cudaEventRecord(sc->ev[1], s));
         XE_CUDA(cudaGraphLaunch(g->exec, s));
+        if (timing) XE_CUDA(cudaEventRecord(sc->ev[2], s));
     } else {
-        bool marked = false;
+        bool marked = false, counted = false;
         for (const LaunchRec &r : recs) {
             if (timing && !marked && r.kind != 0) {
                 XE_CUDA(cudaEventRecord(sc->ev[1], s));   // staging done (or none)
                 marked = true;
             }
+            if (timing && !counted && r.kind == 3) {
+                XE_CUDA(cudaEventRecord(sc->ev[2], s));   // correlation done, counts follow
+                counted = true;
+            }
             XE_CUDA(enqueue(r, s));
         }
         if (timing && !marked) XE_CUDA(cudaEventRecord(sc->ev[1], s));
+        if (timing && !counted) XE_CUDA(cudaEventRecord(sc->ev[2], s));
     }
     if (timing) {
-        XE_CUDA(cudaEventRecord(sc->ev[2], s));
-        for (int k = 0; k < 3; ++k) g_last_ev[k] = sc->ev[k];
+        XE_CUDA(cudaEventRecord(sc->ev[3], s));
+        for (int k = 0; k < 4; ++k) g_last_ev[k] = sc->ev[k];
     }
     return XE_OK;
 }
@@ -895,14 +972,20 @@ int xe_set_option(const char *key, int64_t value) {
 int xe_set_timing(int enable) { return xe_set_option("timing", enable); }
 
 int xe_last_timing(float *stage_ms, float *correlate_ms) {
+    return xe_last_timing_counts(stage_ms, correlate_ms, nullptr);
+}
+
+int xe_last_timing_counts(float *stage_ms, float *correlate_ms, float *count_ms) {
     if (!g_last_ev[0]) return XE_EAGAIN;
-    cudaError_t e = cudaEventSynchronize(g_last_ev[2]);
+    cudaError_t e = cudaEventSynchronize(g_last_ev[3]);
     if (e != cudaSuccess) return fail(XE_ECUDA, "event sync: %s", cudaGetErrorString(e));
-    float a = 0, b = 0;
+    float a = 0, b = 0, c = 0;
     cudaEventElapsedTime(&a, g_last_ev[0], g_last_ev[1]);
     cudaEventElapsedTime(&b, g_last_ev[1], g_last_ev[2]);
+    cudaEventElapsedTime(&c, g_last_ev[2], g_last_ev[3]);
     if (stage_ms) *stage_ms = a;
     if (correlate_ms) *correlate_ms = b;
+    if (count_ms) *count_ms = c;
     return XE_OK;
 }
 
@@ -974,6 +1057,36 @@ int xe_correlate_accumulate(const xe_job *jobs, int n_jobs, void *stream) {
     }
     std::lock_guard<std::mutex> lk(g_mu);
     return run_jobs(jobs, n_jobs, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream), 1, 0);
+}
+
+int xe_correlate_masked_batch(const xe_masked_job *jobs, int n_jobs, void *stream) {
+    if (!jobs || n_jobs < 1) return fail(XE_EINVAL, "empty batch");
+    std::vector<xe_job> plain(static_cast<size_t>(n_jobs));
+    std::vector<int> acc(static_cast<size_t>(n_jobs));
+    for (int q = 0; q < n_jobs; ++q) {
+        const xe_masked_job &m = jobs[q];
+        int rc = check_job(m.in, m.N, m.T, m.n_chan, m.vis);
+        if (rc) return rc;
+        if (m.encoding != XE_ENC_TWOS && m.encoding != XE_ENC_OFFSET)
+            return fail(XE_EINVAL, "job %d: unknown encoding %d", q, m.encoding);
+        if (m.counts && (reinterpret_cast<uintptr_t>(m.counts) & 3))
+            return fail(XE_EINVAL, "job %d: counts must be 4-byte aligned", q);
+        plain[size_t(q)] = xe_job{m.in, m.vis, m.N, m.n_chan, m.T};
+        acc[size_t(q)] = m.accumulate ? 1 : 0;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_job_mask = jobs;
+    g_job_acc = acc.data();
+    const int rc = run_jobs(plain.data(), n_jobs, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream), 0, 0);
+    g_job_acc = nullptr;
+    g_job_mask = nullptr;
+    return rc;
+}
+
+int xe_correlate_masked(const uint8_t *in, const uint8_t *flags, int N, int64_t T, int n_chan,
+                        int encoding, int32_t *vis, int32_t *counts, int accumulate, void *stream) {
+    xe_masked_job j{in, flags, vis, counts, N, n_chan, T, encoding, accumulate};
+    return xe_correlate_masked_batch(&j, 1, stream);
 }
 
 int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,

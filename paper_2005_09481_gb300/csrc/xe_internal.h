@@ -47,14 +47,40 @@ struct JobDev {
     int C;
     int kblocks;              // ceil(T / samples_per_stage)
     int accumulate;           // 1: this job adds into vis (vis += V) even if the launch overwrites
+    int mode;                 // kModeMasked | kModeOffsetBinary bits (masked staging only)
     int64_t stage_block0;     // first block of this job in the stage (or anchor) grid
+    const uint8_t *flags;     // validity bits [C][T_in][ceil(N/8)] (bit n%8 of byte n/8,
+                              // 1 = valid), or null = every sample valid
+    uint8_t *count_planes;    // masked job with counts: where the staging kernel writes the
+                              // validity planes of its count job (same layout as `planes`,
+                              // re slots only), else null
 };
+
+// JobDev::mode bits.  A masked job is staged by the masking variant of the staging kernel:
+// each sample byte becomes (byte ^ key) & valid, where key = 0x88 for offset-binary input
+// (nibble u encodes u - 8; XOR with 8 gives the two's-complement nibble of the same value)
+// and valid = 0xFF if the sample's flag bit is set and it lies inside [0,T) x [0,N).
+// A count job correlates the 0/1 validity planes written by its masked job: only the re
+// plane slots are loaded and one MMA per K step accumulates F_I F_J^T (the Re output is the
+// valid-sample count n_ij; the Im output of a count job is meaningless and never read).
+constexpr int kModeMasked = 1;
+constexpr int kModeOffsetBinary = 2;
+constexpr int kModeCount = 4;
 
 struct JobTable {
     int n_jobs;
     int accumulate;           // 1: add into vis instead of overwriting
     int64_t total_stage_blocks;
     JobDev jobs[kMaxJobs];
+};
+
+// Valid-sample counts of one masked job: counts[e] (+)= src[2e], e < n (the Re part of its
+// count job's output).
+struct CountDev {
+    const int32_t *src;       // count job output [C][B][2]
+    int32_t *counts;          // [C][B]
+    int64_t n;                // C * B
+    int accumulate;           // 1: counts += n_ij
 };
 
 // One output tile of the triangle: rows [i0, i0+128), columns [j0, j0+nj).
@@ -117,17 +143,19 @@ enum DeviceStatus : int {
     kStatusTimeoutEpilogue = 3,
 };
 
-// Kernel launchers (xe_tc.cu, xe_imma.cu).
-cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s);
+// Kernel launchers (xe_tc.cu, xe_imma.cu, xe_mask.cu).  `masked` selects the masking
+// variant of the e4m3 staging kernel (any job with kModeMasked).
+cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s, bool masked = false);
+cudaError_t launch_counts(const CountDev &cd, cudaStream_t s);
 cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
                       bool clustered = false);
 int tc_max_clusters();
 cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
-const void *stage_kernel_fn(int elem_bytes);
-unsigned stage_grid(const JobTable &jt, int elem_bytes);
-int stage_smem_bytes(int elem_bytes);
+const void *stage_kernel_fn(int elem_bytes, bool masked = false);
+unsigned stage_grid(const JobTable &jt, int elem_bytes, bool masked = false);
+int stage_smem_bytes(int elem_bytes, bool masked = false);
 cudaError_t stage_prepare();
 const void *tc_kernel_fn(int elem_bytes, bool clustered = false);
 const void *imma_kernel_fn();
@@ -144,5 +172,9 @@ int record_error(int code, const char *msg);
 
 // Host encoders of a small integer as an MMA operand (e4m3 for 1 byte, f16 for 2 bytes).
 uint32_t operand_code(int v, int elem_bytes);
+
+// Every kernel takes its JobTable (and PlanDev) by value: keep them within the 32764-byte
+// kernel parameter limit.
+static_assert(sizeof(JobTable) + sizeof(PlanDev) <= 32000, "kernel parameters too large");
 
 }  // namespace xe

@@ -236,14 +236,39 @@ constexpr int kRawStride = 288;
 __device__ __forceinline__ int raw_row(int t) { return 4 * (t & 15) + (t >> 4); }
 
 constexpr int kStageSmem = 3 * 64 * kRawStride;   // three packed input tiles (dynamic smem)
+// The masking variant also rings the validity bits of each tile: 64 rows x 32 bytes
+// (256 inputs), rows in the same permuted order as the packed tile.
+constexpr int kFlagRowBytes = 32;
+constexpr int kStageSmemMasked = kStageSmem + 3 * 64 * kFlagRowBytes;
+constexpr int kStageBlocksPerSmMasked = 3;
 
+// Four validity bits (inputs 4g..4g+3) -> a byte mask (bit k -> 0xFF in byte k).  The
+// multiply moves bit k to bit 8k (k <= 3, no carries), the AND keeps those bits.
+__device__ __forceinline__ uint32_t byte_mask_of_nibble(uint32_t nib) {
+    return ((nib * 0x00204081u) & 0x01010101u) * 0xFFu;
+}
+
+// MASK = false: the plain conversion.  MASK = true (jobs with kModeMasked): every sample
+// byte b becomes (b ^ key) & valid (offset-binary key 0x88; valid from the job's flag bits
+// and the [0,T) x [0,N) range), and if the job asks for counts the validity itself is also
+// written as an operand plane (e4m3 1.0 or 0) for its count job.
+template <bool MASK>
 __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__ JobTable jt) {
     constexpr int KS = 64;
     extern __shared__ __align__(16) uint8_t stage_smem[];
     auto raw = reinterpret_cast<uint8_t (*)[KS][kRawStride]>(stage_smem);
+    auto fl = reinterpret_cast<uint8_t (*)[KS][kFlagRowBytes]>(stage_smem + kStageSmem);
     const int tid = threadIdx.x;
     const int64_t total = jt.total_stage_blocks;
 
+    auto vec_ok = [&](const JobDev &jb) {
+        return (jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0;
+    };
+    // Flag rows can be copied 16 bytes at a time when every row starts 16-byte aligned.
+    auto flag_vec_ok = [&](const JobDev &jb) {
+        const int64_t frow = (jb.N + 7) / 8;
+        return (frow & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.flags) & 15) == 0;
+    };
     // Issue the loads of one item into buffer b (vector path: N % 16 == 0, aligned input).
     auto issue = [&](int64_t blk, int b) {
         const StageItem it = stage_item(jt, blk);
@@ -259,9 +284,19 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
             cp_async16(&raw[b][raw_row(r)][seg * 16], ok ? static_cast<const void *>(src + t * jb.N + n)
                                                  : static_cast<const void *>(jb.in), ok ? 16u : 0u);
         }
-    };
-    auto vec_ok = [&](const JobDev &jb) {
-        return (jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0;
+        if (MASK && jb.flags && flag_vec_ok(jb) && tid < 128) {
+            // Row r, 16-byte half h of the tile's 32 flag bytes; bytes past the end of the
+            // flag row are not read (zero-filled), rows past T are zero.
+            const int r = tid >> 1, h = tid & 1;
+            const int64_t frow = (jb.N + 7) / 8;
+            const int64_t t = int64_t(it.kb) * KS + r;
+            const int64_t byte0 = it.n0 / 8 + 16 * h;
+            const int64_t left = frow - byte0;
+            const uint32_t nbytes = (t < jb.T && left > 0) ? uint32_t(left < 16 ? left : 16) : 0u;
+            const uint8_t *fsrc = jb.flags + (int64_t(it.c) * jb.T_in + jb.t0 + t) * frow + byte0;
+            cp_async16(&fl[b][raw_row(r)][16 * h], nbytes ? static_cast<const void *>(fsrc)
+                                                          : static_cast<const void *>(jb.flags), nbytes);
+        }
     };
 
     // Three buffers: the tiles of the next two items are in flight while one is converted.
@@ -287,6 +322,18 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
                 raw[b][raw_row(r)][tid] = (t < jb.T && n < jb.N) ? src[t * jb.N + n] : uint8_t(0);
             }
         }
+        if (MASK && jb.flags && !(vec_ok(jb) && flag_vec_ok(jb))) {
+            // Scalar flag loads: 64 rows x 32 bytes, zero outside the row and past T.
+            const int64_t frow = (jb.N + 7) / 8;
+            for (int idx = tid; idx < KS * kFlagRowBytes; idx += 256) {
+                const int r = idx / kFlagRowBytes, col = idx % kFlagRowBytes;
+                const int64_t t = int64_t(it.kb) * KS + r;
+                const int64_t byte = it.n0 / 8 + col;
+                fl[b][raw_row(r)][col] =
+                    (t < jb.T && byte < frow)
+                        ? jb.flags[(int64_t(it.c) * jb.T_in + jb.t0 + t) * frow + byte] : uint8_t(0);
+            }
+        }
         cp_async_wait2();
         __syncthreads();
 
@@ -296,13 +343,34 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
         // Lane l of warp w: input group g = 8w + l/4 (inputs 4g..4g+3), 16-sample chunk q = l%4;
         // the four lanes of a group write the four chunks of a row together (full sectors).
         const int g = (tid >> 5) * 8 + ((tid & 31) >> 2), q = tid & 3;
+        // Masking: key, and the validity of inputs 4g..4g+3 inside [0, N).
+        uint32_t key = 0, range_nib = 0xFu;
+        bool use_flags = false;
+        uint32_t vbits[4] = {0u, 0u, 0u, 0u};   // [input]: validity of this lane's 16 samples
+                                                // (bit 4 kk + r = sample 16 q + 4 kk + r)
+        if (MASK) {
+            key = (jb.mode & kModeOffsetBinary) ? 0x88888888u : 0u;
+            const int left = jb.N - (it.n0 + 4 * g);
+            range_nib = left >= 4 ? 0xFu : left > 0 ? (1u << left) - 1u : 0u;
+            use_flags = jb.flags != nullptr;
+        }
         uint32_t re[4][4], im[4][4];
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
             uint32_t w[4];
 #pragma unroll
-            for (int r = 0; r < 4; ++r)
-                w[r] = *reinterpret_cast<const uint32_t *>(&raw[b][raw_row(q * 16 + kk * 4 + r)][4 * g]);
+            for (int r = 0; r < 4; ++r) {
+                const int tl = q * 16 + kk * 4 + r;
+                w[r] = *reinterpret_cast<const uint32_t *>(&raw[b][raw_row(tl)][4 * g]);
+                if (MASK) {
+                    uint32_t nib = (int64_t(it.kb) * KS + tl < jb.T) ? range_nib : 0u;
+                    if (use_flags) nib &= uint32_t(fl[b][raw_row(tl)][g >> 1]) >> ((g & 1) * 4);
+                    nib &= 0xFu;
+                    w[r] = (w[r] ^ key) & byte_mask_of_nibble(nib);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) vbits[i] |= ((nib >> i) & 1u) << (kk * 4 + r);
+                }
+            }
             const uint32_t a = __byte_perm(w[0], w[1], 0x5140), bb = __byte_perm(w[2], w[3], 0x5140);
             const uint32_t cc = __byte_perm(w[0], w[1], 0x7362), d = __byte_perm(w[2], w[3], 0x7362);
             const uint32_t v[4] = {__byte_perm(a, bb, 0x5410), __byte_perm(a, bb, 0x7632),
@@ -319,6 +387,22 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
             uint8_t *pre = plane0 + int64_t(row) * kRowBytes + ((q ^ ((row >> 1) & 3)) << 4);
             *reinterpret_cast<uint4 *>(pre) = make_uint4(re[i][0], re[i][1], re[i][2], re[i][3]);
             *reinterpret_cast<uint4 *>(pre + im_off) = make_uint4(im[i][0], im[i][1], im[i][2], im[i][3]);
+        }
+        if (MASK && jb.count_planes) {
+            // Validity plane of the count job: the same rows, chunks and swizzle as the re
+            // plane above, one e4m3 byte per sample (0x38 = 1.0 where valid, else 0).
+            uint8_t *cplane0 = jb.count_planes + int64_t(it.c) * jb.plane_chan_bytes +
+                               (int64_t(it.kb) * 2 * jb.n_pad + it.n0) * kRowBytes;
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const int row = 4 * g + i;
+                uint32_t wv[4];
+#pragma unroll
+                for (int kk = 0; kk < 4; ++kk)
+                    wv[kk] = byte_mask_of_nibble((vbits[i] >> (4 * kk)) & 0xFu) & 0x38383838u;
+                uint8_t *pc = cplane0 + int64_t(row) * kRowBytes + ((q ^ ((row >> 1) & 3)) << 4);
+                *reinterpret_cast<uint4 *>(pc) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+            }
         }
         __syncthreads();   // raw[b] is refilled by the next iteration's prefetch
         b = b == 2 ? 0 : b + 1;
@@ -338,13 +422,15 @@ static int sm_count() {
 }
 
 // Grid of the staging launch (also used when the launch is placed in a CUDA graph).
-unsigned stage_grid(const JobTable &jt, int elem_bytes) {
+unsigned stage_grid(const JobTable &jt, int elem_bytes, bool masked) {
     if (elem_bytes == 2) return unsigned(jt.total_stage_blocks);
-    const int64_t cap = int64_t(sm_count()) * kStageBlocksPerSm;
+    const int64_t cap = int64_t(sm_count()) * (masked ? kStageBlocksPerSmMasked : kStageBlocksPerSm);
     return unsigned(jt.total_stage_blocks < cap ? jt.total_stage_blocks : cap);
 }
 
-int stage_smem_bytes(int elem_bytes) { return elem_bytes == 1 ? kStageSmem : 0; }
+int stage_smem_bytes(int elem_bytes, bool masked) {
+    return elem_bytes == 1 ? (masked ? kStageSmemMasked : kStageSmem) : 0;
+}
 
 cudaError_t stage_prepare() {
     static int done_dev[64] = {0};
@@ -352,20 +438,27 @@ cudaError_t stage_prepare() {
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64 && done_dev[dev]) return cudaSuccess;
-    e = cudaFuncSetAttribute(stage_e4m3_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem);
+    e = cudaFuncSetAttribute(stage_e4m3_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStageSmem);
+    if (e != cudaSuccess) return e;
+    e = cudaFuncSetAttribute(stage_e4m3_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             kStageSmemMasked);
     if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done_dev[dev] = 1;
     return cudaSuccess;
 }
 
-cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s) {
+cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s, bool masked) {
     if (jt.total_stage_blocks <= 0) return cudaSuccess;
     if (jt.total_stage_blocks > 0x7fffffffLL) return cudaErrorInvalidValue;
-    const dim3 grid(stage_grid(jt, elem_bytes));
+    if (masked && elem_bytes != 1) return cudaErrorInvalidValue;
+    const dim3 grid(stage_grid(jt, elem_bytes, masked));
     if (elem_bytes == 1) {
         cudaError_t e = stage_prepare();
         if (e != cudaSuccess) return e;
-        stage_e4m3_kernel<<<grid, 256, kStageSmem, s>>>(jt);
+        if (masked)
+            stage_e4m3_kernel<true><<<grid, 256, kStageSmemMasked, s>>>(jt);
+        else
+            stage_e4m3_kernel<false><<<grid, 256, kStageSmem, s>>>(jt);
     } else {
         stage_kernel<2><<<grid, 256, 0, s>>>(jt);
     }
@@ -490,6 +583,8 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 const JobDev &jb = jt.jobs[tl.job];
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
+                // Count job (plain kernel only): the re plane slots alone.
+                const bool re_only = !MC && (jb.mode & kModeCount);
                 for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
                         set_status(plan.status, kStatusTimeoutProducer);
@@ -502,10 +597,23 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                         if (++stage == kStages) { stage = 0; ph ^= 1u; }
                         continue;
                     }
-                    mbar_arrive_expect_tx(&full[stage], 2 * kAPlane + 2 * bbytes);
                     uint8_t *st = smem + stage * kStageBytes;
                     const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
                     const uint8_t *pim = pre + int64_t(jb.n_pad) * kRowBytes;
+                    if (re_only) {
+                        mbar_arrive_expect_tx(&full[stage], kAPlane + bbytes);
+                        if (k + kPrefetchStages < sg.k_hi) {
+                            const uint8_t *fre = pre + int64_t(kPrefetchStages) * 2 * jb.n_pad * kRowBytes;
+                            bulk_prefetch_l2(fre + int64_t(tl.i0) * kRowBytes, kAPlane);
+                            bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
+                        }
+                        bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
+                        bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
+                        ++fills;
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                        continue;
+                    }
+                    mbar_arrive_expect_tx(&full[stage], 2 * kAPlane + 2 * bbytes);
                     if (k + kPrefetchStages < sg.k_hi) {
                         // Bring the plane tiles of a later stage into L2 ahead of their copy.
                         const uint8_t *fre = pre + int64_t(kPrefetchStages) * 2 * jb.n_pad * kRowBytes;
@@ -565,6 +673,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                     continue;
                 }
                 const Tile tl = plan.tiles[sg.tile];
+                const bool re_only = !MC && (jt.jobs[tl.job].mode & kModeCount);
                 const uint32_t idesc = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, false);
                 const uint32_t idesc_neg = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, true);
                 if (!mbar_wait(acc_empty, acc_ph ^ 1u, status)) {
@@ -590,7 +699,10 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                         const uint64_t b_re = sdesc_k_sw64(base + 2 * kAPlane + off);
                         const uint64_t b_im = sdesc_k_sw64(base + 2 * kAPlane + kBPlane + off);
                         const uint32_t acc = (k > sg.k_lo || s > 0) ? 1u : 0u;
-                        if (EB == 1) {
+                        if (re_only) {
+                            if (EB == 1) mma_f8f6f4(d_re, a_re, b_re, idesc, acc);   // + F_I F_J^T
+                            else mma_f16(d_re, a_re, b_re, idesc, acc);
+                        } else if (EB == 1) {
                             mma_f8f6f4(d_re, a_re, b_re, idesc, acc);      // + A_I A_J^T
                             mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);       // + B_I B_J^T
                             mma_f8f6f4(d_im, a_im, b_re, idesc, acc);      // + B_I A_J^T
@@ -799,9 +911,11 @@ __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
 
 int tc_smem_bytes() { return kTcSmem; }
 
-const void *stage_kernel_fn(int elem_bytes) {
-    return elem_bytes == 1 ? reinterpret_cast<const void *>(stage_e4m3_kernel)
-                           : reinterpret_cast<const void *>(stage_kernel<2>);
+const void *stage_kernel_fn(int elem_bytes, bool masked) {
+    if (elem_bytes == 1)
+        return masked ? reinterpret_cast<const void *>(stage_e4m3_kernel<true>)
+                      : reinterpret_cast<const void *>(stage_e4m3_kernel<false>);
+    return reinterpret_cast<const void *>(stage_kernel<2>);
 }
 
 const void *tc_kernel_fn(int elem_bytes, bool clustered) {

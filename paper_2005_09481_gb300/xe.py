@@ -33,6 +33,15 @@ class Job(ctypes.Structure):
                 ("n_chan", ctypes.c_int), ("T", ctypes.c_int64)]
 
 
+class MaskedJob(ctypes.Structure):
+    _fields_ = [("in_", ctypes.c_void_p), ("flags", ctypes.c_void_p), ("vis", ctypes.c_void_p),
+                ("counts", ctypes.c_void_p), ("N", ctypes.c_int), ("n_chan", ctypes.c_int),
+                ("T", ctypes.c_int64), ("encoding", ctypes.c_int), ("accumulate", ctypes.c_int)]
+
+
+ENCODINGS = {"twos": 0, "offset": 1}
+
+
 def lib_path() -> str:
     return _build.LIB
 
@@ -61,6 +70,9 @@ def load():
             "xe_set_option": ([ctypes.c_char_p, i64], i32),
             "xe_set_timing": ([i32], i32),
             "xe_last_timing": ([p, p], i32),
+            "xe_last_timing_counts": ([p, p, p], i32),
+            "xe_correlate_masked": ([p, p, i32, i64, i32, i32, p, p, i32, p], i32),
+            "xe_correlate_masked_batch": ([p, i32, p], i32),
             "xe_device_status": ([p], i32),
             "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
             "xe_plan_dump": ([p, p, p, i32, i32, i32, i32, p, i64], i64),
@@ -122,6 +134,14 @@ def last_timing() -> tuple[float, float]:
     return a.value, b.value
 
 
+def last_timing_counts() -> tuple[float, float, float]:
+    """(stage, correlate, counts) device milliseconds of the last call on this thread."""
+    a, b, c = ctypes.c_float(), ctypes.c_float(), ctypes.c_float()
+    _check(load().xe_last_timing_counts(ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)),
+           "xe_last_timing_counts")
+    return a.value, b.value, c.value
+
+
 def device_status(stream=None):
     _check(load().xe_device_status(_stream_handle(stream)), "xe_device_status")
 
@@ -130,7 +150,8 @@ def peak_probe(kind: str, with_aux: bool = False):
     """Measured dense TFLOP/s of 'tc_fp8' (tcgen05 e4m3), 'imma_s8' (mma.sync int8) or
     'tc_fp8_fill' (tcgen05 e4m3 with concurrent shared-memory fills; aux = fill GB/s)."""
     out, aux = ctypes.c_double(), ctypes.c_double(0.0)
-    _check(load().xe_peak_probe({"tc_fp8": 0, "imma_s8": 1, "tc_fp8_fill": 2, "tc_fp8_fill_l2": 3}[kind], ctypes.byref(out),
+    _check(load().xe_peak_probe({"tc_fp8": 0, "imma_s8": 1, "tc_fp8_fill": 2, "tc_fp8_fill_l2": 3}[kind],
+                                ctypes.byref(out),
                                 ctypes.byref(aux)), "xe_peak_probe")
     return (out.value, aux.value) if with_aux else out.value
 
@@ -265,6 +286,67 @@ def correlate_noalloc(inp, N: int, T: int, C: int = 1, out=None, stream=None):
                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(rc, "xe_correlate_noalloc")
     return out
+
+
+def flag_bytes(N: int) -> int:
+    """Bytes of one sample row of validity bits (one bit per input)."""
+    return (N + 7) // 8
+
+
+def empty_counts(N: int, C: int = 1, device="cuda"):
+    import torch
+    return torch.empty((C, n_baselines(N)), dtype=torch.int32, device=device)
+
+
+def _flags_shape(flags, N, T, C):
+    import torch
+    if flags is None:
+        return
+    if flags.dtype != torch.uint8 or not flags.is_contiguous() or not flags.is_cuda:
+        raise ValueError("flags must be a contiguous uint8 CUDA tensor")
+    if flags.numel() != C * T * flag_bytes(N):
+        raise ValueError(f"flags has {flags.numel()} bytes, expected C*T*ceil(N/8) = "
+                         f"{C * T * flag_bytes(N)}")
+
+
+def correlate_masked(inp, flags, N: int, T: int, C: int = 1, encoding: str = "twos",
+                     out=None, counts=None, with_counts: bool = True, accumulate: bool = False,
+                     stream=None):
+    """Flag-masked correlation: V_ij = sum_t f_i(t) f_j(t) x_i(t) conj(x_j(t)) and the
+    valid-sample counts n_ij.  flags: uint8 [C, T, ceil(N/8)] validity bits or None (all
+    valid); encoding 'twos' or 'offset'.  Returns (vis, counts or None)."""
+    _shape(inp, N, T, C)
+    _flags_shape(flags, N, T, C)
+    if out is None:
+        out = empty_vis(N, C, inp.device)
+    if with_counts and counts is None:
+        counts = empty_counts(N, C, inp.device)
+    if not with_counts:
+        counts = None
+    rc = load().xe_correlate_masked(
+        ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(flags.data_ptr() if flags is not None else 0),
+        N, T, C, ENCODINGS[encoding], ctypes.c_void_p(out.data_ptr()),
+        ctypes.c_void_p(counts.data_ptr() if counts is not None else 0), 1 if accumulate else 0,
+        _stream_handle(stream))
+    _check(rc, "xe_correlate_masked")
+    return out, counts
+
+
+def correlate_masked_batch(jobs, stream=None):
+    """jobs: list of dicts with keys in, flags (or None), vis, counts (or None), N, T, C,
+    encoding ('twos'/'offset'), accumulate (bool).  One staging + one correlation launch."""
+    arr = (MaskedJob * len(jobs))()
+    for k, j in enumerate(jobs):
+        _shape(j["in"], j["N"], j["T"], j["C"])
+        _flags_shape(j.get("flags"), j["N"], j["T"], j["C"])
+        f, c = j.get("flags"), j.get("counts")
+        arr[k] = MaskedJob(j["in"].data_ptr(), f.data_ptr() if f is not None else None,
+                           j["vis"].data_ptr(), c.data_ptr() if c is not None else None,
+                           j["N"], j["C"], j["T"], ENCODINGS[j.get("encoding", "twos")],
+                           1 if j.get("accumulate") else 0)
+    _check(load().xe_correlate_masked_batch(arr, len(jobs), _stream_handle(stream)),
+           "xe_correlate_masked_batch")
+    return [(j["vis"], j.get("counts")) for j in jobs]
 
 
 class StreamCfg(ctypes.Structure):

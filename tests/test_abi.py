@@ -73,6 +73,27 @@ def test_argument_validation_before_any_device_call():
     assert L.xe_last_error()
 
 
+def test_masked_argument_validation_before_any_device_call():
+    L = xe.load()
+    buf = (ctypes.c_uint8 * 64)()
+    flags = (ctypes.c_uint8 * 64)()
+    out = (ctypes.c_int32 * 64)()
+    cnt = (ctypes.c_int32 * 64)()
+    # bad encoding, bad sizes, misaligned outputs: rejected before any device work
+    assert L.xe_correlate_masked(buf, flags, 4, 4, 1, 2, out, cnt, 0, None) == xe.XE_EINVAL
+    assert L.xe_correlate_masked(buf, flags, 4, 4, 1, -1, out, cnt, 0, None) == xe.XE_EINVAL
+    assert L.xe_correlate_masked(buf, flags, 0, 4, 1, 0, out, cnt, 0, None) == xe.XE_EINVAL
+    assert L.xe_correlate_masked(None, flags, 4, 4, 1, 0, out, cnt, 0, None) == xe.XE_EINVAL
+    assert L.xe_correlate_masked(buf, flags, 4, 16777216, 1, 0, out, cnt, 0, None) == xe.XE_EOVERFLOW
+    bad_cnt = ctypes.c_void_p(ctypes.addressof(cnt) + 2)
+    assert L.xe_correlate_masked(buf, flags, 4, 4, 1, 0, out, bad_cnt, 0, None) == xe.XE_EINVAL
+    bad_vis = ctypes.c_void_p(ctypes.addressof(out) + 4)
+    assert L.xe_correlate_masked(buf, flags, 4, 4, 1, 1, bad_vis, cnt, 0, None) == xe.XE_EINVAL
+    assert L.xe_correlate_masked_batch(None, 1, None) == xe.XE_EINVAL
+    assert L.xe_correlate_masked(buf, flags, 4, 4, 1, 5, out, cnt, 0, None) == xe.XE_EINVAL
+    assert b"encoding" in L.xe_last_error()
+
+
 def test_options_validation():
     with pytest.raises(xe.XeError):
         xe.set_option("operand_bytes", 3)
