@@ -52,6 +52,9 @@ struct Options {
     int autotune = 0;                      // 1: time candidate plans on first sight of a shape
     int timing = 0;
     int inject_stall = 0;                  // test hook for the bounded-wait path (next call only)
+    int count_weight = 50;                 // cost of a count-job k-iteration, % of a data one
+    int part_overhead = 2;                 // modelled cost of one extra tile part, % of a
+                                           // whole data tile (workspace fix-up)
 };
 static Options g_opt;
 static std::mutex g_mu;
@@ -62,6 +65,7 @@ struct JobShape {
     int N;
     int64_t T;
     int C;
+    int weight = 100;         // cost of one k-iteration of its tiles, percent of a data tile's
 };
 
 struct TuneCfg {
@@ -135,11 +139,64 @@ static void stream_k(const std::vector<Tile> &tiles, int t_lo, int t_hi, int G,
     }
 }
 
-static void schedule(HostPlan &p, int G, int sched) {
+// Weighted schedule: every tile is cut into the same number s of equal k-parts, and the
+// parts are dealt in k-phase order (all first parts, then all second parts, ...; heavier
+// jobs first within a phase) each to the CTA with the least weighted load so far, so that
+// CTAs still read nearby k-blocks at the same time (shared in L2) while light count-job
+// parts fill the gaps left by data-job parts.  A part costs kblocks/s * weight, plus a
+// modelled fix-up cost when s > 1; the s in [1, 4] with the smallest modelled makespan wins.
+static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &weight,
+                              std::vector<std::vector<Seg>> &per) {
+    const int n = int(p.tiles.size());
+    int min_kb = 1 << 30, max_kb = 0;
+    for (const Tile &t : p.tiles) {
+        min_kb = std::min(min_kb, t.kblocks);
+        max_kb = std::max(max_kb, t.kblocks);
+    }
+    std::vector<int> order(static_cast<size_t>(n));
+    for (int t = 0; t < n; ++t) order[size_t(t)] = t;
+    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+        return weight[size_t(p.tiles[size_t(a)].job)] > weight[size_t(p.tiles[size_t(b)].job)];
+    });
+    using Load = std::pair<double, int>;
+    auto deal = [&](int s, std::vector<std::vector<Seg>> *out) {
+        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+        for (int b = 0; b < G; ++b) heap.push(Load{0.0, b});
+        const double over = s > 1 ? g_opt.part_overhead / 100.0 * max_kb : 0.0;
+        double makespan = 0;
+        for (int k = 0; k < s; ++k)
+            for (int t : order) {
+                const Tile &tl = p.tiles[size_t(t)];
+                const int lo = int(int64_t(k) * tl.kblocks / s), hi = int(int64_t(k + 1) * tl.kblocks / s);
+                if (hi <= lo) continue;
+                Load l = heap.top();
+                heap.pop();
+                l.first += double(hi - lo) * weight[size_t(tl.job)] / 100.0 + over;
+                makespan = std::max(makespan, l.first);
+                if (out) (*out)[size_t(l.second)].push_back(Seg{t, lo, hi, -1});
+                heap.push(l);
+            }
+        return makespan;
+    };
+    int best_s = 1;
+    double best = 1e300;
+    for (int s = 1; s <= std::min(4, std::max(1, min_kb)); ++s) {
+        const double m = deal(s, nullptr);
+        if (m < best * (1 - 1e-9)) {
+            best = m;
+            best_s = s;
+        }
+    }
+    deal(best_s, &per);
+}
+
+static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weight) {
     p.clustered = false;
     const int n = int(p.tiles.size());
     std::vector<std::vector<Seg>> per(static_cast<size_t>(G));
-    if (sched == kSchedSplit) {
+    if (sched == kSchedWeighted) {
+        schedule_weighted(p, G, weight, per);
+    } else if (sched == kSchedSplit) {
         int s = n < G ? std::max(1, G / n) : 1;
         int min_kb = 1 << 30;
         for (const Tile &t : p.tiles) min_kb = std::min(min_kb, t.kblocks);
@@ -296,7 +353,10 @@ static TuneCfg heuristic(const std::vector<JobShape> &jobs, int eb, int n_sm) {
     if (c.sched < 0) {
         std::vector<Tile> tiles;
         enumerate_tiles(jobs, eb, c.tile_n, tiles);
-        if (!uniform_kblocks(tiles)) c.sched = kSchedLPT;
+        bool weighted = false;
+        for (const JobShape &j : jobs) weighted = weighted || j.weight != 100;
+        if (weighted) c.sched = kSchedWeighted;
+        else if (!uniform_kblocks(tiles)) c.sched = kSchedLPT;
         else if (int(tiles.size()) < c.n_cta) c.sched = kSchedSplit;
         else c.sched = kSchedHybrid;
     }
@@ -308,7 +368,9 @@ static bool build_plan(const std::vector<JobShape> &jobs, int eb, const TuneCfg 
     if (p.tiles.empty()) return false;
     int G = std::max(1, cfg.n_cta);
     if (cfg.sched == kSchedPairSplit) G = std::max(2, G & ~1);
-    schedule(p, G, cfg.sched);
+    std::vector<int> weight;
+    for (const JobShape &j : jobs) weight.push_back(std::max(1, j.weight));
+    schedule(p, G, cfg.sched, weight);
     if (!finalize_parts(p)) return false;
     // The symmetric two-part exchange waits for the partner part, so it is used only when
     // both parts are the only work of their CTAs (all of them resident at once).
@@ -405,6 +467,7 @@ static std::vector<int64_t> shape_key(const std::vector<JobShape> &jobs, int eb)
         key.push_back(j.N);
         key.push_back(j.T);
         key.push_back(j.C);
+        key.push_back(j.weight);
     }
     return key;
 }
@@ -626,6 +689,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 cj.stage_block0 = blocks;
                 count_of[size_t(k)] = idx;
                 shapes.push_back(shapes[size_t(k)]);
+                shapes.back().weight = g_opt.count_weight;
                 plane_off += size_t(cj.plane_chan_bytes) * size_t(cj.C);
             }
             jt.total_stage_blocks = blocks;
@@ -963,6 +1027,12 @@ int xe_set_option(const char *key, int64_t value) {
         g_opt.timing = value ? 1 : 0;
     } else if (!strcmp(key, "inject_stall")) {
         g_opt.inject_stall = value ? 1 : 0;
+    } else if (!strcmp(key, "count_weight")) {
+        if (value < 1 || value > 100) return fail(XE_EINVAL, "count_weight must lie in [1, 100]");
+        g_opt.count_weight = int(value);
+    } else if (!strcmp(key, "part_overhead")) {
+        if (value < 0 || value > 100) return fail(XE_EINVAL, "part_overhead must lie in [0, 100]");
+        g_opt.part_overhead = int(value);
     } else {
         return fail(XE_EINVAL, "unknown option '%s'", key);
     }

@@ -131,7 +131,10 @@ enum Sched : int {
     kSchedHybrid = 2,         // whole tiles in full waves, the last partial wave stream-K
     kSchedLPT = 3,            // whole tiles, longest first, to the least-loaded CTA
     kSchedPairSplit = 4,      // clustered kernel: tile pairs sharing a column block, k-split
-    kNumSched = 5,
+    kSchedWeighted = 5,       // tiles cut into k-aligned parts of about equal weighted cost
+                              // (count jobs weigh less than data jobs), longest part first
+                              // to the least-loaded CTA
+    kNumSched = 6,
 };
 
 constexpr int64_t kWsSlotElems = 2LL * kBN * kBM;  // re and im planes, [col][row] int32

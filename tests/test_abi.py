@@ -204,7 +204,7 @@ def _check_plan(shapes, n_cta, sched, tile_n):
     return d
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("tile_n", [128, 256])
 def test_schedules_cover_every_tile_and_k_once(sched, tile_n):
     for shapes, n_cta in [([(2048, 32768, 1)], 152), ([(300, 1000, 3)], 7), ([(100, 64, 1)], 152),

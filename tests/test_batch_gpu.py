@@ -55,7 +55,7 @@ def test_uneven_batch_equals_oracle_and_solo(xe):
         np.testing.assert_array_equal(g, solo.cpu().numpy())
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("tile_n", [128, 256])
 def test_every_schedule_and_tile_width_is_exact(xe, sched, tile_n):
     shapes = [(300, 1000, 2), (520, 2000, 1), (64, 64, 1)]
