@@ -11,7 +11,8 @@ section 2.2), real-time channels = that / (2,098,176 * 390625).
 With --gpus N > 1 (under torch.distributed.run) every rank correlates its own channel
 (weak scaling, no data-path collective); value = all ranks' cMAC / the slowest rank's time.
 --impl reference times the CPU oracle (plain int64 triple loop) on this host's cores on a
-bounded sample of the same workload.
+bounded sample of the same workload.  --workload masked (also summarised under "masked" in
+the default line) times the flag-masked correlation with valid-sample counts.
 """
 from __future__ import annotations
 
@@ -249,6 +250,73 @@ def run_batch_workload(args):
     return 0
 
 
+MASKED_WORKLOAD = ("flag-masked full-array channel: N=2048, T=32768, offset-binary quantised Gaussian "
+                   "+ plane wave, validity bits per (sample, input): 2% random + 256-sample bursts")
+
+
+def measure_masked(steps, warmup, dev, flush, check=True):
+    """Flag-masked correlation with valid-sample counts (offset-binary input), device-resident
+    inputs, L2 flushed between steps.  Returns a dict of rates and per-kernel device times."""
+    import numpy as np
+    import torch
+    from paper_2005_09481_gb300 import synth, xe
+    N, T = N_IN, T_SAMPLES
+    packed = synth.to_offset_binary(synth.gauss_plane(N, T, 1))
+    flags = synth.flags(N, T, 1, p_bad=0.02, burst=256)
+    d_in, d_f = torch.from_numpy(packed).to(dev), torch.from_numpy(flags).to(dev)
+    vis, cnt = xe.empty_vis(N, 1, dev), xe.empty_counts(N, 1, dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        xe.correlate_masked(d_in, d_f, N, T, 1, encoding="offset", out=vis, counts=cnt, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    parts = []
+    xe.set_timing(True)
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        xe.correlate_masked(d_in, d_f, N, T, 1, encoding="offset", out=vis, counts=cnt, stream=stream)
+        ends[k].record(stream)
+        parts.append(xe.last_timing_counts())
+    torch.cuda.synchronize()
+    xe.set_timing(False)
+    xe.device_status(stream)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+    cm = xe.cmac(N, T, 1)
+    out = {"value": cm / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
+           "stage_ms": statistics.mean(p[0] for p in parts),
+           "correlate_ms": statistics.mean(p[1] for p in parts),
+           "count_extract_ms": statistics.mean(p[2] for p in parts),
+           "gpu_launches_per_step": 3, "workload": MASKED_WORKLOAD}
+    if check:
+        import oracle
+        want = oracle.correlate_masked_dense(packed, flags, N, T, 1, 1)
+        wc = oracle.flag_counts_dense(flags, N, T, 1)
+        out["exact"] = bool(np.array_equal(vis.cpu().numpy(), want) and np.array_equal(cnt.cpu().numpy(), wc))
+    return out
+
+
+def run_masked_workload(args):
+    import torch
+    from paper_2005_09481_gb300 import xe
+    xe.load()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    with ClockSampler(uuid) as clk:
+        m = measure_masked(args.steps, args.warmup, dev, flush)
+    line = {"metric": METRIC, "value": m["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": m["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+            "config": {"workload": MASKED_WORKLOAD, "N": N_IN, "T": T_SAMPLES, "n_chan": 1,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "realtime_channels": m["value"] / REALTIME_CMAC, "masked": m,
+            "clocks": clk.summary(), "gpu_launches": 3 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_stream_workload(args):
     """Streaming serve at the CHIME sample rate: ramp the channel count while it is
     sustained; report the largest sustained count with its throughput and latency."""
@@ -288,7 +356,9 @@ def main():
     ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="xe", choices=["xe", "reference"])
-    ap.add_argument("--workload", default="headline", choices=["headline", "batch16", "uneven64", "stream"])
+    ap.add_argument("--workload", default="headline",
+                    choices=["headline", "batch16", "uneven64", "stream", "masked"])
+    ap.add_argument("--no-masked", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-channels", type=int, default=256)
@@ -306,6 +376,8 @@ def main():
         return run_batch_workload(args)
     if args.workload == "stream":
         return run_stream_workload(args)
+    if args.workload == "masked":
+        return run_masked_workload(args)
 
     import numpy as np
     import torch
@@ -393,6 +465,10 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = ws * cm_step * k_e2e / float(t.item())
 
+    masked = None
+    if ws == 1 and not args.no_masked:
+        masked = measure_masked(max(20, min(300, args.steps // 4)), 5, dev, flush)
+
     stream = None
     if ws == 1 and not args.no_stream:
         from paper_2005_09481_gb300 import serve
@@ -442,6 +518,7 @@ def main():
             "stream": ({k: stream[k] for k in ("channels", "sustained", "cmac_per_s", "p50_latency_ms",
                                                "p99_latency_ms", "frame_T", "integ_T", "device_source")}
                        if stream else None),
+            "masked": masked,
             "paper_context": {"fiji_chip_cmac_s": 1.10e12, "note": "derived from Table tab:computing "
                               "(93.4 ms per 49152-sample block at N=2048), AMD S9300x2, 722 MHz"},
         }

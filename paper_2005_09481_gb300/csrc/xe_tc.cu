@@ -27,6 +27,7 @@
 //                 through a workspace by the last segment to finish (arrival counter, no
 //                 spinning on other CTAs).
 #include <cstdint>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "xe_internal.h"
@@ -583,8 +584,29 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 const JobDev &jb = jt.jobs[tl.job];
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
-                // Count job (plain kernel only): the re plane slots alone.
-                const bool re_only = !MC && (jb.mode & kModeCount);
+                if (!MC && (jb.mode & kModeCount)) {
+                    // Count job (plain kernel only): the re plane slots alone.
+                    for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
+                        if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
+                            set_status(plan.status, kStatusTimeoutProducer);
+                            ok = false;
+                            break;
+                        }
+                        uint8_t *st = smem + stage * kStageBytes;
+                        const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
+                        mbar_arrive_expect_tx(&full[stage], kAPlane + bbytes);
+                        if (k + kPrefetchStages < sg.k_hi) {
+                            const uint8_t *fre = pre + int64_t(kPrefetchStages) * 2 * jb.n_pad * kRowBytes;
+                            bulk_prefetch_l2(fre + int64_t(tl.i0) * kRowBytes, kAPlane);
+                            bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
+                        }
+                        bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
+                        bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
+                        ++fills;
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
+                    }
+                    continue;
+                }
                 for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
                         set_status(plan.status, kStatusTimeoutProducer);
@@ -600,19 +622,6 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                     uint8_t *st = smem + stage * kStageBytes;
                     const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
                     const uint8_t *pim = pre + int64_t(jb.n_pad) * kRowBytes;
-                    if (re_only) {
-                        mbar_arrive_expect_tx(&full[stage], kAPlane + bbytes);
-                        if (k + kPrefetchStages < sg.k_hi) {
-                            const uint8_t *fre = pre + int64_t(kPrefetchStages) * 2 * jb.n_pad * kRowBytes;
-                            bulk_prefetch_l2(fre + int64_t(tl.i0) * kRowBytes, kAPlane);
-                            bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
-                        }
-                        bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
-                        bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
-                        ++fills;
-                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-                        continue;
-                    }
                     mbar_arrive_expect_tx(&full[stage], 2 * kAPlane + 2 * bbytes);
                     if (k + kPrefetchStages < sg.k_hi) {
                         // Bring the plane tiles of a later stage into L2 ahead of their copy.
@@ -683,41 +692,47 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 }
                 acc_ph ^= 1u;
                 tc_fence_after();
-                for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
-                    if (!mbar_wait(&full[stage], ph, status)) {
-                        set_status(plan.status, kStatusTimeoutMma);
-                        ok = false;
-                        break;
-                    }
-                    tc_fence_after();
-                    const uint32_t base = smem_u32(smem + stage * kStageBytes);
-#pragma unroll
-                    for (int s = 0; s < 2; ++s) {
-                        const uint32_t off = 32u * s;
-                        const uint64_t a_re = sdesc_k_sw64(base + off);
-                        const uint64_t a_im = sdesc_k_sw64(base + kAPlane + off);
-                        const uint64_t b_re = sdesc_k_sw64(base + 2 * kAPlane + off);
-                        const uint64_t b_im = sdesc_k_sw64(base + 2 * kAPlane + kBPlane + off);
-                        const uint32_t acc = (k > sg.k_lo || s > 0) ? 1u : 0u;
-                        if (re_only) {
-                            if (EB == 1) mma_f8f6f4(d_re, a_re, b_re, idesc, acc);   // + F_I F_J^T
-                            else mma_f16(d_re, a_re, b_re, idesc, acc);
-                        } else if (EB == 1) {
-                            mma_f8f6f4(d_re, a_re, b_re, idesc, acc);      // + A_I A_J^T
-                            mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);       // + B_I B_J^T
-                            mma_f8f6f4(d_im, a_im, b_re, idesc, acc);      // + B_I A_J^T
-                            mma_f8f6f4(d_im, a_re, b_im, idesc_neg, 1u);   // - A_I B_J^T
-                        } else {
-                            mma_f16(d_re, a_re, b_re, idesc, acc);
-                            mma_f16(d_re, a_im, b_im, idesc, 1u);
-                            mma_f16(d_im, a_im, b_re, idesc, acc);
-                            mma_f16(d_im, a_re, b_im, idesc_neg, 1u);
+                // The k-loop, compiled once per operand set: RO = count job (re slots only).
+                auto mainloop = [&](auto ro_tag) {
+                    constexpr bool RO = decltype(ro_tag)::value;
+                    for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
+                        if (!mbar_wait(&full[stage], ph, status)) {
+                            set_status(plan.status, kStatusTimeoutMma);
+                            ok = false;
+                            break;
                         }
+                        tc_fence_after();
+                        const uint32_t base = smem_u32(smem + stage * kStageBytes);
+#pragma unroll
+                        for (int s = 0; s < 2; ++s) {
+                            const uint32_t off = 32u * s;
+                            const uint64_t a_re = sdesc_k_sw64(base + off);
+                            const uint64_t a_im = sdesc_k_sw64(base + kAPlane + off);
+                            const uint64_t b_re = sdesc_k_sw64(base + 2 * kAPlane + off);
+                            const uint64_t b_im = sdesc_k_sw64(base + 2 * kAPlane + kBPlane + off);
+                            const uint32_t acc = (k > sg.k_lo || s > 0) ? 1u : 0u;
+                            if constexpr (RO) {
+                                if (EB == 1) mma_f8f6f4(d_re, a_re, b_re, idesc, acc);   // + F_I F_J^T
+                                else mma_f16(d_re, a_re, b_re, idesc, acc);
+                            } else if (EB == 1) {
+                                mma_f8f6f4(d_re, a_re, b_re, idesc, acc);      // + A_I A_J^T
+                                mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);       // + B_I B_J^T
+                                mma_f8f6f4(d_im, a_im, b_re, idesc, acc);      // + B_I A_J^T
+                                mma_f8f6f4(d_im, a_re, b_im, idesc_neg, 1u);   // - A_I B_J^T
+                            } else {
+                                mma_f16(d_re, a_re, b_re, idesc, acc);
+                                mma_f16(d_re, a_im, b_im, idesc, 1u);
+                                mma_f16(d_im, a_im, b_re, idesc, acc);
+                                mma_f16(d_im, a_re, b_im, idesc_neg, 1u);
+                            }
+                        }
+                        if (MC) mma_commit_multicast(&empty[stage], 0x3);
+                        else mma_commit(&empty[stage]);
+                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
                     }
-                    if (MC) mma_commit_multicast(&empty[stage], 0x3);
-                    else mma_commit(&empty[stage]);
-                    if (++stage == kStages) { stage = 0; ph ^= 1u; }
-                }
+                };
+                if (re_only) mainloop(std::true_type{});
+                else mainloop(std::false_type{});
                 if (ok) mma_commit(acc_full);
             }
             if (!ok) {
