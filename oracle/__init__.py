@@ -19,6 +19,10 @@ Readings where the paper is silent: high nibble = real, low nibble = imaginary, 
 complement, conjugate on the second index, row-major packed upper triangle with {Re, Im}
 interleaved.
 
+Phased-array beams (section 2.1; "Pulsar Beamforming" in Table tab:computing):
+``beamform`` (C loop) and ``beamform_dense`` (library matmul), y_b(t) = sum_i w_{b,i} x_i(t)
+with int8 complex weights (reading: the paper gives no formula or weight format).
+
 Flag-masked correlation (flags travel with the data, section 2.2 and Table
 tab:data-flow; RFI excision precedes correlation, Table tab:computing):
 ``correlate_masked`` / ``flag_counts`` (C loops) and ``correlate_masked_dense`` /
@@ -76,6 +80,8 @@ def _load():
             lib.xe_oracle_correlate_masked.restype = ctypes.c_int
             lib.xe_oracle_flag_counts.argtypes = [p, i64, i64, i64, p]
             lib.xe_oracle_flag_counts.restype = ctypes.c_int
+            lib.xe_oracle_beamform.argtypes = [p, p, i64, i64, i64, i64, p]
+            lib.xe_oracle_beamform.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -270,3 +276,44 @@ def flag_counts_dense(flags, N: int, T: int, C: int = 1, t_chunk: int = 8192) ->
             M += F.T @ F
         out[c] = np.rint(M[iu]).astype(np.int64)
     return out
+
+
+def _check_w(w, N: int, B: int) -> np.ndarray:
+    a = np.ascontiguousarray(w, dtype=np.int8)
+    if a.size != B * N * 2:
+        raise ValueError(f"weights must hold B*N*2 = {B * N * 2} int8 values")
+    return a.reshape(B, N, 2)
+
+
+def beamform(packed: np.ndarray, w, N: int, T: int, C: int = 1, B: int = 1) -> np.ndarray:
+    """Plain C loop: y_b(t) = sum_i w_{b,i} x_i(t).  w: int8 [B][N][2]; int64 [C, T, B, 2]."""
+    b = _check_in(packed, N, T, C)
+    wa = _check_w(w, N, B)
+    out = np.empty((C, T, B, 2), np.int64)
+    rc = _load().xe_oracle_beamform(_ptr(b), _ptr(wa), N, T, C, B, _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_beamform rejected its arguments")
+    return out
+
+
+def beamform_dense(packed: np.ndarray, w, N: int, T: int, C: int = 1, B: int = 1,
+                   t_chunk: int = 8192) -> np.ndarray:
+    """The beams as a matrix product Y = X W^T (complex128 library matmul, exact: every
+    partial sum is an integer of magnitude below 2 * 8 * 128 * N < 2**53).
+    int64 [C, T, B, 2]."""
+    b = _check_in(packed, N, T, C).reshape(C, T, N)
+    wa = _check_w(w, N, B).astype(np.int64)
+    W = (wa[..., 0] + 1j * wa[..., 1]).astype(np.complex128)          # [B, N]
+    out = np.empty((C, T, B, 2), np.int64)
+    for c in range(C):
+        for t0 in range(0, T, t_chunk):
+            re, im = decode(b[c, t0:t0 + t_chunk])
+            Y = (re + 1j * im).astype(np.complex128) @ W.T                # [t, B]
+            out[c, t0:t0 + t_chunk, :, 0] = np.rint(Y.real).astype(np.int64)
+            out[c, t0:t0 + t_chunk, :, 1] = np.rint(Y.imag).astype(np.int64)
+    return out
+
+
+def beam_cmac(N: int, T: int, C: int = 1, B: int = 1) -> float:
+    """Complex multiply-accumulates of the beams: C * T * B * N."""
+    return float(C) * T * B * N

@@ -203,6 +203,40 @@ int xe_oracle_flag_counts(const uint8_t *flags, int64_t N, int64_t T, int64_t C,
     return 0;
 }
 
+/*
+ * Phased-array beams (section 2.1: besides the correlation, the X-engine nodes form 10
+ * phased-array beams for pulsar timing; Table tab:computing lists "Pulsar Beamforming").
+ * The paper gives no formula; the reading (R12) is the weighted coherent sum over inputs,
+ *     y_b(t) = sum_i w_{b,i} x_i(t),
+ * with complex integer weights w (int8 real and imaginary parts), exact in integers.
+ * in: uint8 [C][T][N]; w: int8 [B][N][2] {re, im}; y: int64 [C][T][B][2].
+ */
+int xe_oracle_beamform(const uint8_t *in, const int8_t *w, int64_t N, int64_t T, int64_t C,
+                       int64_t B, int64_t *y)
+{
+    if (N < 1 || T < 0 || C < 1 || B < 1 || !in || !w || !y)
+        return -1;
+    for (int64_t c = 0; c < C; ++c) {
+        const uint8_t *chan = in + c * T * N;
+#pragma omp parallel for schedule(static)
+        for (int64_t t = 0; t < T; ++t) {
+            for (int64_t b = 0; b < B; ++b) {
+                int64_t acc_re = 0, acc_im = 0;
+                for (int64_t i = 0; i < N; ++i) {
+                    int64_t a, bb;
+                    decode_sample(chan[t * N + i], &a, &bb);
+                    const int64_t wr = w[(b * N + i) * 2 + 0], wi = w[(b * N + i) * 2 + 1];
+                    acc_re += wr * a - wi * bb;     /* Re{(wr + i wi)(a + i bb)} */
+                    acc_im += wr * bb + wi * a;     /* Im{(wr + i wi)(a + i bb)} */
+                }
+                y[((c * T + t) * B + b) * 2 + 0] = acc_re;
+                y[((c * T + t) * B + b) * 2 + 1] = acc_im;
+            }
+        }
+    }
+    return 0;
+}
+
 /* Complex multiply-accumulates of one correlation: C * T * N(N+1)/2 (section 2.2). */
 double xe_oracle_cmac(int64_t N, int64_t T, int64_t C)
 {

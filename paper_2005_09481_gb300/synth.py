@@ -112,3 +112,18 @@ def flags(N: int, T: int, C: int = 1, p_bad: float = 0.1, seed: int = BASE_SEED,
 def to_offset_binary(packed: np.ndarray) -> np.ndarray:
     """The same sample values written with offset-binary nibbles (value = nibble - 8)."""
     return (np.asarray(packed, np.uint8) ^ np.uint8(0x88)).astype(np.uint8)
+
+
+def beam_weights(B: int, N: int, seed: int = BASE_SEED, amp: int = 127) -> np.ndarray:
+    """Phased-array steering weights int8 [B][N][2] {re, im}: beam b steers to a seeded
+    phase gradient, w_{b,i} = amp * exp(-i (2 pi k_b i / N + phi_b)), rounded half to even
+    and clipped to [-127, 127]."""
+    rng = np.random.default_rng(seed + 104729)
+    k = rng.uniform(-N / 8, N / 8, size=B)
+    phi = rng.uniform(0.0, 2.0 * np.pi, size=B)
+    i = np.arange(N)
+    ph = 2.0 * np.pi * k[:, None] * i[None, :] / N + phi[:, None]
+    w = np.empty((B, N, 2), np.int8)
+    w[..., 0] = np.clip(np.rint(amp * np.cos(ph)), -127, 127).astype(np.int8)
+    w[..., 1] = np.clip(np.rint(-amp * np.sin(ph)), -127, 127).astype(np.int8)
+    return w
