@@ -12,7 +12,8 @@ With --gpus N > 1 (under torch.distributed.run) every rank correlates its own ch
 (weak scaling, no data-path collective); value = all ranks' cMAC / the slowest rank's time.
 --impl reference times the CPU oracle (plain int64 triple loop) on this host's cores on a
 bounded sample of the same workload.  --workload masked (also summarised under "masked" in
-the default line) times the flag-masked correlation with valid-sample counts.
+the default line) times the flag-masked correlation with valid-sample counts;
+--workload beams (also under "beams") the 10 phased-array beams of the same input.
 """
 from __future__ import annotations
 
@@ -297,6 +298,77 @@ def measure_masked(steps, warmup, dev, flush, check=True):
     return out
 
 
+BEAM_WORKLOAD = ("pulsar phased-array beams: N=2048, T=32768, 1 channel, 10 beams, int8 steering weights, "
+                 "quantised Gaussian + plane wave")
+N_BEAMS = 10
+
+
+def measure_beams(steps, warmup, dev, flush, check=True):
+    """Phased-array beams (device-resident inputs, L2 flushed between steps).  Returns rates,
+    per-kernel device times and the HBM roofline of the beam kernel."""
+    import numpy as np
+    import torch
+    from paper_2005_09481_gb300 import synth, xe
+    N, T, B = N_IN, T_SAMPLES, N_BEAMS
+    packed = synth.gauss_plane(N, T, 1)
+    w = synth.beam_weights(B, N)
+    d_in, d_w = torch.from_numpy(packed).to(dev), torch.from_numpy(w).to(dev)
+    y = xe.empty_beams(T, B, 1, dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(warmup):
+        xe.beamform(d_in, d_w, N, T, 1, out=y, stream=stream)
+    torch.cuda.synchronize()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    parts = []
+    xe.set_timing(True)
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        xe.beamform(d_in, d_w, N, T, 1, out=y, stream=stream)
+        ends[k].record(stream)
+        parts.append(xe.last_timing())
+    torch.cuda.synchronize()
+    xe.set_timing(False)
+    xe.device_status(stream)
+    ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends)) / steps
+    beam_ms = statistics.mean(p[1] for p in parts)
+    algo_bytes = N * T + T * B * 8               # packed input read once + beams written
+    _, hbm, src = peaks()
+    out = {"value": T * B * N / (ms * 1e-3), "unit": "beam cMAC/s", "ms_per_step": ms, "steps": steps,
+           "samples_per_s": T / (ms * 1e-3), "weight_prep_ms": statistics.mean(p[0] for p in parts),
+           "beam_kernel_ms": beam_ms, "gpu_launches_per_step": 2, "workload": BEAM_WORKLOAD,
+           "roofline": {"bound": "hbm", "achieved": algo_bytes / (beam_ms * 1e-3) / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": algo_bytes / (beam_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                        "algorithmic": "N*T input bytes + T*B*8 output bytes per launch",
+                        "peak_source": f"{src}: hbm_gbs of MEASURED_PEAKS.json"}}
+    if check:
+        import oracle
+        want = oracle.beamform_dense(packed, w, N, T, 1, B)
+        out["exact"] = bool(np.array_equal(y.cpu().numpy(), want))
+    return out
+
+
+def run_beam_workload(args):
+    import torch
+    from paper_2005_09481_gb300 import xe
+    xe.load()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    with ClockSampler(uuid) as clk:
+        m = measure_beams(args.steps, args.warmup, dev, flush)
+    line = {"metric": "phased-array beam cMAC/s (10 beams, N=2048)", "value": m["value"], "unit": m["unit"],
+            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3",
+            "data": "synthetic",
+            "config": {"workload": BEAM_WORKLOAD, "N": N_IN, "T": T_SAMPLES, "beams": N_BEAMS,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "roofline": m["roofline"], "beams": m, "clocks": clk.summary(), "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_masked_workload(args):
     import torch
     from paper_2005_09481_gb300 import xe
@@ -357,8 +429,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="xe", choices=["xe", "reference"])
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch16", "uneven64", "stream", "masked"])
+                    choices=["headline", "batch16", "uneven64", "stream", "masked", "beams"])
     ap.add_argument("--no-masked", action="store_true")
+    ap.add_argument("--no-beams", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-channels", type=int, default=256)
@@ -378,6 +451,8 @@ def main():
         return run_stream_workload(args)
     if args.workload == "masked":
         return run_masked_workload(args)
+    if args.workload == "beams":
+        return run_beam_workload(args)
 
     import numpy as np
     import torch
@@ -468,6 +543,9 @@ def main():
     masked = None
     if ws == 1 and not args.no_masked:
         masked = measure_masked(max(20, min(300, args.steps // 4)), 5, dev, flush)
+    beams = None
+    if ws == 1 and not args.no_beams:
+        beams = measure_beams(max(20, min(300, args.steps // 4)), 5, dev, flush)
 
     stream = None
     if ws == 1 and not args.no_stream:
@@ -519,6 +597,7 @@ def main():
                                                "p99_latency_ms", "frame_T", "integ_T", "device_source")}
                        if stream else None),
             "masked": masked,
+            "beams": beams,
             "paper_context": {"fiji_chip_cmac_s": 1.10e12, "note": "derived from Table tab:computing "
                               "(93.4 ms per 49152-sample block at N=2048), AMD S9300x2, 722 MHz"},
         }

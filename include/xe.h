@@ -195,6 +195,31 @@ int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jo
  * batch shape was first seen, else the default choice.  XE_EAGAIN if none yet. */
 int xe_last_config(int *n_cta, int *tile_n, int *sched);
 
+/* ---- phased-array beams ------------------------------------------------------------ */
+
+/* Besides the correlation, the X-engine nodes form phased-array beams for pulsar timing
+ * (section 2.1: 10 beams; "Pulsar Beamforming" in Table tab:computing).  The paper gives
+ * no formula or weight format; this library computes the weighted coherent sum
+ *
+ *     y_b(t) = sum_{i < N} w_{b,i} x_i(t),    b < n_beams,
+ *
+ * exactly in integers, with complex int8 weights:
+ *
+ *   weights  int8  [n_beams][N][2]      {re, im} of w_{b,i}, each in [-127, 127]
+ *                                       (-128 is accepted and also exact)
+ *   beams    int32 [C][T][n_beams][2]   {re, im} of y_b(t), time-major (all beams of one
+ *                                       sample contiguous)
+ *
+ * in (the correlation's input format), weights and beams are caller-owned DEVICE pointers;
+ * beams is overwritten.  1 <= n_beams <= 128.  Enqueued on `stream`, not synchronised.
+ * Runs on the tcgen05 tensor cores: each weight component is split exactly as
+ * w = 16 w_hi + w_lo (both in [-8, 8]), so every operand is exact in FP8 e4m3 and every f32
+ * partial sum is an integer below 2^24 (<= 128 N).  Beams are formed in groups of at most
+ * 64 per launch.  Returns XE_OK, XE_EINVAL (bad sizes, null or misaligned pointers),
+ * XE_ENOMEM, XE_ECUDA or XE_ENODEV. */
+int xe_beamform(const uint8_t *in, int N, int64_t T, int n_chan, const int8_t *weights, int n_beams,
+                int32_t *beams, void *stream);
+
 /* ---- streaming server (continuous integration of frames) --------------------------- */
 
 typedef struct xe_stream_cfg {

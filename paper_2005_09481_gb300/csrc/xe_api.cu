@@ -400,6 +400,8 @@ struct Scratch {
     int *status = nullptr;
     int32_t *cvis = nullptr;      // outputs of the count jobs of masked calls ([C][B][2] each)
     size_t cvis_bytes = 0;
+    uint8_t *beam_wt = nullptr;   // beam weights as MMA operand tiles
+    size_t beam_wt_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -1151,6 +1153,62 @@ int xe_correlate_masked_batch(const xe_masked_job *jobs, int n_jobs, void *strea
     g_job_acc = nullptr;
     g_job_mask = nullptr;
     return rc;
+}
+
+int xe_beamform(const uint8_t *in, int N, int64_t T, int n_chan, const int8_t *weights, int n_beams,
+                int32_t *beams, void *stream) {
+    if (!in || !weights || !beams) return fail(XE_EINVAL, "null input, weight or beam pointer");
+    if (N < 1 || N > XE_MAX_N) return fail(XE_EINVAL, "N=%d outside [1, %d]", N, XE_MAX_N);
+    if (T < 1) return fail(XE_EINVAL, "T=%lld < 1", (long long)T);
+    if (n_chan < 1) return fail(XE_EINVAL, "n_chan=%d < 1", n_chan);
+    if (n_beams < 1 || n_beams > kBeamMaxBeams)
+        return fail(XE_EINVAL, "n_beams=%d outside [1, %d]", n_beams, kBeamMaxBeams);
+    if (reinterpret_cast<uintptr_t>(beams) & 3) return fail(XE_EINVAL, "beams must be 4-byte aligned");
+    if (int64_t(n_chan) * ((T + kBeamRows - 1) / kBeamRows) > 0x7fffffffLL)
+        return fail(XE_EINVAL, "too many sample tiles");
+    std::lock_guard<std::mutex> lk(g_mu);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Device *d = nullptr;
+    int rc = get_device(&d);
+    if (rc) return rc;
+    Scratch *sc = nullptr;
+    rc = get_scratch(d, s, &sc);
+    if (rc) return rc;
+    // Beams in groups of at most kBeamMaxPerLaunch (4 MMA columns each); every group is one
+    // weight preparation and one launch over all inputs (exact in one f32 accumulation).
+    const int group = std::min(n_beams, kBeamMaxPerLaunch);
+    rc = grow(reinterpret_cast<void **>(&sc->beam_wt), &sc->beam_wt_bytes, beam_wt_bytes(group, N), false);
+    if (rc) return rc;
+    const bool timing = g_opt.timing != 0;
+    const int n_chunks = (N + kBeamChunk - 1) / kBeamChunk;
+    for (int b0 = 0; b0 < n_beams; b0 += group) {
+        const int nb = std::min(group, n_beams - b0);
+        const int ncols = beam_ncols(nb);
+        if (timing && b0 == 0) XE_CUDA(cudaEventRecord(sc->ev[0], s));
+        XE_CUDA(launch_beam_weights(weights, b0, nb, N, ncols, sc->beam_wt, s));
+        if (timing && b0 == 0) XE_CUDA(cudaEventRecord(sc->ev[1], s));
+        BeamDev bd{};
+        bd.in = in;
+        bd.wt = sc->beam_wt;
+        bd.y = beams;
+        bd.status = sc->status;
+        bd.T = T;
+        bd.N = N;
+        bd.C = n_chan;
+        bd.B_total = n_beams;
+        bd.b0 = b0;
+        bd.B = nb;
+        bd.ncols = ncols;
+        bd.k_lo = 0;
+        bd.k_hi = n_chunks;
+        XE_CUDA(launch_beam(bd, s));
+    }
+    if (timing) {
+        XE_CUDA(cudaEventRecord(sc->ev[2], s));
+        XE_CUDA(cudaEventRecord(sc->ev[3], s));
+        for (int k = 0; k < 4; ++k) g_last_ev[k] = sc->ev[k];
+    }
+    return XE_OK;
 }
 
 int xe_correlate_masked(const uint8_t *in, const uint8_t *flags, int N, int64_t T, int n_chan,

@@ -146,6 +146,33 @@ enum DeviceStatus : int {
     kStatusTimeoutEpilogue = 3,
 };
 
+// ---- phased-array beams (xe_beam.cu) ---------------------------------------------------
+
+constexpr int kBeamRows = 128;          // time samples per CTA (MMA M)
+constexpr int kBeamChunk = 64;          // inputs per pipeline stage (K = 128 e4m3: re, im)
+constexpr int kBeamMaxBeams = 128;      // per call
+constexpr int kBeamMaxPerLaunch = 64;   // 4 MMA columns per beam (Re/Im x hi/lo), N <= 256
+
+struct BeamDev {
+    const uint8_t *in;        // packed input [C][T][N]
+    const uint8_t *wt;        // weights as MMA B tiles: [n_chunks][2][ncols][64 B] e4m3, swizzled
+    int32_t *y;               // beams [C][T][B_total][2]
+    int *status;              // device status word (0 = ok)
+    int64_t T;
+    int N;
+    int C;
+    int B_total;              // beams per sample row of y
+    int b0;                   // first beam of this launch
+    int B;                    // beams of this launch (<= kBeamMaxPerLaunch)
+    int ncols;                // MMA N: 4B rounded up to a multiple of 16
+    int k_lo, k_hi;           // input chunks [k_lo, k_hi) summed by this launch
+};
+
+cudaError_t launch_beam_weights(const int8_t *w, int b0, int nb, int N, int ncols, uint8_t *wt, cudaStream_t s);
+cudaError_t launch_beam(const BeamDev &bd, cudaStream_t s);
+int beam_ncols(int B);
+size_t beam_wt_bytes(int B, int N);
+
 // Kernel launchers (xe_tc.cu, xe_imma.cu, xe_mask.cu).  `masked` selects the masking
 // variant of the e4m3 staging kernel (any job with kModeMasked).
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s, bool masked = false);

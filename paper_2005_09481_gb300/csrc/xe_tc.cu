@@ -30,6 +30,7 @@
 #include <type_traits>
 #include <cuda_runtime.h>
 
+#include "xe_codes.cuh"
 #include "xe_internal.h"
 #include "xe_ptx.cuh"
 
@@ -37,22 +38,7 @@ namespace xe {
 
 // ---- operand encodings ---------------------------------------------------------------
 
-// e4m3: sign bit 7, 4-bit exponent (bias 7) in bits 3-6, 3-bit mantissa.  Integers up to
-// 16 in magnitude are exact.  f16: sign bit 15, 5-bit exponent (bias 15), 10-bit mantissa.
-__host__ __device__ constexpr uint32_t encode_small_int(int v, int elem_bytes) {
-    if (v == 0) return 0u;
-    const uint32_t neg = v < 0 ? 1u : 0u;
-    const int m = v < 0 ? -v : v;
-    const int e = m >= 16 ? 4 : m >= 8 ? 3 : m >= 4 ? 2 : m >= 2 ? 1 : 0;
-    const int frac = m - (1 << e);
-    if (elem_bytes == 1)
-        return (neg << 7) | (uint32_t(e + 7) << 3) | uint32_t(frac << (3 - e));
-    return (neg << 15) | (uint32_t(e + 15) << 10) | uint32_t(frac << (10 - e));
-}
-
 uint32_t operand_code(int v, int elem_bytes) { return encode_small_int(v, elem_bytes); }
-
-__host__ __device__ constexpr int nibble_value(int nib) { return nib >= 8 ? nib - 16 : nib; }
 
 struct NibbleCodes {
     uint16_t c[16];
@@ -64,27 +50,6 @@ __host__ __device__ constexpr NibbleCodes make_codes(int elem_bytes) {
 }
 __constant__ NibbleCodes c_codes_e4m3 = make_codes(1);
 __constant__ NibbleCodes c_codes_f16 = make_codes(2);
-
-// Four e4m3 codes packed little-endian into one word: nibble values lo..lo+3.
-__host__ __device__ constexpr uint32_t pack_codes(int lo) {
-    return encode_small_int(nibble_value(lo), 1) | (encode_small_int(nibble_value(lo + 1), 1) << 8) |
-           (encode_small_int(nibble_value(lo + 2), 1) << 16) | (encode_small_int(nibble_value(lo + 3), 1) << 24);
-}
-
-// Four two's-complement nibbles (one in the low 4 bits of each byte) -> four e4m3 codes.
-// A byte permute looks each nibble up in the 16-entry code table (held in four words:
-// values 0..3, 4..7, -8..-5, -4..-1): the low 3 bits select within the non-negative or the
-// negative half, bit 3 chooses the half.
-__device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t x) {
-    constexpr uint32_t P0 = pack_codes(0), P1 = pack_codes(4), N0 = pack_codes(8), N1 = pack_codes(12);
-    const uint32_t y = x & 0x07070707u;
-    const uint32_t z = y | (y >> 4);
-    const uint32_t sel = __byte_perm(z, 0, 0x0020);
-    const uint32_t pos = __byte_perm(P0, P1, sel);
-    const uint32_t neg = __byte_perm(N0, N1, sel);
-    const uint32_t m = ((x >> 3) & 0x01010101u) * 0xFFu;
-    return (pos & ~m) | (neg & m);
-}
 
 // ---- staging kernel ----------------------------------------------------------------------
 

@@ -73,6 +73,7 @@ def load():
             "xe_last_timing_counts": ([p, p, p], i32),
             "xe_correlate_masked": ([p, p, i32, i64, i32, i32, p, p, i32, p], i32),
             "xe_correlate_masked_batch": ([p, i32, p], i32),
+            "xe_beamform": ([p, i32, i64, i32, p, i32, p, p], i32),
             "xe_device_status": ([p], i32),
             "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
             "xe_plan_dump": ([p, p, p, i32, i32, i32, i32, p, i64], i64),
@@ -347,6 +348,29 @@ def correlate_masked_batch(jobs, stream=None):
     _check(load().xe_correlate_masked_batch(arr, len(jobs), _stream_handle(stream)),
            "xe_correlate_masked_batch")
     return [(j["vis"], j.get("counts")) for j in jobs]
+
+
+def empty_beams(T: int, B: int, C: int = 1, device="cuda"):
+    import torch
+    return torch.empty((C, T, B, 2), dtype=torch.int32, device=device)
+
+
+def beamform(inp, weights, N: int, T: int, C: int = 1, out=None, stream=None):
+    """Phased-array beams y_b(t) = sum_i w_{b,i} x_i(t): device uint8 input [C, T, N], int8
+    weights [B, N, 2] -> int32 [C, T, B, 2] (async on stream)."""
+    import torch
+    _shape(inp, N, T, C)
+    if weights.dtype != torch.int8 or not weights.is_cuda or not weights.is_contiguous():
+        raise ValueError("weights must be a contiguous int8 CUDA tensor [B, N, 2]")
+    if weights.numel() % (2 * N) != 0:
+        raise ValueError("weights must hold B * N * 2 values")
+    B = weights.numel() // (2 * N)
+    if out is None:
+        out = empty_beams(T, B, C, inp.device)
+    rc = load().xe_beamform(ctypes.c_void_p(inp.data_ptr()), N, T, C, ctypes.c_void_p(weights.data_ptr()),
+                            B, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(rc, "xe_beamform")
+    return out
 
 
 class StreamCfg(ctypes.Structure):

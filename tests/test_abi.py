@@ -94,6 +94,23 @@ def test_masked_argument_validation_before_any_device_call():
     assert b"encoding" in L.xe_last_error()
 
 
+def test_beamform_argument_validation_before_any_device_call():
+    L = xe.load()
+    buf = (ctypes.c_uint8 * 64)()
+    w = (ctypes.c_int8 * 64)()
+    y = (ctypes.c_int32 * 64)()
+    assert L.xe_beamform(None, 4, 4, 1, w, 1, y, None) == xe.XE_EINVAL
+    assert L.xe_beamform(buf, 4, 4, 1, None, 1, y, None) == xe.XE_EINVAL
+    assert L.xe_beamform(buf, 4, 4, 1, w, 0, y, None) == xe.XE_EINVAL
+    assert L.xe_beamform(buf, 4, 4, 1, w, 129, y, None) == xe.XE_EINVAL
+    assert L.xe_beamform(buf, 0, 4, 1, w, 1, y, None) == xe.XE_EINVAL
+    assert L.xe_beamform(buf, 4, 0, 1, w, 1, y, None) == xe.XE_EINVAL
+    bad = ctypes.c_void_p(ctypes.addressof(y) + 2)
+    assert L.xe_beamform(buf, 4, 4, 1, w, 1, bad, None) == xe.XE_EINVAL
+    assert L.xe_beamform(buf, 4, 4, 1, w, 200, y, None) == xe.XE_EINVAL
+    assert b"n_beams" in L.xe_last_error()
+
+
 def test_options_validation():
     with pytest.raises(xe.XeError):
         xe.set_option("operand_bytes", 3)
