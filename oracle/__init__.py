@@ -23,6 +23,11 @@ Phased-array beams (section 2.1; "Pulsar Beamforming" in Table tab:computing):
 ``beamform`` (C loop) and ``beamform_dense`` (library matmul), y_b(t) = sum_i w_{b,i} x_i(t)
 with int8 complex weights (reading: the paper gives no formula or weight format).
 
+Corner turn and pre-sum (section 2.1 bundles of four frequencies per cylinder, section 2.3
+transpose, "Re-Order and Pre-Sum" in Table tab:computing): ``corner_turn`` and ``presum``
+(C loops).  Readings: bundle = [T][n_freq][n_in] of one cylinder, full-array input
+n = cyl * n_in + i; pre-sum = per-input time sums of re and im.
+
 Flag-masked correlation (flags travel with the data, section 2.2 and Table
 tab:data-flow; RFI excision precedes correlation, Table tab:computing):
 ``correlate_masked`` / ``flag_counts`` (C loops) and ``correlate_masked_dense`` /
@@ -82,6 +87,10 @@ def _load():
             lib.xe_oracle_flag_counts.restype = ctypes.c_int
             lib.xe_oracle_beamform.argtypes = [p, p, i64, i64, i64, i64, p]
             lib.xe_oracle_beamform.restype = ctypes.c_int
+            lib.xe_oracle_corner_turn.argtypes = [p, i64, i64, i64, i64, p]
+            lib.xe_oracle_corner_turn.restype = ctypes.c_int
+            lib.xe_oracle_presum.argtypes = [p, i64, i64, i64, p]
+            lib.xe_oracle_presum.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -317,3 +326,25 @@ def beamform_dense(packed: np.ndarray, w, N: int, T: int, C: int = 1, B: int = 1
 def beam_cmac(N: int, T: int, C: int = 1, B: int = 1) -> float:
     """Complex multiply-accumulates of the beams: C * T * B * N."""
     return float(C) * T * B * N
+
+
+def corner_turn(bundles: np.ndarray, n_cyl: int, n_freq: int, n_in: int, T: int) -> np.ndarray:
+    """uint8 bundles [n_cyl][T][n_freq][n_in] -> frames uint8 [n_freq][T][n_cyl * n_in]."""
+    b = np.ascontiguousarray(bundles, dtype=np.uint8).reshape(-1)
+    if b.size != n_cyl * T * n_freq * n_in:
+        raise ValueError("bundles must hold n_cyl * T * n_freq * n_in bytes")
+    out = np.empty((n_freq, T, n_cyl * n_in), np.uint8)
+    rc = _load().xe_oracle_corner_turn(_ptr(b), n_cyl, n_freq, n_in, T, _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_corner_turn rejected its arguments")
+    return out
+
+
+def presum(frames: np.ndarray, N: int, T: int, C: int = 1) -> np.ndarray:
+    """Per-input time sums of re and im: int64 [C, N, 2]."""
+    b = _check_in(frames, N, T, C)
+    out = np.empty((C, N, 2), np.int64)
+    rc = _load().xe_oracle_presum(_ptr(b), N, T, C, _ptr(out))
+    if rc != 0:
+        raise ValueError("xe_oracle_presum rejected its arguments")
+    return out

@@ -237,6 +237,53 @@ int xe_oracle_beamform(const uint8_t *in, const int8_t *w, int64_t N, int64_t T,
     return 0;
 }
 
+/*
+ * Corner turn at the X-engine (section 2.1: the F-engine's inter-crate stage delivers
+ * "bundles" of four frequency channels, each bundle holding one cylinder's inputs; each GPU
+ * node combines four bundles into full-array data for those frequencies; section 2.3: the
+ * node completes the transpose; Table tab:computing: "Re-Order and Pre-Sum").  Reading
+ * (R13): a bundle is uint8 [T][n_freq][n_in] (time, then frequency, then the cylinder's
+ * inputs); input n of the full array is cyl * n_in + i.
+ *   bundles: uint8 [n_cyl][T][n_freq][n_in]  ->  frames: uint8 [n_freq][T][n_cyl * n_in]
+ */
+int xe_oracle_corner_turn(const uint8_t *bundles, int64_t n_cyl, int64_t n_freq, int64_t n_in,
+                          int64_t T, uint8_t *frames)
+{
+    if (n_cyl < 1 || n_freq < 1 || n_in < 1 || T < 0 || !bundles || !frames)
+        return -1;
+    const int64_t N = n_cyl * n_in;
+    for (int64_t f = 0; f < n_freq; ++f)
+        for (int64_t t = 0; t < T; ++t)
+            for (int64_t cyl = 0; cyl < n_cyl; ++cyl)
+                for (int64_t i = 0; i < n_in; ++i)
+                    frames[(f * T + t) * N + cyl * n_in + i] =
+                        bundles[((cyl * T + t) * n_freq + f) * n_in + i];
+    return 0;
+}
+
+/*
+ * Pre-sum (reading R14): the per-input time sums s_n = sum_t x_n(t) of one block of samples,
+ * re and im separately.  frames: uint8 [C][T][N]; sums: int64 [C][N][2].
+ */
+int xe_oracle_presum(const uint8_t *frames, int64_t N, int64_t T, int64_t C, int64_t *sums)
+{
+    if (N < 1 || T < 0 || C < 1 || !frames || !sums)
+        return -1;
+    for (int64_t c = 0; c < C; ++c)
+        for (int64_t n = 0; n < N; ++n) {
+            int64_t sr = 0, si = 0;
+            for (int64_t t = 0; t < T; ++t) {
+                int64_t a, b;
+                decode_sample(frames[(c * T + t) * N + n], &a, &b);
+                sr += a;
+                si += b;
+            }
+            sums[(c * N + n) * 2 + 0] = sr;
+            sums[(c * N + n) * 2 + 1] = si;
+        }
+    return 0;
+}
+
 /* Complex multiply-accumulates of one correlation: C * T * N(N+1)/2 (section 2.2). */
 double xe_oracle_cmac(int64_t N, int64_t T, int64_t C)
 {

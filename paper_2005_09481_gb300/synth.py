@@ -127,3 +127,15 @@ def beam_weights(B: int, N: int, seed: int = BASE_SEED, amp: int = 127) -> np.nd
     w[..., 0] = np.clip(np.rint(amp * np.cos(ph)), -127, 127).astype(np.int8)
     w[..., 1] = np.clip(np.rint(-amp * np.sin(ph)), -127, 127).astype(np.int8)
     return w
+
+
+def bundles_of(frames: np.ndarray, n_cyl: int) -> np.ndarray:
+    """Split full-array frames uint8 [n_freq][T][N] into per-cylinder bundles uint8
+    [n_cyl][T][n_freq][N / n_cyl] (the F-engine's delivery format read as R13): cylinder
+    `cyl` holds inputs cyl * (N / n_cyl) .. +N / n_cyl - 1 of every frequency."""
+    f = np.asarray(frames, np.uint8)
+    n_freq, T, N = f.shape
+    n_in = N // n_cyl
+    if n_in * n_cyl != N:
+        raise ValueError("N must be a multiple of n_cyl")
+    return np.ascontiguousarray(f.reshape(n_freq, T, n_cyl, n_in).transpose(2, 1, 0, 3))
