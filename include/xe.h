@@ -195,6 +195,48 @@ int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jo
  * batch shape was first seen, else the default choice.  XE_EAGAIN if none yet. */
 int xe_last_config(int *n_cta, int *tile_n, int *sched);
 
+/* ---- corner turn and input views --------------------------------------------------- */
+
+/* The F-engine delivers each GPU node bundles of four frequency channels, every bundle with
+ * the inputs of one cylinder only; the node combines four bundles into full-array data
+ * (section 2.1; section 2.3: the node completes the transpose; Table tab:computing:
+ * "Re-Order and Pre-Sum").  The paper gives no byte layout; this library reads a bundle as
+ *
+ *   bundles  uint8 [n_cyl][T][n_freq][n_in]    (one cylinder per bundle, contiguous)
+ *   frames   uint8 [n_freq][T][n_cyl * n_in]   full-array input n = cyl * n_in + i
+ *   presums  int32 [n_freq][N][2]              sum over the T samples of {re, im} of x_n
+ *
+ * An input view describes where sample (c, t, n) of a correlation's input lives:
+ *     byte  in + c * chan_stride + t * time_stride + (n / seg_inputs) * seg_stride
+ *              + n % seg_inputs
+ * A plain [C][T][N] input is chan_stride = T N, time_stride = N, seg_inputs = N.  Strides are
+ * in bytes; when every stride and seg_inputs are multiples of 16 (and `in` 16-byte aligned)
+ * the staging kernel loads 16 bytes at a time, otherwise it loads bytes. */
+typedef struct xe_view {
+    int64_t chan_stride;
+    int64_t time_stride;
+    int64_t seg_inputs;
+    int64_t seg_stride;
+} xe_view;
+
+/* Fill *view with the view of n_freq channels of N = n_cyl * n_in inputs held as cylinder
+ * bundles (layout above).  Returns XE_OK or XE_EINVAL. */
+int xe_bundle_view(int n_cyl, int n_freq, int n_in, int64_t T, xe_view *view);
+
+/* As xe_correlate_async (tensor-core path), reading the input through `view` (a host struct
+ * read during the call).  With xe_bundle_view this correlates the bundles directly: the
+ * corner turn happens inside the staging kernel's loads and no frame is materialised.
+ * Returns as xe_correlate_async. */
+int xe_correlate_view(const uint8_t *in, const xe_view *view, int N, int64_t T, int n_chan, int32_t *vis,
+                      void *stream);
+
+/* Materialise the corner turn: bundles -> frames (layouts above), and, if presums is not
+ * NULL, the per-input pre-sums.  All pointers are caller-owned DEVICE memory.  Enqueued on
+ * `stream`.  Returns XE_OK, XE_EINVAL, XE_EOVERFLOW (T > XE_MAX_T), XE_ENOMEM, XE_ECUDA or
+ * XE_ENODEV. */
+int xe_corner_turn(const uint8_t *bundles, int n_cyl, int n_freq, int n_in, int64_t T, uint8_t *frames,
+                   int32_t *presums, void *stream);
+
 /* ---- phased-array beams ------------------------------------------------------------ */
 
 /* Besides the correlation, the X-engine nodes form phased-array beams for pulsar timing

@@ -402,6 +402,8 @@ struct Scratch {
     size_t cvis_bytes = 0;
     uint8_t *beam_wt = nullptr;   // beam weights as MMA operand tiles
     size_t beam_wt_bytes = 0;
+    int32_t *corner_partial = nullptr;   // per-block pre-sums of the corner turn
+    size_t corner_partial_bytes = 0;
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
@@ -563,6 +565,22 @@ static thread_local cudaEvent_t g_last_ev[4] = {nullptr, nullptr, nullptr, nullp
 static thread_local const int *g_job_acc = nullptr;   // per-job accumulate flags (stream server)
 // Per-job masking of a masked batch (null for plain batches).
 static thread_local const xe_masked_job *g_job_mask = nullptr;
+// Per-job input views of a view call (null: every input is a plain [C][T][N] array).
+static thread_local const xe_view *g_job_view = nullptr;
+
+static void set_view(JobDev &jd, const xe_job &j, const xe_view *v) {
+    if (v) {
+        jd.s_c = v->chan_stride;
+        jd.s_t = v->time_stride;
+        jd.s_seg = v->seg_stride;
+        jd.seg = int(v->seg_inputs);
+    } else {
+        jd.s_c = j.T * int64_t(j.N);
+        jd.s_t = j.N;
+        jd.s_seg = 0;
+        jd.seg = j.N;
+    }
+}
 
 static int check_job(const uint8_t *in, int N, int64_t T, int C, const int32_t *vis) {
     if (!in || !vis) return fail(XE_EINVAL, "null input or output pointer");
@@ -597,6 +615,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 jd.vis = j.vis;
                 jd.T = j.T;
                 jd.T_in = j.T;
+                set_view(jd, j, nullptr);
                 jd.N = j.N;
                 jd.C = j.n_chan;
                 jd.vis_chan_elems = int64_t(j.N) * (j.N + 1);
@@ -656,6 +675,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 jd.T = Tw;
                 jd.t0 = w * wt;
                 jd.T_in = j.T;
+                set_view(jd, j, g_job_view ? &g_job_view[act[g0 + size_t(k)]] : nullptr);
                 jd.N = j.N;
                 jd.n_pad = n_pad_of(j.N);
                 jd.C = j.n_chan;
@@ -1209,6 +1229,66 @@ int xe_beamform(const uint8_t *in, int N, int64_t T, int n_chan, const int8_t *w
         for (int k = 0; k < 4; ++k) g_last_ev[k] = sc->ev[k];
     }
     return XE_OK;
+}
+
+int xe_corner_turn(const uint8_t *bundles, int n_cyl, int n_freq, int n_in, int64_t T, uint8_t *frames,
+                   int32_t *presums, void *stream) {
+    if (!bundles || !frames) return fail(XE_EINVAL, "null bundle or frame pointer");
+    if (n_cyl < 1 || n_freq < 1 || n_in < 1 || T < 1 || int64_t(n_cyl) * n_in > XE_MAX_N)
+        return fail(XE_EINVAL, "bad bundle shape");
+    if (T > XE_MAX_T) return fail(XE_EOVERFLOW, "T=%lld > %lld: pre-sums could overflow int32", (long long)T,
+                                  (long long)XE_MAX_T);
+    if (presums && (reinterpret_cast<uintptr_t>(presums) & 3)) return fail(XE_EINVAL, "presums must be 4-byte aligned");
+    std::lock_guard<std::mutex> lk(g_mu);
+    const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+    Device *d = nullptr;
+    int rc = get_device(&d);
+    if (rc) return rc;
+    Scratch *sc = nullptr;
+    rc = get_scratch(d, s, &sc);
+    if (rc) return rc;
+    if (presums) {
+        rc = grow(reinterpret_cast<void **>(&sc->corner_partial), &sc->corner_partial_bytes,
+                  size_t(corner_partial_elems(n_cyl, n_freq, n_in, T)) * sizeof(int32_t), false);
+        if (rc) return rc;
+    }
+    const bool timing = g_opt.timing != 0;
+    if (timing) XE_CUDA(cudaEventRecord(sc->ev[0], s));
+    if (timing) XE_CUDA(cudaEventRecord(sc->ev[1], s));
+    XE_CUDA(launch_corner_turn(bundles, n_cyl, n_freq, n_in, T, frames, sc->corner_partial, presums, s));
+    if (timing) {
+        XE_CUDA(cudaEventRecord(sc->ev[2], s));
+        XE_CUDA(cudaEventRecord(sc->ev[3], s));
+        for (int k = 0; k < 4; ++k) g_last_ev[k] = sc->ev[k];
+    }
+    return XE_OK;
+}
+
+int xe_bundle_view(int n_cyl, int n_freq, int n_in, int64_t T, xe_view *view) {
+    if (!view) return fail(XE_EINVAL, "null view");
+    if (n_cyl < 1 || n_freq < 1 || n_in < 1 || T < 1 || int64_t(n_cyl) * n_in > XE_MAX_N)
+        return fail(XE_EINVAL, "bad bundle shape");
+    view->chan_stride = n_in;
+    view->time_stride = int64_t(n_freq) * n_in;
+    view->seg_inputs = n_in;
+    view->seg_stride = T * n_freq * int64_t(n_in);
+    return XE_OK;
+}
+
+int xe_correlate_view(const uint8_t *in, const xe_view *view, int N, int64_t T, int n_chan, int32_t *vis,
+                      void *stream) {
+    int rc = check_job(in, N, T, n_chan, vis);
+    if (rc) return rc;
+    if (!view) return fail(XE_EINVAL, "null view");
+    if (view->seg_inputs < 1 || view->seg_inputs > XE_MAX_N || view->chan_stride < 0 || view->time_stride < 0 ||
+        view->seg_stride < 0)
+        return fail(XE_EINVAL, "bad view: seg_inputs must lie in [1, %d] and strides be >= 0", XE_MAX_N);
+    xe_job j{in, vis, N, n_chan, T};
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_job_view = view;
+    rc = run_jobs(&j, 1, XE_ALGO_TC, reinterpret_cast<cudaStream_t>(stream));
+    g_job_view = nullptr;
+    return rc;
 }
 
 int xe_correlate_masked(const uint8_t *in, const uint8_t *flags, int N, int64_t T, int n_chan,

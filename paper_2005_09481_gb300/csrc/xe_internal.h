@@ -20,7 +20,7 @@ constexpr int kStageBytes = 2 * kAPlane + 2 * kBPlane;  // 48 KB
 constexpr int kTcThreads = 192;    // 4 epilogue warps, 1 producer warp, 1 MMA warp
 constexpr int kEpiStageBytes = 4 * 32 * 33 * 8;  // per epilogue warp: 32 x 33 int2 transpose buffer
 constexpr int kTcSmem = kStages * kStageBytes + kEpiStageBytes + 1024 /*align*/ + 256 /*barriers*/;
-constexpr int kMaxJobs = 256;      // jobs per launch (passed by value)
+constexpr int kMaxJobs = 208;      // jobs per launch (passed by value, within the 32 KB limit)
 
 // Samples per stage: 64 with 1-byte (e4m3) operands, 32 with 2-byte (f16) operands.
 __host__ __device__ constexpr int samples_per_stage(int elem_bytes) {
@@ -54,7 +54,20 @@ struct JobDev {
     uint8_t *count_planes;    // masked job with counts: where the staging kernel writes the
                               // validity planes of its count job (same layout as `planes`,
                               // re slots only), else null
+    // Input view: sample (c, t, n) of the job (t counted from the job's first sample) is the
+    // byte in + c * s_c + t * s_t + (n / seg) * s_seg + n % seg.  A plain [C][T][N] input has
+    // s_c = T N, s_t = N, seg = N; cylinder bundles [n_cyl][T][C][n_in] (the corner turn done
+    // by the staging kernel's loads) have s_c = n_in, s_t = C n_in, seg = n_in, s_seg = T C n_in.
+    int64_t s_c;
+    int64_t s_t;
+    int64_t s_seg;
+    int seg;
 };
+
+// Byte address of sample (c, t, n) of a job's input (see JobDev).
+__host__ __device__ __forceinline__ int64_t view_offset(const JobDev &jb, int c, int64_t t, int n) {
+    return int64_t(c) * jb.s_c + t * jb.s_t + int64_t(n / jb.seg) * jb.s_seg + (n % jb.seg);
+}
 
 // JobDev::mode bits.  A masked job is staged by the masking variant of the staging kernel:
 // each sample byte becomes (byte ^ key) & valid, where key = 0x88 for offset-binary input
@@ -172,6 +185,12 @@ cudaError_t launch_beam_weights(const int8_t *w, int b0, int nb, int N, int ncol
 cudaError_t launch_beam(const BeamDev &bd, cudaStream_t s);
 int beam_ncols(int B);
 size_t beam_wt_bytes(int B, int N);
+
+// ---- corner turn (xe_corner.cu) ---------------------------------------------------------
+
+cudaError_t launch_corner_turn(const uint8_t *bundles, int n_cyl, int n_freq, int n_in, int64_t T,
+                               uint8_t *frames, int32_t *partial, int32_t *presums, cudaStream_t s);
+int64_t corner_partial_elems(int n_cyl, int n_freq, int n_in, int64_t T);
 
 // Kernel launchers (xe_tc.cu, xe_imma.cu, xe_mask.cu).  `masked` selects the masking
 // variant of the e4m3 staging kernel (any job with kModeMasked).

@@ -152,6 +152,10 @@ int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_
     jd.T = T;
     jd.t0 = 0;
     jd.T_in = T;
+    jd.s_c = T * int64_t(N);
+    jd.s_t = N;
+    jd.s_seg = 0;
+    jd.seg = N;
     jd.N = N;
     jd.n_pad = n_pad;
     jd.C = n_chan;

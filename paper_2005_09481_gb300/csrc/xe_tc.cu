@@ -53,6 +53,13 @@ __constant__ NibbleCodes c_codes_f16 = make_codes(2);
 
 // ---- staging kernel ----------------------------------------------------------------------
 
+// Every 16-byte piece of the job's input (16 consecutive inputs of one sample) starts 16-byte
+// aligned and lies inside one segment, so the vector load paths apply.
+__device__ __forceinline__ bool view_vec_ok(const JobDev &jb) {
+    return (jb.N & 15) == 0 && (jb.seg & 15) == 0 && ((jb.s_c | jb.s_t | jb.s_seg) & 15) == 0 &&
+           (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0;
+}
+
 __device__ __forceinline__ int find_job(const JobTable &jt, int64_t blk) {
     int lo = 0, hi = jt.n_jobs - 1;
     while (lo < hi) {
@@ -86,24 +93,23 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ JobT
     const int c = int(rest / jb.kblocks);
     const int n0 = nb * 256;
     const int64_t t0 = int64_t(kb) * KS;
-    const uint8_t *src = jb.in + (int64_t(c) * jb.T_in + jb.t0) * jb.N;
 
     // Load the packed [KS][256] tile; zeros outside [0,T) x [0,N) (value 0 + 0i, exact).
-    if ((jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0) {
+    if (view_vec_ok(jb)) {
         const int seg = tid & 15;          // 16-byte segment of the 256-byte row
         for (int r = tid >> 4; r < KS; r += 16) {
             const int64_t t = t0 + r;
             const int n = n0 + seg * 16;
             uint4 v = make_uint4(0, 0, 0, 0);
             if (t < jb.T && n < jb.N)
-                v = __ldg(reinterpret_cast<const uint4 *>(src + t * jb.N + n));
+                v = __ldg(reinterpret_cast<const uint4 *>(jb.in + view_offset(jb, c, jb.t0 + t, n)));
             *reinterpret_cast<uint4 *>(&raw[r][seg * 16]) = v;
         }
     } else {
         for (int r = 0; r < KS; ++r) {
             const int64_t t = t0 + r;
             const int n = n0 + tid;
-            raw[r][tid] = (t < jb.T && n < jb.N) ? src[t * jb.N + n] : uint8_t(0);
+            raw[r][tid] = (t < jb.T && n < jb.N) ? jb.in[view_offset(jb, c, jb.t0 + t, n)] : uint8_t(0);
         }
     }
     __syncthreads();
@@ -227,9 +233,7 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
     const int tid = threadIdx.x;
     const int64_t total = jt.total_stage_blocks;
 
-    auto vec_ok = [&](const JobDev &jb) {
-        return (jb.N & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.in) & 15) == 0;
-    };
+    auto vec_ok = [&](const JobDev &jb) { return view_vec_ok(jb); };
     // Flag rows can be copied 16 bytes at a time when every row starts 16-byte aligned.
     auto flag_vec_ok = [&](const JobDev &jb) {
         const int64_t frow = (jb.N + 7) / 8;
@@ -239,15 +243,16 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
     auto issue = [&](int64_t blk, int b) {
         const StageItem it = stage_item(jt, blk);
         const JobDev &jb = *it.jb;
-        const uint8_t *src = jb.in + (int64_t(it.c) * jb.T_in + jb.t0) * jb.N;
         const int seg = tid & 15;
         const int n = it.n0 + seg * 16;
+        // Inputs n..n+15 lie in one segment: one base per item row, rows s_t apart.
+        const uint8_t *src = n < jb.N ? jb.in + view_offset(jb, it.c, jb.t0, n) : jb.in;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int r = (tid >> 4) + 16 * j;
             const int64_t t = int64_t(it.kb) * KS + r;
             const bool ok = t < jb.T && n < jb.N;
-            cp_async16(&raw[b][raw_row(r)][seg * 16], ok ? static_cast<const void *>(src + t * jb.N + n)
+            cp_async16(&raw[b][raw_row(r)][seg * 16], ok ? static_cast<const void *>(src + t * jb.s_t)
                                                  : static_cast<const void *>(jb.in), ok ? 16u : 0u);
         }
         if (MASK && jb.flags && flag_vec_ok(jb) && tid < 128) {
@@ -280,12 +285,12 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
         if (next < total && vec_ok(*stage_item(jt, next).jb)) issue(next, b == 0 ? 2 : b - 1);
         cp_async_commit();
         if (!vec_ok(jb)) {
-            // Scalar path (N not a multiple of 16 or unaligned input): byte loads.
-            const uint8_t *src = jb.in + (int64_t(it.c) * jb.T_in + jb.t0) * jb.N;
+            // Scalar path (unaligned rows or segments, or an unaligned input): byte loads.
+            const int n = it.n0 + tid;
+            const uint8_t *src = n < jb.N ? jb.in + view_offset(jb, it.c, jb.t0, n) : jb.in;
             for (int r = 0; r < KS; ++r) {
                 const int64_t t = int64_t(it.kb) * KS + r;
-                const int n = it.n0 + tid;
-                raw[b][raw_row(r)][tid] = (t < jb.T && n < jb.N) ? src[t * jb.N + n] : uint8_t(0);
+                raw[b][raw_row(r)][tid] = (t < jb.T && n < jb.N) ? src[t * jb.s_t] : uint8_t(0);
             }
         }
         if (MASK && jb.flags && !(vec_ok(jb) && flag_vec_ok(jb))) {

@@ -74,6 +74,9 @@ def load():
             "xe_correlate_masked": ([p, p, i32, i64, i32, i32, p, p, i32, p], i32),
             "xe_correlate_masked_batch": ([p, i32, p], i32),
             "xe_beamform": ([p, i32, i64, i32, p, i32, p, p], i32),
+            "xe_bundle_view": ([i32, i32, i32, i64, p], i32),
+            "xe_correlate_view": ([p, p, i32, i64, i32, p, p], i32),
+            "xe_corner_turn": ([p, i32, i32, i32, i64, p, p, p], i32),
             "xe_device_status": ([p], i32),
             "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
             "xe_plan_dump": ([p, p, p, i32, i32, i32, i32, p, i64], i64),
@@ -348,6 +351,61 @@ def correlate_masked_batch(jobs, stream=None):
     _check(load().xe_correlate_masked_batch(arr, len(jobs), _stream_handle(stream)),
            "xe_correlate_masked_batch")
     return [(j["vis"], j.get("counts")) for j in jobs]
+
+
+class View(ctypes.Structure):
+    _fields_ = [("chan_stride", ctypes.c_int64), ("time_stride", ctypes.c_int64),
+                ("seg_inputs", ctypes.c_int64), ("seg_stride", ctypes.c_int64)]
+
+
+def bundle_view(n_cyl: int, n_freq: int, n_in: int, T: int) -> View:
+    """The input view of n_freq channels held as cylinder bundles [n_cyl][T][n_freq][n_in]."""
+    v = View()
+    _check(load().xe_bundle_view(n_cyl, n_freq, n_in, T, ctypes.byref(v)), "xe_bundle_view")
+    return v
+
+
+def correlate_view(inp, view: View, N: int, T: int, C: int = 1, out=None, stream=None):
+    """Correlation of C channels whose samples are addressed through `view` (device uint8
+    tensor `inp` holding them) -> int32 [C, B, 2]."""
+    import torch
+    if inp.dtype != torch.uint8 or not inp.is_cuda:
+        raise ValueError("input must be a uint8 CUDA tensor")
+    if out is None:
+        out = empty_vis(N, C, inp.device)
+    rc = load().xe_correlate_view(ctypes.c_void_p(inp.data_ptr()), ctypes.byref(view), N, T, C,
+                                  ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
+    _check(rc, "xe_correlate_view")
+    return out
+
+
+def correlate_bundles(bundles, n_cyl: int, n_freq: int, n_in: int, T: int, out=None, stream=None):
+    """Full-array correlation of n_freq channels straight from cylinder bundles
+    uint8 [n_cyl, T, n_freq, n_in] (corner turn fused into the staging loads)."""
+    if bundles.numel() != n_cyl * T * n_freq * n_in:
+        raise ValueError("bundles must hold n_cyl * T * n_freq * n_in bytes")
+    return correlate_view(bundles, bundle_view(n_cyl, n_freq, n_in, T), n_cyl * n_in, T, n_freq,
+                          out=out, stream=stream)
+
+
+def corner_turn(bundles, n_cyl: int, n_freq: int, n_in: int, T: int, frames=None, presums: bool = True,
+                stream=None):
+    """Bundles uint8 [n_cyl, T, n_freq, n_in] -> (frames uint8 [n_freq, T, n_cyl * n_in],
+    pre-sums int32 [n_freq, N, 2] or None)."""
+    import torch
+    if bundles.dtype != torch.uint8 or not bundles.is_cuda or not bundles.is_contiguous():
+        raise ValueError("bundles must be a contiguous uint8 CUDA tensor")
+    if bundles.numel() != n_cyl * T * n_freq * n_in:
+        raise ValueError("bundles must hold n_cyl * T * n_freq * n_in bytes")
+    N = n_cyl * n_in
+    if frames is None:
+        frames = torch.empty((n_freq, T, N), dtype=torch.uint8, device=bundles.device)
+    ps = torch.empty((n_freq, N, 2), dtype=torch.int32, device=bundles.device) if presums else None
+    rc = load().xe_corner_turn(ctypes.c_void_p(bundles.data_ptr()), n_cyl, n_freq, n_in, T,
+                               ctypes.c_void_p(frames.data_ptr()),
+                               ctypes.c_void_p(ps.data_ptr() if ps is not None else 0), _stream_handle(stream))
+    _check(rc, "xe_corner_turn")
+    return frames, ps
 
 
 def empty_beams(T: int, B: int, C: int = 1, device="cuda"):
