@@ -13,7 +13,9 @@ With --gpus N > 1 (under torch.distributed.run) every rank correlates its own ch
 --impl reference times the CPU oracle (plain int64 triple loop) on this host's cores on a
 bounded sample of the same workload.  --workload masked (also summarised under "masked" in
 the default line) times the flag-masked correlation with valid-sample counts;
---workload beams (also under "beams") the 10 phased-array beams of the same input.
+--workload beams (also under "beams") the 10 phased-array beams of the same input;
+--workload corner (also under "corner") the corner turn of cylinder bundles and the
+correlation read straight from the bundles.
 """
 from __future__ import annotations
 
@@ -369,6 +371,90 @@ def run_beam_workload(args):
     return 0
 
 
+CORNER_WORKLOAD = ("corner turn of 4 cylinder bundles x 4 frequencies (512 inputs each) into 4 full-array "
+                   "channels, N=2048, T=32768, with per-input pre-sums; and the fused bundle-view correlation")
+
+
+def measure_corner(steps, warmup, dev, flush, check=True):
+    """Corner turn (+ pre-sums) of the CHIME node shape, and the 4-channel correlation read
+    straight from the bundles against the same correlation of materialised frames."""
+    import numpy as np
+    import torch
+    from paper_2005_09481_gb300 import synth, xe
+    n_cyl, n_freq, n_in, T = 4, 4, 512, T_SAMPLES
+    N = n_cyl * n_in
+    frames = synth.gauss_plane(N, T, n_freq)
+    d_b = torch.from_numpy(synth.bundles_of(frames, n_cyl)).to(dev)
+    d_f = torch.from_numpy(frames).to(dev)
+    out = torch.empty_like(d_f)
+    vis = xe.empty_vis(N, n_freq, dev)
+    stream = torch.cuda.current_stream(dev)
+    xe.set_timing(True)
+
+    def timed(fn):
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+        parts = []
+        for k, (a, b) in enumerate(ev):
+            flush.fill_(k & 0xFF)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            parts.append(xe.last_timing())
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in ev) / steps, parts
+
+    ms_ct, p_ct = timed(lambda: xe.corner_turn(d_b, n_cyl, n_freq, n_in, T, frames=out, presums=False, stream=stream))
+    ms_ps, _ = timed(lambda: xe.corner_turn(d_b, n_cyl, n_freq, n_in, T, frames=out, presums=True, stream=stream))
+    ms_cf, p_cf = timed(lambda: xe.correlate(d_f, N, T, n_freq, out=vis, stream=stream))
+    ms_cb, p_cb = timed(lambda: xe.correlate_bundles(d_b, n_cyl, n_freq, n_in, T, out=vis, stream=stream))
+    xe.set_timing(False)
+    xe.device_status(stream)
+    _, hbm, src = peaks()
+    kern_ms = statistics.mean(p[1] for p in p_ct)
+    byt = 2 * n_cyl * T * n_freq * n_in
+    res = {"corner_turn_ms": ms_ct, "corner_turn_with_presums_ms": ms_ps,
+           "correlate_from_frames_ms": ms_cf, "correlate_from_bundles_ms": ms_cb,
+           "stage_from_frames_ms": statistics.mean(p[0] for p in p_cf),
+           "stage_from_bundles_ms": statistics.mean(p[0] for p in p_cb),
+           "workload": CORNER_WORKLOAD,
+           "roofline": {"bound": "hbm", "achieved": byt / (kern_ms * 1e-3) / 1e9, "peak": hbm, "unit": "GB/s",
+                        "frac": byt / (kern_ms * 1e-3) / 1e9 / hbm, "traffic": None,
+                        "kernel": "corner_turn_kernel<16> (no pre-sums)",
+                        "algorithmic": "1 B read + 1 B written per sample",
+                        "peak_source": f"{src}: hbm_gbs of MEASURED_PEAKS.json"}}
+    if check:
+        import oracle
+        xe.corner_turn(d_b, n_cyl, n_freq, n_in, T, frames=out, presums=False)
+        xe.correlate_bundles(d_b, n_cyl, n_freq, n_in, T, out=vis)
+        torch.cuda.synchronize()
+        res["exact"] = bool(np.array_equal(out.cpu().numpy(), frames) and
+                            np.array_equal(vis[0].cpu().numpy(), oracle.correlate_dense(frames[:1], N, T, 1)[0]))
+    return res
+
+
+def run_corner_workload(args):
+    import torch
+    from paper_2005_09481_gb300 import xe
+    xe.load()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    with ClockSampler(uuid) as clk:
+        m = measure_corner(args.steps, args.warmup, dev, flush)
+    cm = xe.cmac(N_IN, T_SAMPLES, 4)
+    line = {"metric": METRIC, "value": cm / (m["correlate_from_bundles_ms"] * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": m["correlate_from_bundles_ms"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+            "config": {"workload": CORNER_WORKLOAD, "N": N_IN, "T": T_SAMPLES, "n_chan": 4,
+                       "l2": f"flushed between timed steps ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "roofline": m["roofline"], "corner": m, "clocks": clk.summary(), "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_masked_workload(args):
     import torch
     from paper_2005_09481_gb300 import xe
@@ -429,9 +515,10 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="xe", choices=["xe", "reference"])
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch16", "uneven64", "stream", "masked", "beams"])
+                    choices=["headline", "batch16", "uneven64", "stream", "masked", "beams", "corner"])
     ap.add_argument("--no-masked", action="store_true")
     ap.add_argument("--no-beams", action="store_true")
+    ap.add_argument("--no-corner", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-channels", type=int, default=256)
@@ -453,6 +540,8 @@ def main():
         return run_masked_workload(args)
     if args.workload == "beams":
         return run_beam_workload(args)
+    if args.workload == "corner":
+        return run_corner_workload(args)
 
     import numpy as np
     import torch
@@ -540,17 +629,22 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_value = ws * cm_step * k_e2e / float(t.item())
 
+    # The real-time stream leg runs before the legs whose exactness checks keep the host's
+    # cores busy (its producer is paced on the host).
+    stream = None
+    if ws == 1 and not args.no_stream:
+        from paper_2005_09481_gb300 import serve
+        stream = serve.run_realtime(args.stream_channels, args.stream_seconds)
+
     masked = None
     if ws == 1 and not args.no_masked:
         masked = measure_masked(max(20, min(300, args.steps // 4)), 5, dev, flush)
     beams = None
     if ws == 1 and not args.no_beams:
         beams = measure_beams(max(20, min(300, args.steps // 4)), 5, dev, flush)
-
-    stream = None
-    if ws == 1 and not args.no_stream:
-        from paper_2005_09481_gb300 import serve
-        stream = serve.run_realtime(args.stream_channels, args.stream_seconds)
+    corner = None
+    if ws == 1 and not args.no_corner:
+        corner = measure_corner(max(10, min(50, args.steps // 20)), 3, dev, flush)
 
     if rank == 0:
         bf16, hbm, src = peaks()
@@ -598,6 +692,7 @@ def main():
                        if stream else None),
             "masked": masked,
             "beams": beams,
+            "corner": corner,
             "paper_context": {"fiji_chip_cmac_s": 1.10e12, "note": "derived from Table tab:computing "
                               "(93.4 ms per 49152-sample block at N=2048), AMD S9300x2, 722 MHz"},
         }
