@@ -99,6 +99,21 @@ int xe_correlate_async(const uint8_t *in, int N, int64_t T, int n_chan, int32_t 
 int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis,
                       int algo);
 
+/* Asynchronous host-buffer correlation for callers that feed a stream of host blocks.
+ * Enqueues the copies and the correlation of host_in into slot `slot` (0 <= slot <
+ * XE_HOST_SLOTS; each slot owns device buffers inside the library) and returns at once;
+ * host_vis receives the visibilities, valid once xe_host_wait(slot) has returned XE_OK.
+ * Both host buffers must stay untouched until then (pinned memory is required for the
+ * copies to overlap).  Successive calls on different slots overlap: the device -> host copy
+ * of one result runs while the next block is copied in and correlated.  Calling on a slot
+ * that is still in flight returns XE_EAGAIN.  The input is copied in chunks of
+ * "host_chunk_t" samples (option), each correlated as soon as it has landed (tensor-core
+ * path).  Returns as xe_correlate_host (XE_ETIMEOUT from xe_host_wait if a device wait gave
+ * up). */
+#define XE_HOST_SLOTS 4
+int xe_correlate_host_async(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis, int slot);
+int xe_host_wait(int slot);
+
 /* ---- batched correlation (one persistent launch over many jobs) ------------------- */
 
 /* One job of a batch: n_chan channels of N inputs over T samples, with its own
@@ -397,7 +412,10 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *   "count_weight"   cost of a count job's k-iteration in schedule 5, percent of a data
  *                    job's (1 .. 100, default 50);
  *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 5, percent of
- *                    a whole tile (0 .. 100, default 2).
+ *                    a whole tile (0 .. 100, default 2);
+ *   "host_chunk_t"   samples per chunk of the host-buffer entry points' copy/correlate
+ *                    pipeline (0 = one copy then one correlation; else a multiple of 64;
+ *                    default 8192).
  * Returns XE_OK or XE_EINVAL. */
 int xe_set_option(const char *key, int64_t value);
 

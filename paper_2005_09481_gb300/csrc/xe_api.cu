@@ -52,6 +52,8 @@ struct Options {
     int autotune = 0;                      // 1: time candidate plans on first sight of a shape
     int timing = 0;
     int inject_stall = 0;                  // test hook for the bounded-wait path (next call only)
+    int64_t host_chunk_t = 8192;           // samples per pipelined chunk of xe_correlate_host
+                                           // (0: one copy, then one correlation)
     int count_weight = 50;                 // cost of a count-job k-iteration, % of a data one
     int part_overhead = 2;                 // modelled cost of one extra tile part, % of a
                                            // whole data tile (workspace fix-up)
@@ -407,13 +409,27 @@ struct Scratch {
     cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
 };
 
+// One slot of the host-buffer entry points: its own device input and output buffers, so that
+// the device -> host copy of one slot's result overlaps the next slot's copies and compute.
 struct HostIO {
-    cudaStream_t stream = nullptr;
+    std::vector<cudaEvent_t> landed; // one per chunk in flight: its copy has completed
+    cudaEvent_t computed = nullptr;  // the slot's correlation has completed
+    cudaEvent_t delivered = nullptr; // the slot's result is in host memory
+    bool in_flight = false;
     uint8_t *d_in = nullptr;
     size_t in_bytes = 0;
     int32_t *d_vis = nullptr;
     size_t vis_bytes = 0;
 };
+
+// Streams shared by the slots: host -> device copies, compute, device -> host copies.
+struct HostStreams {
+    cudaStream_t copy = nullptr;
+    cudaStream_t compute = nullptr;
+    cudaStream_t d2h = nullptr;
+};
+
+constexpr int kHostSlots = XE_HOST_SLOTS + 1;   // the last one serves xe_correlate_host
 
 struct LaunchRec {
     int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor, 3 counts
@@ -434,7 +450,8 @@ struct GraphRec {
 struct Device {
     int id = -1;
     int n_sm = 0;
-    HostIO io;
+    HostIO io[kHostSlots];
+    HostStreams hs;
     std::map<std::vector<int64_t>, DevPlan *> plans;
     std::map<std::vector<int64_t>, TuneCfg> tuned;
     std::map<cudaStream_t, Scratch *> scratch;
@@ -1049,6 +1066,10 @@ int xe_set_option(const char *key, int64_t value) {
         g_opt.timing = value ? 1 : 0;
     } else if (!strcmp(key, "inject_stall")) {
         g_opt.inject_stall = value ? 1 : 0;
+    } else if (!strcmp(key, "host_chunk_t")) {
+        if (value != 0 && (value < 64 || value > XE_MAX_T || value % 64 != 0))
+            return fail(XE_EINVAL, "host_chunk_t must be 0 or a multiple of 64 in [64, %lld]", (long long)XE_MAX_T);
+        g_opt.host_chunk_t = value;
     } else if (!strcmp(key, "count_weight")) {
         if (value < 1 || value > 100) return fail(XE_EINVAL, "count_weight must lie in [1, 100]");
         g_opt.count_weight = int(value);
@@ -1104,31 +1125,128 @@ int xe_correlate(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis) 
     return xe_correlate_async(in, N, T, n_chan, vis, XE_ALGO_AUTO, nullptr);
 }
 
-int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis,
-                      int algo) {
+// Enqueue one host-buffer correlation into slot `slot` (the caller holds g_mu): copies of the
+// input on the copy stream, chunk by chunk; the correlation on the compute stream, each chunk
+// as soon as its bytes have landed (the first chunk overwrites, later ones add: int32 sums of
+// exact partial sums are exact); the copy of the result on the device -> host stream.
+static int host_enqueue(Device *d, int slot, const uint8_t *host_in, int N, int64_t T, int n_chan,
+                        int32_t *host_vis, int algo) {
+    HostIO &io = d->io[slot];
+    HostStreams &hs = d->hs;
+    if (io.in_flight) return fail(XE_EAGAIN, "host slot %d is still in flight: call xe_host_wait first", slot);
+    if (!hs.copy) {
+        XE_CUDA(cudaStreamCreateWithFlags(&hs.copy, cudaStreamNonBlocking));
+        XE_CUDA(cudaStreamCreateWithFlags(&hs.compute, cudaStreamNonBlocking));
+        XE_CUDA(cudaStreamCreateWithFlags(&hs.d2h, cudaStreamNonBlocking));
+    }
+    if (!io.computed) {
+        XE_CUDA(cudaEventCreateWithFlags(&io.computed, cudaEventDisableTiming));
+        XE_CUDA(cudaEventCreateWithFlags(&io.delivered, cudaEventDisableTiming));
+    }
+    const size_t in_bytes = size_t(n_chan) * size_t(T) * size_t(N);
+    const size_t vis_bytes = size_t(n_chan) * size_t(N) * size_t(N + 1) * sizeof(int32_t);
+    int rc = grow(reinterpret_cast<void **>(&io.d_in), &io.in_bytes, in_bytes, false);
+    if (rc) return rc;
+    rc = grow(reinterpret_cast<void **>(&io.d_vis), &io.vis_bytes, vis_bytes, false);
+    if (rc) return rc;
+    const int64_t chunk = g_opt.host_chunk_t;
+    const int64_t n_chunks = (algo == XE_ALGO_IMMA || chunk == 0 || chunk >= T) ? 1 : (T + chunk - 1) / chunk;
+    const int64_t step = n_chunks == 1 ? T : chunk;
+    while (int64_t(io.landed.size()) < std::min<int64_t>(n_chunks, 64)) {
+        cudaEvent_t e;
+        XE_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        io.landed.push_back(e);
+    }
+    const size_t row = size_t(N);
+    for (int64_t k = 0; k < n_chunks; ++k) {
+        const int64_t t0 = k * step, t1 = std::min(T, t0 + step);
+        cudaEvent_t ev = io.landed[size_t(k % int64_t(io.landed.size()))];
+        if (k >= int64_t(io.landed.size())) XE_CUDA(cudaEventSynchronize(ev));   // event reuse
+        for (int c = 0; c < n_chan; ++c) {
+            const size_t off = (size_t(c) * size_t(T) + size_t(t0)) * row;
+            XE_CUDA(cudaMemcpyAsync(io.d_in + off, host_in + off, size_t(t1 - t0) * row, cudaMemcpyHostToDevice,
+                                    hs.copy));
+        }
+        XE_CUDA(cudaEventRecord(ev, hs.copy));
+        XE_CUDA(cudaStreamWaitEvent(hs.compute, ev, 0));
+        if (n_chunks == 1) {
+            xe_job j{io.d_in, io.d_vis, N, n_chan, T};
+            rc = run_jobs(&j, 1, algo == XE_ALGO_AUTO ? XE_ALGO_TC : algo, hs.compute);
+        } else {
+            const xe_view view{T * int64_t(N), int64_t(N), int64_t(N), 0};
+            xe_job j{io.d_in + size_t(t0) * row, io.d_vis, N, n_chan, t1 - t0};
+            g_job_view = &view;
+            rc = run_jobs(&j, 1, XE_ALGO_TC, hs.compute, k > 0 ? 1 : 0);
+            g_job_view = nullptr;
+        }
+        if (rc) return rc;
+    }
+    XE_CUDA(cudaEventRecord(io.computed, hs.compute));
+    XE_CUDA(cudaStreamWaitEvent(hs.d2h, io.computed, 0));
+    XE_CUDA(cudaMemcpyAsync(host_vis, io.d_vis, vis_bytes, cudaMemcpyDeviceToHost, hs.d2h));
+    XE_CUDA(cudaEventRecord(io.delivered, hs.d2h));
+    io.in_flight = true;
+    return XE_OK;
+}
+
+// Wait for slot `slot`'s result (the caller holds g_mu); reports a device-side timeout.
+static int host_finish(Device *d, int slot) {
+    HostIO &io = d->io[slot];
+    if (!io.in_flight) return XE_OK;
+    io.in_flight = false;
+    XE_CUDA(cudaEventSynchronize(io.delivered));
+    auto it = d->scratch.find(d->hs.compute);
+    if (it != d->scratch.end()) {
+        int st = 0;
+        XE_CUDA(cudaMemcpy(&st, it->second->status, sizeof(int), cudaMemcpyDeviceToHost));
+        if (st != 0) {
+            XE_CUDA(cudaMemset(it->second->status, 0, sizeof(int)));
+            if (it->second->counters) XE_CUDA(cudaMemset(it->second->counters, 0, it->second->counters_bytes));
+            return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
+        }
+    }
+    return XE_OK;
+}
+
+static int check_host_call(const uint8_t *host_in, int N, int64_t T, int n_chan, const int32_t *host_vis, int algo) {
     int rc = check_job(host_in, N, T, n_chan, host_vis);
     if (rc) return rc;
     if (algo != XE_ALGO_AUTO && algo != XE_ALGO_TC && algo != XE_ALGO_IMMA)
         return fail(XE_EINVAL, "unknown algo %d", algo);
+    return XE_OK;
+}
+
+int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis,
+                      int algo) {
+    int rc = check_host_call(host_in, N, T, n_chan, host_vis, algo);
+    if (rc) return rc;
     std::lock_guard<std::mutex> lk(g_mu);
     Device *d = nullptr;
     rc = get_device(&d);
     if (rc) return rc;
-    HostIO &io = d->io;
-    if (!io.stream) XE_CUDA(cudaStreamCreateWithFlags(&io.stream, cudaStreamNonBlocking));
-    const size_t in_bytes = size_t(n_chan) * size_t(T) * size_t(N);
-    const size_t vis_bytes = size_t(n_chan) * size_t(N) * size_t(N + 1) * sizeof(int32_t);
-    rc = grow(reinterpret_cast<void **>(&io.d_in), &io.in_bytes, in_bytes, false);
+    rc = host_enqueue(d, kHostSlots - 1, host_in, N, T, n_chan, host_vis, algo);
+    const int rc2 = host_finish(d, kHostSlots - 1);
+    return rc ? rc : rc2;
+}
+
+int xe_correlate_host_async(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis, int slot) {
+    int rc = check_host_call(host_in, N, T, n_chan, host_vis, XE_ALGO_TC);
     if (rc) return rc;
-    rc = grow(reinterpret_cast<void **>(&io.d_vis), &io.vis_bytes, vis_bytes, false);
+    if (slot < 0 || slot >= XE_HOST_SLOTS) return fail(XE_EINVAL, "slot %d outside [0, %d)", slot, XE_HOST_SLOTS);
+    std::lock_guard<std::mutex> lk(g_mu);
+    Device *d = nullptr;
+    rc = get_device(&d);
     if (rc) return rc;
-    XE_CUDA(cudaMemcpyAsync(io.d_in, host_in, in_bytes, cudaMemcpyHostToDevice, io.stream));
-    xe_job j{io.d_in, io.d_vis, N, n_chan, T};
-    rc = run_jobs(&j, 1, algo == XE_ALGO_AUTO ? XE_ALGO_TC : algo, io.stream);
+    return host_enqueue(d, slot, host_in, N, T, n_chan, host_vis, XE_ALGO_TC);
+}
+
+int xe_host_wait(int slot) {
+    if (slot < 0 || slot >= XE_HOST_SLOTS) return fail(XE_EINVAL, "slot %d outside [0, %d)", slot, XE_HOST_SLOTS);
+    std::lock_guard<std::mutex> lk(g_mu);
+    Device *d = nullptr;
+    int rc = get_device(&d);
     if (rc) return rc;
-    XE_CUDA(cudaMemcpyAsync(host_vis, io.d_vis, vis_bytes, cudaMemcpyDeviceToHost, io.stream));
-    XE_CUDA(cudaStreamSynchronize(io.stream));
-    return XE_OK;
+    return host_finish(d, slot);
 }
 
 int xe_correlate_batch(const xe_job *jobs, int n_jobs, int use_graph, void *stream) {

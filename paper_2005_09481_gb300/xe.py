@@ -63,6 +63,8 @@ def load():
             "xe_correlate": ([p, i32, i64, i32, p], i32),
             "xe_correlate_async": ([p, i32, i64, i32, p, i32, p], i32),
             "xe_correlate_host": ([p, i32, i64, i32, p, i32], i32),
+            "xe_correlate_host_async": ([p, i32, i64, i32, p, i32], i32),
+            "xe_host_wait": ([i32], i32),
             "xe_correlate_batch": ([p, i32, i32, p], i32),
             "xe_correlate_noalloc": ([p, i32, i64, i32, p, p], i32),
             "xe_correlate_accumulate": ([p, i32, p], i32),
@@ -256,6 +258,29 @@ def correlate_host(inp, N: int, T: int, C: int = 1, out=None, algo: str = "auto"
                                   ctypes.c_void_p(out.data_ptr()), ALGOS[algo])
     _check(rc, "xe_correlate_host")
     return out
+
+
+HOST_SLOTS = 4
+
+
+def correlate_host_async(inp, N: int, T: int, C: int = 1, out=None, slot: int = 0):
+    """Enqueue a host-buffer correlation into `slot` and return (out, slot) at once; `out`
+    (pinned host int32 [C, B, 2]) is valid after host_wait(slot).  Keep `inp` and `out`
+    alive and untouched until then."""
+    import torch
+    _shape(inp, N, T, C)
+    if inp.is_cuda:
+        raise ValueError("correlate_host_async takes host tensors")
+    if out is None:
+        out = torch.empty((C, n_baselines(N), 2), dtype=torch.int32, pin_memory=True)
+    rc = load().xe_correlate_host_async(ctypes.c_void_p(inp.data_ptr()), N, T, C,
+                                        ctypes.c_void_p(out.data_ptr()), slot)
+    _check(rc, "xe_correlate_host_async")
+    return out, slot
+
+
+def host_wait(slot: int):
+    _check(load().xe_host_wait(slot), "xe_host_wait")
 
 
 def correlate_batch(jobs, use_graph: bool = False, stream=None):

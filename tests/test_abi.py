@@ -111,6 +111,16 @@ def test_beamform_argument_validation_before_any_device_call():
     assert b"n_beams" in L.xe_last_error()
 
 
+def test_host_async_validation_before_any_device_call():
+    L = xe.load()
+    buf = (ctypes.c_uint8 * 64)()
+    out = (ctypes.c_int32 * 64)()
+    assert L.xe_correlate_host_async(buf, 4, 4, 1, out, -1) == xe.XE_EINVAL
+    assert L.xe_correlate_host_async(buf, 4, 4, 1, out, 4) == xe.XE_EINVAL
+    assert L.xe_correlate_host_async(None, 4, 4, 1, out, 0) == xe.XE_EINVAL
+    assert L.xe_host_wait(7) == xe.XE_EINVAL
+
+
 def test_options_validation():
     with pytest.raises(xe.XeError):
         xe.set_option("operand_bytes", 3)
@@ -118,6 +128,8 @@ def test_options_validation():
         xe.set_option("exact_chunk_t", 1 << 30)
     with pytest.raises(xe.XeError):
         xe.set_option("no_such_option", 1)
+    with pytest.raises(xe.XeError):
+        xe.set_option("host_chunk_t", 100)
     xe.set_option("operand_bytes", 1)
 
 

@@ -166,6 +166,37 @@ def test_host_buffers_entry_point(xe):
     assert_exact(got.numpy(), oracle.correlate_dense(p, N, T, 2), "host")
 
 
+@pytest.mark.parametrize("chunk", [0, 64, 320, 8192])
+def test_host_buffers_pipelined_chunks(xe, chunk):
+    # The host entry point copies chunk k + 1 while chunk k is correlated (accumulating):
+    # ragged last chunks, several channels (the chunk view's channel stride), one-shot mode.
+    N, T, C = 272, 1000, 3
+    p = synth.uniform(N, T, C, seed=chunk + 1)
+    xe.set_option("host_chunk_t", chunk)
+    try:
+        got = xe.correlate_host(torch.from_numpy(p).pin_memory(), N, T, C)
+    finally:
+        xe.set_option("host_chunk_t", 8192)
+    assert_exact(got.numpy(), oracle.correlate(p, N, T, C), f"host chunk {chunk}")
+
+
+def test_host_async_slots_overlap_and_stay_exact(xe):
+    N, T, C = 512, 4000, 2
+    ins = [synth.uniform(N, T, C, seed=40 + k) for k in range(3)]
+    pinned = [torch.from_numpy(p).pin_memory() for p in ins]
+    outs = [xe.correlate_host_async(pinned[k], N, T, C, slot=k)[0] for k in range(3)]
+    with pytest.raises(xe.XeError) as ei:          # slot 1 is still in flight
+        xe.correlate_host_async(pinned[0], N, T, C, slot=1)
+    assert ei.value.code == xe.XE_EAGAIN
+    for k in (2, 0, 1):
+        xe.host_wait(k)
+    for k in range(3):
+        assert_exact(outs[k].numpy(), oracle.correlate(ins[k], N, T, C), f"slot {k}")
+    out, _ = xe.correlate_host_async(pinned[2], N, T, C, slot=1)   # reuse after the wait
+    xe.host_wait(1)
+    assert_exact(out.numpy(), oracle.correlate(ins[2], N, T, C), "slot reuse")
+
+
 def test_bounded_wait_times_out_and_context_survives(xe):
     # Test hook: the producer warp issues no copies, so the MMA warp's bounded wait on the
     # pipeline barrier runs out (about a second); the kernel sets the status word, every
