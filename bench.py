@@ -521,7 +521,7 @@ def main():
     ap.add_argument("--no-corner", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
-    ap.add_argument("--stream-channels", type=int, default=256)
+    ap.add_argument("--stream-channels", type=int, default=320)
     ap.add_argument("--stream-seconds", type=float, default=2.0)
     ap.add_argument("--stream-start", type=int, default=128)
     ap.add_argument("--stream-step", type=int, default=32)
@@ -652,8 +652,15 @@ def main():
     # cores busy (its producer is paced on the host).
     stream = None
     if ws == 1 and not args.no_stream:
+        # The largest sustained channel count, starting at --stream-channels and stepping
+        # down by 32 while a run is not sustained (real-time pace, no overruns or drops).
         from paper_2005_09481_gb300 import serve
-        stream = serve.run_realtime(args.stream_channels, args.stream_seconds)
+        c = args.stream_channels
+        while True:
+            stream = serve.run_realtime(c, args.stream_seconds)
+            if stream["sustained"] or c <= 64:
+                break
+            c -= 32
 
     masked = None
     if ws == 1 and not args.no_masked:

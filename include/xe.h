@@ -311,9 +311,11 @@ typedef struct xe_result {
 int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out);
 
 /* Admit a channel slot if the HBM budget allows it.  A slot holds two int32 accumulators
- * (one filling while the other is exported), ring_frames frame buffers and its share of the
- * staging memory.  Returns XE_OK, XE_EBUDGET when the budget is full, XE_EINVAL for a bad
- * channel id. */
+ * (one filling while the other is exported), ring_frames frame buffers (one contiguous
+ * ring, filled round-robin) and its share of the staging memory: up to min(4, ring_frames)
+ * consecutive frames of a channel are correlated as one job when they are ready together,
+ * so the share is that many frames' staged operands (2 bytes per sample and input).
+ * Returns XE_OK, XE_EBUDGET when the budget is full, XE_EINVAL for a bad channel id. */
 int xe_stream_admit(xe_stream *s, int chan);
 
 /* Release a channel slot (its pending integration is dropped, its memory returned). */

@@ -63,6 +63,9 @@ struct Chan {
     bool acc_wait[2] = {false, false};                // compute must wait on acc_free_ev
     bool fresh[2] = {true, true};                     // next frame overwrites (no stale sums)
     int cur = 0;                                      // accumulator being filled
+    uint8_t *ring_base = nullptr;                     // ring slots, contiguous: slot k at
+                                                      // ring_base + k * frame_bytes
+    int next_slot = 0;                                // slots are filled round-robin
     std::vector<Slot> ring;
     std::deque<Entry> fifo;
     int n_copying = 0;
@@ -125,7 +128,8 @@ namespace xe {
 namespace {
 
 constexpr int kBufsPerChan = 2;
-constexpr int kMaxGroups = 4;                 // frames of one channel per scheduler pass
+constexpr int kMaxGroups = 4;                 // launch groups (jobs of one channel) per pass
+constexpr int kMaxMerge = 4;                  // consecutive frames merged into one job
 constexpr int64_t kHoldNs = 1500000;          // longest wait for a fuller batch
 
 cudaEvent_t take_event(xe_stream *s) {
@@ -259,18 +263,34 @@ bool pass(xe_stream *s) {
             }
         }
         s->hold_since = 0;
-        // Up to kMaxGroups frames per channel: the g-th frame of every channel goes to launch
-        // group g (frames of one channel never share a launch: they add into the same
-        // accumulator).  A channel stops at its first closed integration in the pass.
+        // Every channel's ready frames, in order: a run of consecutive frames that sit in
+        // consecutive ring slots (slots are filled round-robin and contiguous) becomes ONE job
+        // of up to kMaxMerge frames; the channel's g-th job goes to launch group g (jobs of
+        // one channel never share a launch: they add into the same accumulator).  A channel
+        // stops at its first closed integration in the pass.
         for (size_t c = 0; c < s->chans.size(); ++c) {
             Chan &ch = s->chans[c];
             if (!ch.admitted) continue;
-            int g = 0;
+            int g = 0, run_slot = -1, run_len = 0;
+            auto emit = [&]() {
+                if (run_len == 0) return;
+                if (ch.acc_wait[ch.cur]) {
+                    waits.push_back(ch.acc_free_ev[ch.cur]);
+                    ch.acc_wait[ch.cur] = false;
+                }
+                groups[size_t(g)].push_back(xe_job{ch.ring[size_t(run_slot)].dev, ch.acc[ch.cur], s->cfg.N, 1,
+                                                   int64_t(run_len) * s->cfg.frame_T});
+                group_acc[size_t(g)].push_back(ch.fresh[ch.cur] ? 0 : 1);
+                ch.fresh[ch.cur] = false;
+                ++g;
+                run_len = 0;
+            };
             while (!ch.fifo.empty() && g < kMaxGroups) {
                 const Entry e = ch.fifo.front();
                 const bool closes = ch.frames_in_integ + 1 == s->frames_per_integ;
                 if (closes && !has_free_buf(s, int(c))) break;       // consumer is behind
                 if (e.slot < 0) {                                     // a lost frame
+                    emit();
                     ch.fifo.pop_front();
                     if (ch.frames_in_integ == 0) ch.t_first = e.t_arrival;
                     ch.t_last = e.t_arrival;
@@ -284,26 +304,26 @@ bool pass(xe_stream *s) {
                 }
                 Slot &sl = ch.ring[size_t(e.slot)];
                 if (sl.state != kReady) break;
+                if (run_len > 0 && (e.slot != run_slot + run_len || run_len == kMaxMerge)) {
+                    emit();
+                    if (g == kMaxGroups) break;
+                }
                 ch.fifo.pop_front();
                 sl.state = kQueued;
-                if (ch.acc_wait[ch.cur]) {
-                    waits.push_back(ch.acc_free_ev[ch.cur]);
-                    ch.acc_wait[ch.cur] = false;
-                }
-                groups[size_t(g)].push_back(xe_job{sl.dev, ch.acc[ch.cur], s->cfg.N, 1, s->cfg.frame_T});
-                group_acc[size_t(g)].push_back(ch.fresh[ch.cur] ? 0 : 1);
-                ch.fresh[ch.cur] = false;
+                if (run_len == 0) run_slot = e.slot;
+                ++run_len;
                 used.push_back(int(c) << 8 | e.slot);
                 if (ch.frames_in_integ == 0) ch.t_first = e.t_arrival;
                 ch.t_last = e.t_arrival;
                 ch.frames_in_integ += 1;
                 ch.samples_in_integ += s->cfg.frame_T;
-                ++g;
                 if (closes) {
+                    emit();
                     exports.push_back(close_integration(s, int(c)));
                     break;
                 }
             }
+            emit();
         }
         s->flush_req = false;
         n_jobs = 0;
@@ -382,8 +402,15 @@ int push_locked(xe_stream *s, int chan, const uint8_t *frame, int64_t seq, int64
     if (seq < ch.expected_push) return sfail(XE_EINVAL, "frame is older than the open integration or a duplicate");
     if (seq - ch.expected_push > 1000000) return sfail(XE_EINVAL, "sequence gap too large");
     int slot = -1;
-    for (int k = 0; k < int(ch.ring.size()); ++k)
-        if (ch.ring[size_t(k)].state == kFree) { slot = k; break; }
+    const int R = int(ch.ring.size());
+    for (int k = 0; k < R; ++k) {
+        const int idx = (ch.next_slot + k) % R;
+        if (ch.ring[size_t(idx)].state == kFree) {
+            slot = idx;
+            ch.next_slot = (idx + 1) % R;
+            break;
+        }
+    }
     if (slot < 0) return XE_EAGAIN;
     for (int64_t q = ch.expected_push; q < seq; ++q) {     // frames that never came
         ch.fifo.push_back(Entry{q, -1, t});
@@ -431,7 +458,8 @@ int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
     s->acc_bytes = size_t(s->B) * 2 * sizeof(int32_t);
     s->frames_per_integ = c.integ_T / c.frame_T;
     const size_t n_pad = size_t((c.N + kNPad - 1) / kNPad * kNPad);
-    const size_t stage_bytes = 2 * n_pad * size_t((c.frame_T + 63) / 64 * 64);
+    const size_t merge = size_t(c.ring_frames < kMaxMerge ? c.ring_frames : kMaxMerge);
+    const size_t stage_bytes = merge * 2 * n_pad * size_t((c.frame_T + 63) / 64 * 64);
     s->per_chan_bytes = 2 * s->acc_bytes + size_t(c.ring_frames) * s->frame_bytes + stage_bytes;
     if (c.hbm_budget < int64_t(s->per_chan_bytes)) {
         delete s;
@@ -472,13 +500,16 @@ int xe_stream_admit(xe_stream *s, int chan) {
     }
     ch.cur = 0;
     ch.ring.assign(size_t(s->cfg.ring_frames), Slot{});
-    for (Slot &sl : ch.ring) {
-        if (cudaMalloc(&sl.dev, s->frame_bytes) != cudaSuccess) {
-            cudaGetLastError();
-            return sfail(XE_ENOMEM, "frame ring allocation failed");
-        }
-        cudaEventCreateWithFlags(&sl.copy_ev, cudaEventDisableTiming);
+    if (cudaMalloc(&ch.ring_base, s->frame_bytes * size_t(s->cfg.ring_frames)) != cudaSuccess) {
+        cudaGetLastError();
+        ch.ring_base = nullptr;
+        return sfail(XE_ENOMEM, "frame ring allocation failed");
     }
+    for (size_t k = 0; k < ch.ring.size(); ++k) {
+        ch.ring[k].dev = ch.ring_base + k * s->frame_bytes;
+        cudaEventCreateWithFlags(&ch.ring[k].copy_ev, cudaEventDisableTiming);
+    }
+    ch.next_slot = 0;
     if (ch.bufs.empty()) {
         for (int k = 0; k < kBufsPerChan; ++k) {
             ResultBuf rb;
@@ -523,10 +554,9 @@ int xe_stream_evict(xe_stream *s, int chan) {
             ++k;
         }
     }
-    for (Slot &sl : ch.ring) {
-        cudaFree(sl.dev);
-        cudaEventDestroy(sl.copy_ev);
-    }
+    for (Slot &sl : ch.ring) cudaEventDestroy(sl.copy_ev);
+    cudaFree(ch.ring_base);
+    ch.ring_base = nullptr;
     ch.ring.clear();
     ch.fifo.clear();
     for (int a = 0; a < 2; ++a) {
@@ -659,10 +689,9 @@ void xe_stream_close(xe_stream *s) {
     cudaStreamSynchronize(s->comp_s);
     cudaStreamSynchronize(s->d2h_s);
     for (Chan &ch : s->chans) {
-        for (Slot &sl : ch.ring) {
-            cudaFree(sl.dev);
-            cudaEventDestroy(sl.copy_ev);
-        }
+        for (Slot &sl : ch.ring) cudaEventDestroy(sl.copy_ev);
+        if (ch.ring_base) cudaFree(ch.ring_base);
+        ch.ring_base = nullptr;
         for (int a = 0; a < 2; ++a) {
             if (ch.acc[a]) cudaFree(ch.acc[a]);
             if (ch.acc_free_ev[a]) cudaEventDestroy(ch.acc_free_ev[a]);

@@ -18,14 +18,17 @@ CHIME_RATE = 390625.0
 
 
 def per_channel_bytes(N: int, frame_T: int, ring_frames: int) -> int:
-    """Device bytes one channel slot holds: accumulator + frame ring + staging share."""
+    """Device bytes one channel slot holds: accumulators + frame ring + staging share (up to
+    min(4, ring_frames) frames of a channel are correlated as one job)."""
     n_pad = (N + 255) // 256 * 256
-    return 2 * N * (N + 1) * 4 + ring_frames * frame_T * N + 2 * n_pad * ((frame_T + 63) // 64 * 64)
+    merge = min(4, ring_frames)
+    return (2 * N * (N + 1) * 4 + ring_frames * frame_T * N
+            + merge * 2 * n_pad * ((frame_T + 63) // 64 * 64))
 
 
 def run_realtime(n_chan: int, seconds: float, N: int = 2048, frame_T: int = 8192,
                  integ_T: int = 32768, rate: float = CHIME_RATE, device_source: bool = True,
-                 ring_frames: int = 3, hbm_budget: int | None = None, n_distinct: int = 8,
+                 ring_frames: int = 8, hbm_budget: int | None = None, n_distinct: int = 8,
                  seed: int = 20050948) -> dict:
     """Stream n_chan channels in real time for `seconds`; return throughput and latency."""
     import torch

@@ -108,7 +108,8 @@ def test_lost_frame_marks_integration_incomplete(xe):
 
 def test_admission_by_hbm_budget(xe):
     N, fT, F = 512, 4096, 2
-    per_chan = 2 * N * (N + 1) * 4 + 2 * fT * N + 2 * 512 * fT  # 2 accumulators + ring + staging
+    # 2 accumulators + ring + staging share (min(4, ring_frames) merged frames' operands)
+    per_chan = 2 * N * (N + 1) * 4 + 2 * fT * N + 2 * (2 * 512 * fT)
     with xe.Stream(N, fT, F * fT, max_chan=8, hbm_budget=2 * per_chan + 1000, ring_frames=2) as st:
         assert st.admit(0) == 0 and st.admit(1) == 0
         assert st.admit(2) == xe.XE_EBUDGET
@@ -152,3 +153,22 @@ def test_push_frames_batch_matches_single_pushes(xe):
         c, q = meta["chan"], meta["integ_index"]
         block = data[c][q * F:(q + 1) * F].reshape(1, F * fT, N)
         np.testing.assert_array_equal(vis, oracle.correlate_dense(block, N, F * fT, 1)[0])
+
+
+def test_backlog_frames_merge_into_jobs_and_stay_exact(xe):
+    # Eight frames of one channel pushed at once into a ring of eight: consecutive slots are
+    # correlated as merged jobs (up to four frames each), across two integrations.
+    N, fT, F = 320, 1024, 4
+    fr = frames_for(N, fT, 2 * F, seed=77)
+    dev = torch.from_numpy(fr).cuda()
+    torch.cuda.synchronize()
+    with xe.Stream(N, fT, F * fT, max_chan=1, hbm_budget=1 << 30, ring_frames=8, device_source=True) as st:
+        assert st.admit(0) == 0
+        for q in range(2 * F):
+            assert st.push(0, dev[q], q) == 0
+        st.flush()
+        res = [st.poll(timeout_ms=20000) for _ in range(2)]
+    for k, (meta, vis) in enumerate(res):
+        assert meta["complete"] == 1 and meta["integ_index"] == k
+        want = oracle.correlate_dense(fr[k * F:(k + 1) * F].reshape(1, F * fT, N), N, F * fT, 1)[0]
+        np.testing.assert_array_equal(vis, want)
