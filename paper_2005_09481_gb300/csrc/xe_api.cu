@@ -493,6 +493,31 @@ static std::vector<int64_t> shape_key(const std::vector<JobShape> &jobs, int eb)
     return key;
 }
 
+constexpr size_t kMaxCachedPlans = 1024;
+
+// Bounded plan cache: a stream of ever-new batch shapes (e.g. merged stream frames) would
+// otherwise keep one device blob per shape forever.  Called before a batch builds its launch
+// records (none of which may hold a plan yet); plans of launches already queued may still be
+// read, so the cache (and the graphs that point into it) is dropped only once the device is
+// idle.
+static int trim_plan_cache(Device *d) {
+    if (d->plans.size() < kMaxCachedPlans) return XE_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return fail(XE_ECUDA, "sync before dropping plans: %s", cudaGetErrorString(e));
+    for (auto &kv : d->plans) {
+        cudaFree(kv.second->blob);
+        delete kv.second;
+    }
+    d->plans.clear();
+    for (auto &kv : d->graphs) {
+        cudaGraphExecDestroy(kv.second->exec);
+        cudaGraphDestroy(kv.second->graph);
+        delete kv.second;
+    }
+    d->graphs.clear();
+    return XE_OK;
+}
+
 static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const TuneCfg &cfg,
                     DevPlan **out) {
     std::vector<int64_t> key = shape_key(jobs, eb);
@@ -517,7 +542,10 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
     if (cudaMalloc(&p->blob, total) != cudaSuccess) {
         cudaGetLastError();
         delete p;
-        return fail(XE_ENOMEM, "cannot allocate %zu bytes for a plan", total);
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        return fail(XE_ENOMEM, "cannot allocate %zu bytes for a plan (%zu of %zu bytes free, %zu plans cached)",
+                    total, fr, tot, d->plans.size());
     }
     std::vector<uint8_t> host(total, 0);
     memcpy(host.data(), h.tiles.data(), b_t);
@@ -553,7 +581,9 @@ static int grow(void **ptr, size_t *have, size_t need, bool zero) {
     if (cudaMalloc(ptr, sz) != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
-        return fail(XE_ENOMEM, "cannot allocate %zu bytes of scratch", sz);
+        size_t fr = 0, tot = 0;
+        cudaMemGetInfo(&fr, &tot);
+        return fail(XE_ENOMEM, "cannot allocate %zu bytes of scratch (%zu of %zu bytes free)", sz, fr, tot);
     }
     if (zero) XE_CUDA(cudaMemset(*ptr, 0, sz));
     *have = sz;
@@ -666,6 +696,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
     int64_t max_T = 0;
     for (int q = 0; q < n_jobs; ++q) max_T = std::max(max_T, jobs[q].T);
     const int64_t n_win = (max_T + wt - 1) / wt;
+    size_t max_planes = 0, max_ws = 0, max_counters = 0;
+    const size_t first_rec = out.size();
     for (int64_t w = 0; w < n_win; ++w) {
         std::vector<int> act;
         for (int q = 0; q < n_jobs; ++q)
@@ -732,11 +764,13 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 plane_off += size_t(cj.plane_chan_bytes) * size_t(cj.C);
             }
             jt.total_stage_blocks = blocks;
-            int rc = grow(reinterpret_cast<void **>(&sc->planes), &sc->planes_bytes, plane_off, false);
-            if (rc) return rc;
+            // Plane offsets within the scratch; the base is bound once every group is known
+            // (the scratch is sized for the largest group: growing it per group would free
+            // the buffer earlier groups' records already point into).
+            max_planes = std::max(max_planes, plane_off);
             size_t off = 0;
             for (int k = 0; k < jt.n_jobs; ++k) {
-                jt.jobs[k].planes = sc->planes + off;
+                jt.jobs[k].planes = reinterpret_cast<const uint8_t *>(off);
                 off += size_t(jt.jobs[k].plane_chan_bytes) * size_t(jt.jobs[k].C);
             }
             for (int k = 0; k < ng; ++k)
@@ -758,15 +792,12 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             }
             g_last_cfg = cfg;
             DevPlan *p = nullptr;
-            rc = get_plan(d, shapes, eb, cfg, &p);
+            const int rc = get_plan(d, shapes, eb, cfg, &p);
             if (rc) return rc;
             const size_t ws_need =
                 size_t(std::max(1, p->host.n_partial)) * size_t(kWsSlotElems) * sizeof(int32_t);
-            rc = grow(reinterpret_cast<void **>(&sc->ws), &sc->ws_bytes, ws_need, false);
-            if (rc) return rc;
-            rc = grow(reinterpret_cast<void **>(&sc->counters), &sc->counters_bytes,
-                      p->host.tiles.size() * sizeof(int), true);
-            if (rc) return rc;
+            max_ws = std::max(max_ws, ws_need);
+            max_counters = std::max(max_counters, p->host.tiles.size() * sizeof(int));
             LaunchRec tc = st;
             tc.kind = 1;
             tc.clustered = p->host.clustered;
@@ -777,14 +808,36 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             pd.tile_slots = p->d_tile_slots;
             pd.n_tiles = int(p->host.tiles.size());
             pd.n_cta = p->host.n_cta;
-            pd.ws = sc->ws;
-            pd.counters = sc->counters;
+            pd.ws = nullptr;          // bound below
+            pd.counters = nullptr;
             pd.status = sc->status;
             pd.inject_stall = g_opt.inject_stall;
             // All CTAs of the launch must be resident together for the exchange's wait.
             pd.pair_exchange = p->host.pair_exchange && p->host.n_cta <= d->n_sm ? 1 : 0;
             out.push_back(st);
             out.push_back(tc);
+        }
+    }
+    // Size the scratch for the largest group, then bind it into every record.
+    {
+        int rc = grow(reinterpret_cast<void **>(&sc->planes), &sc->planes_bytes, std::max<size_t>(max_planes, 1), false);
+        if (rc) return rc;
+        rc = grow(reinterpret_cast<void **>(&sc->ws), &sc->ws_bytes, std::max<size_t>(max_ws, 1), false);
+        if (rc) return rc;
+        rc = grow(reinterpret_cast<void **>(&sc->counters), &sc->counters_bytes, std::max<size_t>(max_counters, 4), true);
+        if (rc) return rc;
+        for (size_t r = first_rec; r < out.size(); ++r) {
+            LaunchRec &rec = out[r];
+            if (rec.kind != 0 && rec.kind != 1) continue;
+            for (int k = 0; k < rec.jt.n_jobs; ++k) {
+                JobDev &jd = rec.jt.jobs[k];
+                jd.planes = sc->planes + reinterpret_cast<uintptr_t>(jd.planes);
+                if (jd.count_planes) jd.count_planes = sc->planes + reinterpret_cast<uintptr_t>(jd.count_planes);
+            }
+            if (rec.kind == 1) {
+                rec.pd.ws = sc->ws;
+                rec.pd.counters = sc->counters;
+            }
         }
     }
     if (g_job_mask) {
@@ -897,6 +950,8 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
     if (rc) return rc;
     Scratch *sc = nullptr;
     rc = get_scratch(d, s, &sc);
+    if (rc) return rc;
+    rc = trim_plan_cache(d);
     if (rc) return rc;
     // Candidates overwrite the jobs' outputs, so calls that add into any output never tune.
     if (algo == XE_ALGO_TC && g_opt.autotune && !accumulate && !g_job_acc) {

@@ -22,6 +22,7 @@
 #include <cstring>
 #include <deque>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -119,6 +120,8 @@ struct xe_stream {
     int64_t used_bytes = 0;
     int64_t n_admitted = 0, n_frames = 0, n_integ = 0, n_dropped = 0;
     int last_error = XE_OK;
+    std::string last_msg;            // detail of last_error (from the scheduler thread)
+
     int64_t hold_since = 0;          // first pass that held back a partial batch
     bool flush_req = false;
     int64_t n_launch_groups = 0, n_launch_passes = 0, n_held = 0, launch_ns = 0;
@@ -346,7 +349,10 @@ bool pass(xe_stream *s) {
     std::vector<Pending> pend;
     {
         std::lock_guard<std::mutex> lk(s->mu);
-        if (rc != XE_OK) s->last_error = rc;
+        if (rc != XE_OK) {
+            s->last_error = rc;
+            s->last_msg = xe_last_error();
+        }
         const int pe = take_pass_event(s);
         done = s->pass_events[size_t(pe)].ev;
         cudaEventRecord(done, s->comp_s);
@@ -637,7 +643,8 @@ int xe_stream_poll(xe_stream *s, xe_result *r, int timeout_ms) {
     if (s->last_error != XE_OK) {
         const int e = s->last_error;
         s->last_error = XE_OK;
-        return sfail(e, "a batched launch of the stream failed");
+        const std::string msg = "a batched launch of the stream failed: " + s->last_msg;
+        return sfail(e, msg.c_str());
     }
     if (s->ready.empty()) return XE_EAGAIN;
     *r = s->ready.front();

@@ -169,3 +169,20 @@ def test_clustered_kernel_matches_oracle(xe, N, T, C):
     xe.device_status()
     assert xe.last_config()[2] == 4
     np.testing.assert_array_equal(out.cpu().numpy(), oracle.correlate_dense(p, N, T, C))
+
+
+def test_later_launch_group_needing_more_scratch(xe):
+    # More jobs than one launch holds: 208 small jobs, then 2 large ones.  The second launch
+    # group needs more staging and workspace than the first; the scratch is sized for the
+    # largest group before any launch record is bound to it.
+    shapes = [(64, 64)] * 208 + [(1024, 4096), (2048, 2048)]
+    ins = [synth.uniform(n, t, 1, seed=500 + q) for q, (n, t) in enumerate(shapes)]
+    devs = [torch.from_numpy(p).cuda() for p in ins]
+    outs = [xe.empty_vis(n, 1) for (n, t) in shapes]
+    xe.correlate_batch([(d, o, n, t, 1) for d, o, (n, t) in zip(devs, outs, shapes)])
+    torch.cuda.synchronize()
+    xe.device_status()
+    for q in (0, 207, 208, 209):
+        n, t = shapes[q]
+        want = oracle.correlate_dense(ins[q], n, t, 1) if n > 256 else oracle.correlate(ins[q], n, t, 1)
+        np.testing.assert_array_equal(outs[q].cpu().numpy(), want)
