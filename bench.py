@@ -484,7 +484,8 @@ def run_stream_workload(args):
     runs, best = [], None
     c = args.stream_start
     while c <= args.stream_max:
-        r = serve.run_realtime(c, args.stream_seconds, device_source=not args.host_source)
+        r = serve.run_realtime(c, args.stream_seconds, device_source=not args.host_source,
+                               integ_T=args.stream_integ_frames * 8192)
         runs.append({k: r[k] for k in ("channels", "sustained", "cmac_per_s", "p50_latency_ms",
                                        "p99_latency_ms", "push_overruns", "frames_dropped")})
         print(json.dumps(runs[-1]), file=sys.stderr, flush=True)
@@ -498,7 +499,9 @@ def run_stream_workload(args):
             "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "e4m3", "data": "synthetic",
             "config": {"workload": "streaming serve: N=2048, 8192-sample frames at 390625 samples/s/channel, "
-                                   "32768-sample integrations, device-resident accumulators, HBM-budget admission",
+                                   f"{args.stream_integ_frames * 8192}-sample integrations "
+                                   f"({args.stream_integ_frames * 8192 / 390625.0:.3f} s), device-resident "
+                                   "accumulators, HBM-budget admission",
                        "source": "host" if args.host_source else "device"},
             "realtime_channels": best["channels"] if best else 0,
             "p50_frame_latency_ms": best["p50_latency_ms"] if best else None,
@@ -527,6 +530,8 @@ def main():
     ap.add_argument("--stream-step", type=int, default=32)
     ap.add_argument("--stream-max", type=int, default=1024)
     ap.add_argument("--host-source", action="store_true")
+    ap.add_argument("--stream-integ-frames", type=int, default=4,
+                    help="frames per integration (4 = 83.9 ms; 477 = the paper's 10 s cadence)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

@@ -172,3 +172,52 @@ def test_backlog_frames_merge_into_jobs_and_stay_exact(xe):
         assert meta["complete"] == 1 and meta["integ_index"] == k
         want = oracle.correlate_dense(fr[k * F:(k + 1) * F].reshape(1, F * fT, N), N, F * fT, 1)[0]
         np.testing.assert_array_equal(vis, want)
+
+
+def test_ten_second_cadence_integration(xe):
+    # The paper's export cadence: 10 s integrations (Table tab:data-flow), here 477 frames of
+    # 8192 samples = 3,907,584 samples at 390625 samples/s.  Frames cycle through a few
+    # distinct ones; by linearity in time the exact result is sum_d n_d V(frame_d).
+    N, fT, F, D = 64, 8192, 477, 5
+    fr = frames_for(N, fT, D, seed=99)
+    dev = torch.from_numpy(fr).cuda()
+    torch.cuda.synchronize()
+    with xe.Stream(N, fT, F * fT, max_chan=1, hbm_budget=1 << 30, ring_frames=8, device_source=True) as st:
+        assert st.admit(0) == 0
+        q = 0
+        t0 = time.time()
+        while q < F and time.time() - t0 < 60:
+            rc = st.push(0, dev[q % D], q)
+            if rc == 0:
+                q += 1
+            else:
+                assert rc == xe.XE_EAGAIN
+                time.sleep(0.0005)
+        assert q == F
+        st.flush()
+        meta, vis = st.poll(timeout_ms=30000)
+    assert meta["complete"] == 1 and meta["n_samples"] == F * fT
+    want = np.zeros((N * (N + 1) // 2, 2), np.int64)
+    for d in range(D):
+        n_d = len(range(d, F, D))
+        want += n_d * oracle.correlate64(fr[d], N, fT, 1)[0]
+    np.testing.assert_array_equal(vis, want)
+
+
+def test_ten_second_cadence_extreme_values_fit_int32(xe):
+    # All samples -8-8i for 10 s: Re V_ii = 128 * 3,907,584 = 500,170,752 < 2^31.
+    N, fT, F = 32, 8192, 477
+    frame = torch.from_numpy(synth.constant(N, fT, -8, -8)[0]).cuda()
+    with xe.Stream(N, fT, F * fT, max_chan=1, hbm_budget=1 << 30, ring_frames=8, device_source=True) as st:
+        assert st.admit(0) == 0
+        q = 0
+        while q < F:
+            if st.push(0, frame, q) == 0:
+                q += 1
+            else:
+                time.sleep(0.0005)
+        st.flush()
+        meta, vis = st.poll(timeout_ms=30000)
+    diag = [i * N - i * (i - 1) // 2 for i in range(N)]
+    assert np.all(vis[diag, 0] == 128 * F * fT) and np.all(vis[:, 1] == 0)
+    assert np.all(vis[:, 0] == 128 * F * fT)
