@@ -285,9 +285,8 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
                 uint32_t o[4];
 #pragma unroll
                 for (int u = 0; u < 2; ++u) {
-                    const uint32_t x = rw[2 * q + u];
-                    const uint32_t re = e4m3_of_nibbles((x >> 4) & 0x0F0F0F0Fu);
-                    const uint32_t im = e4m3_of_nibbles(x & 0x0F0F0F0Fu);
+                    uint32_t re, im;
+                    e4m3_of_bytes(rw[2 * q + u], re, im);
                     o[2 * u] = __byte_perm(re, im, 0x5140);
                     o[2 * u + 1] = __byte_perm(re, im, 0x7362);
                 }

@@ -41,4 +41,28 @@ __device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t x) {
     return (pos & ~m) | (neg & m);
 }
 
+// Byte k of the result = 0xFF if bit 7 of byte k of a is set, else 0 (the byte permute's
+// sign-replicate selectors 8..11; the __byte_perm intrinsic uses 3-bit selectors only).
+__device__ __forceinline__ uint32_t byte_sign_mask(uint32_t a) {
+    uint32_t d;
+    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(d) : "r"(a));
+    return d;
+}
+
+// Four packed samples (byte k: high nibble re, low nibble im, two's complement) -> the e4m3
+// codes of their real parts (re) and imaginary parts (im), byte k each.  The same table
+// lookup as e4m3_of_nibbles, with the sign masks taken directly from the nibbles' top bits:
+// the re sign is bit 7 of each byte, the im sign bit 3 (bit 7 after a 4-bit shift).
+__device__ __forceinline__ void e4m3_of_bytes(uint32_t v, uint32_t &re, uint32_t &im) {
+    constexpr uint32_t P0 = pack_codes(0), P1 = pack_codes(4), N0 = pack_codes(8), N1 = pack_codes(12);
+    const uint32_t yi = v & 0x07070707u;
+    const uint32_t si = __byte_perm(yi | (yi >> 4), 0, 0x0020);
+    const uint32_t mi = byte_sign_mask(v << 4);
+    im = (__byte_perm(P0, P1, si) & ~mi) | (__byte_perm(N0, N1, si) & mi);
+    const uint32_t yr = (v >> 4) & 0x07070707u;
+    const uint32_t sr = __byte_perm(yr | (yr >> 4), 0, 0x0020);
+    const uint32_t mr = byte_sign_mask(v);
+    re = (__byte_perm(P0, P1, sr) & ~mr) | (__byte_perm(N0, N1, sr) & mr);
+}
+
 }  // namespace xe

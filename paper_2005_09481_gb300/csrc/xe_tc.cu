@@ -135,10 +135,7 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ JobT
             const uint32_t v[4] = {__byte_perm(a, b, 0x5410), __byte_perm(a, b, 0x7632),
                                    __byte_perm(cc, d, 0x5410), __byte_perm(cc, d, 0x7632)};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                re[i][kk] = e4m3_of_nibbles((v[i] >> 4) & 0x0F0F0F0Fu);
-                im[i][kk] = e4m3_of_nibbles(v[i] & 0x0F0F0F0Fu);
-            }
+            for (int i = 0; i < 4; ++i) e4m3_of_bytes(v[i], re[i][kk], im[i][kk]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -347,10 +344,7 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
             const uint32_t v[4] = {__byte_perm(a, bb, 0x5410), __byte_perm(a, bb, 0x7632),
                                    __byte_perm(cc, d, 0x5410), __byte_perm(cc, d, 0x7632)};
 #pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                re[i][kk] = e4m3_of_nibbles((v[i] >> 4) & 0x0F0F0F0Fu);
-                im[i][kk] = e4m3_of_nibbles(v[i] & 0x0F0F0F0Fu);
-            }
+            for (int i = 0; i < 4; ++i) e4m3_of_bytes(v[i], re[i][kk], im[i][kk]);
         }
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
