@@ -15,10 +15,10 @@
 //
 // beam_weight_kernel  int8 w[B][N][2] -> e4m3 B-operand tiles [chunk][2][ncols][64 B] in the
 //                     64-byte-swizzled image the MMA reads (one bulk copy per stage).
-// beam_kernel         one CTA per (channel, 128 samples).  Eight converter warps stream the
-//                     packed [128 samples][64 inputs] tile of each stage into a 5-deep
-//                     shared-memory ring with coalesced cp.async (4 lanes per 64-byte row
-//                     piece) and convert it to a double-buffered e4m3 A tile; a ninth warp
+// beam_kernel         one CTA per (channel, 128 samples).  Eight converter warps, each owning
+//                     16 sample rows end to end, stream the packed bytes of each stage into a
+//                     3-deep shared-memory ring with coalesced cp.async (4 lanes per 64-byte
+//                     row piece) and convert them to a triple-buffered e4m3 A tile; a ninth warp
 //                     streams the weight tiles through a ring of bulk copies and issues the
 //                     MMAs; the roles meet on mbarriers.  The converter warps then read tensor
 //                     memory and write y[c][t][b][re, im].
@@ -34,9 +34,10 @@ namespace xe {
 constexpr int kBeamSub = 2;                         // sub-tiles of 32 inputs (64 B of e4m3) per stage
 constexpr int kBeamASub = kBeamRows * 64;           // 8 KB
 constexpr int kBeamABuf = kBeamSub * kBeamASub;     // 16 KB
-constexpr int kBeamRawStride = 80;                  // bytes per row of a raw ring slot (64 + pad)
-constexpr int kBeamRawSlot = kBeamRows * kBeamRawStride;
-constexpr int kBeamRawDepth = 5;                    // raw slots: stages in flight = depth - 1
+constexpr int kBeamABufs = 3;                       // A tiles: conversion waits for stage i - 3
+constexpr int kBeamRawSlot = kBeamRows * 64;        // raw ring slot: 64-byte rows, 16-byte pieces
+                                                    // XOR-swizzled by (row >> 1) & 3
+constexpr int kBeamRawDepth = 3;                    // raw slots: stages in flight = depth - 1
 constexpr int kBeamConvThreads = 256;               // 8 converter warps, two threads per row
 constexpr int kBeamThreads = kBeamConvThreads + 32; // + 1 MMA / weight-copy warp
 
@@ -47,12 +48,18 @@ size_t beam_wt_bytes(int B, int N) {
     return chunks * kBeamSub * size_t(beam_ncols(B)) * 64;
 }
 
-// Weight-ring depth for an MMA width: deeper rings prefetch further ahead (distance
-// depth - 2) but cost shared memory.
-__host__ __device__ constexpr int beam_w_depth(int ncols) { return ncols <= 64 ? 4 : ncols <= 128 ? 3 : 2; }
+// Weight ring for an MMA width: `depth` slots, copies issued `ahead` stages early.  The copy
+// of stage j reuses the slot of stage j - depth, so issuing it (at stage j - ahead) waits for
+// the MMAs of stage j - depth, depth - ahead = 3 stages back.  Up to 64 columns two CTAs fit
+// on an SM (<= 114 KB each, the 1 KB per-CTA reservation included); wider MMAs run one CTA
+// per SM and take the deeper ring.
+__host__ __device__ constexpr int beam_w_depth(int ncols) {
+    return ncols <= 48 ? 5 : ncols <= 64 ? 4 : ncols <= 128 ? 5 : 4;
+}
+__host__ __device__ constexpr int beam_w_ahead(int ncols) { return beam_w_depth(ncols) - 3; }
 
 static int beam_smem_bytes(int ncols) {
-    return 1024 /*align*/ + 2 * kBeamABuf + kBeamRawDepth * kBeamRawSlot +
+    return 1024 /*align*/ + kBeamABufs * kBeamABuf + kBeamRawDepth * kBeamRawSlot +
            beam_w_depth(ncols) * kBeamSub * ncols * 64 + 128 /*barriers, tensor-memory slot*/;
 }
 
@@ -117,18 +124,6 @@ __device__ __forceinline__ void beam_cp_async16(void *dst, const void *src, uint
                  : "memory");
 }
 
-// Barrier over the converter warps only (named barrier 1), OR-reducing a flag.
-__device__ __forceinline__ bool conv_bar_or(bool flag) {
-    uint32_t r;
-    asm volatile(
-        "{\n\t.reg .pred p, q;\n\tsetp.ne.u32 p, %1, 0;\n\t"
-        "barrier.cta.red.or.pred q, 1, %2, p;\n\tselp.u32 %0, 1, 0, q;\n\t}"
-        : "=r"(r)
-        : "r"(flag ? 1u : 0u), "n"(kBeamConvThreads)
-        : "memory");
-    return r != 0;
-}
-
 // Roles (see the file header).  Barriers:
 //   a_full[buf]   8 converter warps arrive when A tile `buf` holds its stage
 //   w_full[slot]  the weight tile of a stage has landed (transaction count)
@@ -138,13 +133,13 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(beam_smem_raw) + 1023) & ~uintptr_t(1023));
     const int w_depth = beam_w_depth(bd.ncols);
     const int w_bytes = kBeamSub * bd.ncols * 64;
-    uint8_t *a_buf = smem;                                         // [2][2][128][64]
-    uint8_t *raw = smem + 2 * kBeamABuf;                           // [5][128][80]
+    uint8_t *a_buf = smem;                                         // [3][2][128][64]
+    uint8_t *raw = smem + kBeamABufs * kBeamABuf;                  // [3][128][64], swizzled
     uint8_t *w_buf = raw + kBeamRawDepth * kBeamRawSlot;           // [w_depth][2][ncols][64]
-    uint64_t *mma_done = reinterpret_cast<uint64_t *>(w_buf + w_depth * w_bytes);   // [2]
-    uint64_t *a_full = mma_done + 2;                                                 // [2]
-    uint64_t *w_full = a_full + 2;                                                   // [4]
-    uint64_t *drain = w_full + 4;
+    uint64_t *mma_done = reinterpret_cast<uint64_t *>(w_buf + w_depth * w_bytes);   // [3]
+    uint64_t *a_full = mma_done + kBeamABufs;                                        // [3]
+    uint64_t *w_full = a_full + kBeamABufs;                                          // [5]
+    uint64_t *drain = w_full + 5;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -156,11 +151,11 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
     const int nk = bd.k_hi - bd.k_lo;
 
     if (tid == 0) {
-        for (int i = 0; i < 2; ++i) {
+        for (int i = 0; i < kBeamABufs; ++i) {
             mbar_init(&mma_done[i], 1);
             mbar_init(&a_full[i], kBeamConvThreads / 32);
         }
-        for (int i = 0; i < 4; ++i) mbar_init(&w_full[i], 1);
+        for (int i = 0; i < 5; ++i) mbar_init(&w_full[i], 1);
         mbar_init(drain, 1);
         fence_mbar_init();
     }
@@ -176,7 +171,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
     if (warp == 8) {
         // ---------------- weight copies + MMA issue (one thread) ----------------
         if (lane == 0) {
-            const int w_ahead = w_depth - 2;
+            const int w_ahead = beam_w_ahead(bd.ncols);
             auto issue_w = [&](int i) {
                 const int slot = i % w_depth;
                 mbar_arrive_expect_tx(&w_full[slot], uint32_t(w_bytes));
@@ -187,17 +182,19 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             const uint32_t idesc = idesc_dense(kBeamRows, uint32_t(bd.ncols), 0, 0, false);
             bool ok = true;
             for (int i = 0; i < nk && ok; ++i) {
-                const int buf = i & 1, slot = i % w_depth;
-                // The weight slot of stage i + w_ahead last served stage i - 2.
-                const int next = i + w_ahead;
-                if (next < nk) {
-                    if (i >= 2 && !mbar_wait(&mma_done[buf], uint32_t((i - 2) >> 1) & 1u, status)) {
+                const int buf = i % kBeamABufs, slot = i % w_depth;
+                // The weight copy of stage j = i + w_ahead reuses the slot of stage j - w_depth.
+                const int j = i + w_ahead;
+                if (j < nk) {
+                    const int prev = j - w_depth;
+                    if (prev >= 0 && !mbar_wait(&mma_done[prev % kBeamABufs],
+                                                uint32_t(prev / kBeamABufs) & 1u, status)) {
                         ok = false;
                         break;
                     }
-                    issue_w(next);
+                    issue_w(j);
                 }
-                if (!mbar_wait(&a_full[buf], uint32_t(i >> 1) & 1u, status) ||
+                if (!mbar_wait(&a_full[buf], uint32_t(i / kBeamABufs) & 1u, status) ||
                     !mbar_wait(&w_full[slot], uint32_t(i / w_depth) & 1u, status)) {
                     ok = false;
                     break;
@@ -225,30 +222,34 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
         // ---------------- converters (and the epilogue) ----------------
         const bool vec = (bd.N & 15) == 0 && (reinterpret_cast<uintptr_t>(bd.in) & 15) == 0;
         const uint8_t *chan = bd.in + int64_t(c) * bd.T * bd.N;
-        // Stage k -> raw slot: row = time sample, 64 bytes = inputs 64k..64k+63.  Vector path:
-        // 512 pieces of 16 B, piece p = tid + 256 j covers row p / 4, bytes 16 (p % 4) .. +15,
-        // so four adjacent lanes read one row's 64 contiguous bytes.  Outside [0,T) x [0,N)
-        // the slot holds zeros (value 0 + 0i).
+        // Converter warp w owns time rows 16w .. 16w + 15 end to end: it copies their bytes
+        // into the raw ring, converts them and arrives on a_full, so the warps never wait on
+        // each other.  Stage k -> raw slot: row = time sample, 64 bytes = inputs
+        // 64k..64k+63.  Vector path: the warp's 64 pieces of 16 B, piece p = lane + 32 j
+        // covers row 16w + p / 4, bytes 16 (p % 4) .. +15 (four adjacent lanes read one row's
+        // 64 contiguous bytes).  Outside [0,T) x [0,N) the slot holds zeros (value 0 + 0i).
+        const int r = 16 * warp + (lane >> 1), half = lane & 1;   // conversion: row r, sub-tile `half`
         auto issue_raw = [&](int k, int slot) {
             uint8_t *dst = raw + slot * kBeamRawSlot;
             if (vec) {
 #pragma unroll
                 for (int j = 0; j < 2; ++j) {
-                    const int p = tid + kBeamConvThreads * j;
-                    const int row = p >> 2, col = (p & 3) * 16;
+                    const int p = lane + 32 * j;
+                    const int row = 16 * warp + (p >> 2), col = (p & 3) * 16;
                     const int64_t t = t0 + row;
                     const int64_t n = int64_t(k) * kBeamChunk + col;
                     const bool ok = t < bd.T && n < bd.N;
-                    beam_cp_async16(dst + row * kBeamRawStride + col,
+                    beam_cp_async16(dst + row * 64 + ((col >> 4) ^ ((row >> 1) & 3)) * 16,
                                     ok ? static_cast<const void *>(chan + t * bd.N + n) : static_cast<const void *>(bd.in),
                                     ok ? 16u : 0u);
                 }
             } else {
-                const int row = tid & (kBeamRows - 1), half = tid >> 7;
-                const int64_t t = t0 + row;
+                const int64_t t = t0 + r;
                 for (int b = 0; b < 32; ++b) {
-                    const int64_t n = int64_t(k) * kBeamChunk + 32 * half + b;
-                    dst[row * kBeamRawStride + 32 * half + b] = (t < bd.T && n < bd.N) ? chan[t * bd.N + n] : uint8_t(0);
+                    const int col = 32 * half + b;
+                    const int64_t n = int64_t(k) * kBeamChunk + col;
+                    dst[r * 64 + ((((col >> 4) ^ ((r >> 1) & 3))) << 4) + (col & 15)] =
+                        (t < bd.T && n < bd.N) ? chan[t * bd.N + n] : uint8_t(0);
                 }
             }
         };
@@ -257,27 +258,30 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             if (i < nk) issue_raw(bd.k_lo + i, i);
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
-        const int r = tid & (kBeamRows - 1), half = tid >> 7;   // conversion: row r, sub-tile `half`
-        bool ok = true, late = false;
+        bool ok = true;
         for (int i = 0; i < nk; ++i) {
-            const int buf = i & 1;
+            const int buf = i % kBeamABufs;
             asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 1) : "memory");
-            // All converters: stage i has landed in its slot (byte stores of the scalar path
-            // included), stage i - 1 has been read from the slot refilled below, and nobody
-            // timed out.
-            if (conv_bar_or(late)) {
+            // The warp's copies of stage i have landed (byte stores of the scalar path
+            // included) and its lanes have finished reading stage i - 1 from the slot that is
+            // refilled below.
+            __syncwarp();
+            if (i + kAhead < nk) issue_raw(bd.k_lo + i + kAhead, (i + kAhead) % kBeamRawDepth);
+            asm volatile("cp.async.commit_group;" ::: "memory");
+            // A tile `buf` is free once the MMAs of stage i - 3 have completed; the warp
+            // decides together (a lane that gave up stops the whole warp).
+            const bool free_ok = i < kBeamABufs ||
+                                 mbar_wait(&mma_done[buf], uint32_t((i - kBeamABufs) / kBeamABufs) & 1u, status);
+            if (__any_sync(0xffffffffu, !free_ok)) {
                 ok = false;
                 break;
             }
-            if (i + kAhead < nk) issue_raw(bd.k_lo + i + kAhead, (i + kAhead) % kBeamRawDepth);
-            asm volatile("cp.async.commit_group;" ::: "memory");
-            // A tile `buf` is free once the MMAs of stage i - 2 have completed.
-            if (i >= 2 && !mbar_wait(&mma_done[buf], uint32_t((i - 2) >> 1) & 1u, status)) late = true;
             // Row r, inputs 32 half .. +31: 8 raw words -> 16 words of {re, im} e4m3 pairs;
             // 16-byte piece q = inputs 8q..8q+7, XOR-swizzled by row.
-            const uint8_t *src = raw + (i % kBeamRawDepth) * kBeamRawSlot + r * kBeamRawStride + 32 * half;
-            const uint4 w0 = *reinterpret_cast<const uint4 *>(src);
-            const uint4 w1 = *reinterpret_cast<const uint4 *>(src + 16);
+            const uint8_t *src = raw + (i % kBeamRawDepth) * kBeamRawSlot + r * 64;
+            const int sw = (r >> 1) & 3;
+            const uint4 w0 = *reinterpret_cast<const uint4 *>(src + (((2 * half) ^ sw) << 4));
+            const uint4 w1 = *reinterpret_cast<const uint4 *>(src + (((2 * half + 1) ^ sw) << 4));
             const uint32_t rw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
             uint8_t *dst = a_buf + buf * kBeamABuf + half * kBeamASub + r * 64;
 #pragma unroll
@@ -298,15 +302,18 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
         }
         asm volatile("cp.async.wait_all;" ::: "memory");
         // Every MMA of this CTA has completed once the last stage's commit has arrived.
-        if (ok && nk > 0 && !mbar_wait(&mma_done[(nk - 1) & 1], uint32_t((nk - 1) >> 1) & 1u, status)) ok = false;
+        if (ok && nk > 0 &&
+            !mbar_wait(&mma_done[(nk - 1) % kBeamABufs], uint32_t((nk - 1) / kBeamABufs) & 1u, status))
+            ok = false;
         if (!ok) atomicCAS(bd.status, 0, kStatusTimeoutEpilogue);
         tc_fence_after();
         if (ok && *status == 0) {
             // Tensor-memory lane = row = sample t; column 4b + {Re hi, Im hi, Re lo, Im lo}.
-            // Warps w and w + 4 read the same lanes (w % 4) and split the 32-column groups.
-            const int64_t t = t0 + r;
+            // Warp w reads lanes 32 (w % 4) .. +31 (lane l: row 32 (w % 4) + l); warps w and
+            // w + 4 split the 32-column groups.
+            const int64_t t = t0 + 32 * (warp & 3) + lane;
             int32_t *yrow = bd.y + ((int64_t(c) * bd.T + t) * bd.B_total + bd.b0) * 2;
-            for (int c0 = 32 * half; c0 < bd.ncols; c0 += 64) {
+            for (int c0 = 32 * (warp >> 2); c0 < bd.ncols; c0 += 64) {
                 uint32_t v[32];
                 tmem_ld_32x32b_x32(tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(c0), v);
                 tmem_ld_wait();
