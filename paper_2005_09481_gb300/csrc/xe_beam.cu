@@ -8,7 +8,7 @@
 //     Re y_b = sum_i (wr a - wi c),    Im y_b = sum_i (wi a + wr c).
 // Each int8 weight component is split exactly as w = 16 w_hi + w_lo with w_lo in [-8, 7] and
 // w_hi in [-8, 8], so every operand is an integer of magnitude <= 16, exact in FP8 e4m3:
-//     D[t][col] = sum_k X'[t][k] W'[col][k],   K = 2N (inputs, re and im interleaved),
+//     D[t][col] = sum_k X'[t][k] W'[col][k],   K = 2N (per input: im at 2n, re at 2n + 1),
 //     col = 4b + {0: Re hi, 1: Im hi, 2: Re lo, 3: Im lo},   y_b = 16 D[hi] + D[lo],
 // one tcgen05 kind::f8f6f4 MMA chain per 128 time samples, f32 accumulation in tensor memory.
 // Exact: every partial sum is an integer of magnitude <= 128 N < 2^24 (N <= 65536).
@@ -70,8 +70,9 @@ __device__ __forceinline__ int w_lo(int w) { return ((w + 8) & 15) - 8; }
 __device__ __forceinline__ int w_hi(int w) { return (w - w_lo(w)) / 16; }
 
 // One thread per 16-byte piece of the tile image: (chunk k, sub-tile s, row col, piece q)
-// holds inputs n = 64k + 32s + 8q .. +7, each as two e4m3 codes {K = (n, re), K = (n, im)}:
-//   Re rows (col % 4 = 0 hi, 2 lo):  { w_r, -w_i }     Im rows (col % 4 = 1 hi, 3 lo): { w_i, w_r }
+// holds inputs n = 64k + 32s + 8q .. +7, each as two e4m3 codes {K = (n, im), K = (n, re)}
+// (the order the converters produce, the nibble order of a packed sample):
+//   Re rows (col % 4 = 0 hi, 2 lo):  { -w_i, w_r }     Im rows (col % 4 = 1 hi, 3 lo): { w_r, w_i }
 // of weight beam b0 + col / 4.  Rows past the launch's nb beams and inputs n >= N are zero.
 __global__ void beam_weight_kernel(const int8_t *__restrict__ w, int b0, int nb, int N, int ncols,
                                    int n_chunks, uint8_t *__restrict__ wt) {
@@ -97,9 +98,9 @@ __global__ void beam_weight_kernel(const int8_t *__restrict__ w, int b0, int nb,
                 const bool hi = part < 2;
                 const int pr = hi ? w_hi(wr) : w_lo(wr), pi = hi ? w_hi(wi) : w_lo(wi);
                 const bool im_row = part & 1;
-                const int k_re = im_row ? pi : pr;
-                const int k_im = im_row ? pr : -pi;
-                pair |= (encode_small_int(k_re, 1) | (encode_small_int(k_im, 1) << 8)) << (16 * h);
+                const int k_re = im_row ? pi : pr;      // coefficient of the input's re part
+                const int k_im = im_row ? pr : -pi;     // coefficient of its im part
+                pair |= (encode_small_int(k_im, 1) | (encode_small_int(k_re, 1) << 8)) << (16 * h);
             }
             v[u2] = pair;
         }
@@ -276,7 +277,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
                 ok = false;
                 break;
             }
-            // Row r, inputs 32 half .. +31: 8 raw words -> 16 words of {re, im} e4m3 pairs;
+            // Row r, inputs 32 half .. +31: 8 raw words -> 16 words of {im, re} e4m3 pairs;
             // 16-byte piece q = inputs 8q..8q+7, XOR-swizzled by row.
             const uint8_t *src = raw + (i % kBeamRawDepth) * kBeamRawSlot + r * 64;
             const int sw = (r >> 1) & 3;
@@ -288,12 +289,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             for (int q = 0; q < 4; ++q) {
                 uint32_t o[4];
 #pragma unroll
-                for (int u = 0; u < 2; ++u) {
-                    uint32_t re, im;
-                    e4m3_of_bytes(rw[2 * q + u], re, im);
-                    o[2 * u] = __byte_perm(re, im, 0x5140);
-                    o[2 * u + 1] = __byte_perm(re, im, 0x7362);
-                }
+                for (int u = 0; u < 2; ++u) e4m3_of_bytes_nibble_order(rw[2 * q + u], o[2 * u], o[2 * u + 1]);
                 *reinterpret_cast<uint4 *>(dst + ((q ^ ((r >> 1) & 3)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
             }
             fence_proxy_async_smem();

@@ -26,43 +26,31 @@ __host__ __device__ constexpr uint32_t pack_codes(int lo) {
            (encode_small_int(nibble_value(lo + 2), 1) << 16) | (encode_small_int(nibble_value(lo + 3), 1) << 24);
 }
 
-// Four two's-complement nibbles (one in the low 4 bits of each byte) -> four e4m3 codes.
-// A byte permute looks each nibble up in the 16-entry code table (held in four words:
-// values 0..3, 4..7, -8..-5, -4..-1): the low 3 bits select within the non-negative or the
-// negative half, bit 3 chooses the half.
-__device__ __forceinline__ uint32_t e4m3_of_nibbles(uint32_t x) {
+// Four packed samples -> their eight e4m3 codes in nibble order: lo = {im0, re0, im1, re1},
+// hi = {im2, re2, im3, re3} (byte k of v: high nibble re_k, low nibble im_k).  The word's own
+// nibbles, with bit 3 cleared, are the byte-permute selectors into the code tables (the
+// selector uses the low 16 bits, i.e. samples 0 and 1, hence the shift for samples 2 and 3);
+// the sign masks come from sign-replicate selectors on v (re signs, bit 7 of each byte) and
+// v << 4 (im signs, bit 3).
+__device__ __forceinline__ void e4m3_of_bytes_nibble_order(uint32_t v, uint32_t &lo, uint32_t &hi) {
     constexpr uint32_t P0 = pack_codes(0), P1 = pack_codes(4), N0 = pack_codes(8), N1 = pack_codes(12);
-    const uint32_t y = x & 0x07070707u;
-    const uint32_t z = y | (y >> 4);
-    const uint32_t sel = __byte_perm(z, 0, 0x0020);
-    const uint32_t pos = __byte_perm(P0, P1, sel);
-    const uint32_t neg = __byte_perm(N0, N1, sel);
-    const uint32_t m = ((x >> 3) & 0x01010101u) * 0xFFu;
-    return (pos & ~m) | (neg & m);
+    const uint32_t m = v & 0x77777777u;
+    const uint32_t v4 = v << 4;
+    uint32_t ml, mh;
+    asm("prmt.b32 %0, %1, %2, 0x9D8C;" : "=r"(ml) : "r"(v), "r"(v4));
+    asm("prmt.b32 %0, %1, %2, 0xBFAE;" : "=r"(mh) : "r"(v), "r"(v4));
+    lo = (__byte_perm(P0, P1, m) & ~ml) | (__byte_perm(N0, N1, m) & ml);
+    const uint32_t m2 = m >> 16;
+    hi = (__byte_perm(P0, P1, m2) & ~mh) | (__byte_perm(N0, N1, m2) & mh);
 }
 
-// Byte k of the result = 0xFF if bit 7 of byte k of a is set, else 0 (the byte permute's
-// sign-replicate selectors 8..11; the __byte_perm intrinsic uses 3-bit selectors only).
-__device__ __forceinline__ uint32_t byte_sign_mask(uint32_t a) {
-    uint32_t d;
-    asm("prmt.b32 %0, %1, 0, 0xBA98;" : "=r"(d) : "r"(a));
-    return d;
-}
-
-// Four packed samples (byte k: high nibble re, low nibble im, two's complement) -> the e4m3
-// codes of their real parts (re) and imaginary parts (im), byte k each.  The same table
-// lookup as e4m3_of_nibbles, with the sign masks taken directly from the nibbles' top bits:
-// the re sign is bit 7 of each byte, the im sign bit 3 (bit 7 after a 4-bit shift).
+// Four packed samples -> the e4m3 codes of their real parts (re) and imaginary parts (im),
+// byte k each: the nibble-order codes above, de-interleaved by two byte permutes.
 __device__ __forceinline__ void e4m3_of_bytes(uint32_t v, uint32_t &re, uint32_t &im) {
-    constexpr uint32_t P0 = pack_codes(0), P1 = pack_codes(4), N0 = pack_codes(8), N1 = pack_codes(12);
-    const uint32_t yi = v & 0x07070707u;
-    const uint32_t si = __byte_perm(yi | (yi >> 4), 0, 0x0020);
-    const uint32_t mi = byte_sign_mask(v << 4);
-    im = (__byte_perm(P0, P1, si) & ~mi) | (__byte_perm(N0, N1, si) & mi);
-    const uint32_t yr = (v >> 4) & 0x07070707u;
-    const uint32_t sr = __byte_perm(yr | (yr >> 4), 0, 0x0020);
-    const uint32_t mr = byte_sign_mask(v);
-    re = (__byte_perm(P0, P1, sr) & ~mr) | (__byte_perm(N0, N1, sr) & mr);
+    uint32_t lo, hi;
+    e4m3_of_bytes_nibble_order(v, lo, hi);
+    re = __byte_perm(lo, hi, 0x7531);
+    im = __byte_perm(lo, hi, 0x6420);
 }
 
 }  // namespace xe
