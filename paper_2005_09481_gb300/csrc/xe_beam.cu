@@ -16,12 +16,14 @@
 // beam_weight_kernel  int8 w[B][N][2] -> e4m3 B-operand tiles [chunk][2][ncols][64 B] in the
 //                     64-byte-swizzled image the MMA reads (one bulk copy per stage).
 // beam_kernel         one CTA per (channel, 128 samples).  Eight converter warps, each owning
-//                     16 sample rows end to end, stream the packed bytes of each stage into a
-//                     3-deep shared-memory ring with coalesced cp.async (4 lanes per 64-byte
-//                     row piece) and convert them to a triple-buffered e4m3 A tile; a ninth warp
-//                     streams the weight tiles through a ring of bulk copies and issues the
-//                     MMAs; the roles meet on mbarriers.  The converter warps then read tensor
-//                     memory and write y[c][t][b][re, im].
+//                     half of every stage's bytes for 32 sample rows end to end, stream the
+//                     packed bytes into a 3-deep shared-memory ring with cp.async (whole
+//                     32-byte sectors) and convert them into a ring of four e4m3 A tiles held
+//                     in tensor memory (tcgen05.st; the MMA reads A from there, so the A tiles
+//                     cost no shared-memory bandwidth); a ninth warp streams the weight tiles
+//                     through a ring of bulk copies and issues the MMAs; the roles meet on
+//                     mbarriers.  The converter warps then read the accumulator and write
+//                     y[c][t][b][re, im].
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -31,14 +33,13 @@
 
 namespace xe {
 
-constexpr int kBeamSub = 2;                         // sub-tiles of 32 inputs (64 B of e4m3) per stage
-constexpr int kBeamASub = kBeamRows * 64;           // 8 KB
-constexpr int kBeamABuf = kBeamSub * kBeamASub;     // 16 KB
-constexpr int kBeamABufs = 3;                       // A tiles: conversion waits for stage i - 3
+constexpr int kBeamSub = 2;                         // weight sub-tiles of 32 inputs (64 B of e4m3) per stage
+constexpr int kBeamACols = 32;                      // tensor-memory columns of one A tile (128 B per row)
+constexpr int kBeamABufs = 4;                       // A tiles: conversion waits for stage i - 4
 constexpr int kBeamRawSlot = kBeamRows * 64;        // raw ring slot: 64-byte rows, 16-byte pieces
                                                     // XOR-swizzled by (row >> 1) & 3
 constexpr int kBeamRawDepth = 3;                    // raw slots: stages in flight = depth - 1
-constexpr int kBeamConvThreads = 256;               // 8 converter warps, two threads per row
+constexpr int kBeamConvThreads = 256;               // 8 converter warps, two per tensor-memory lane quarter
 constexpr int kBeamThreads = kBeamConvThreads + 32; // + 1 MMA / weight-copy warp
 
 int beam_ncols(int B) { return (4 * (B < kBeamMaxPerLaunch ? B : kBeamMaxPerLaunch) + 15) / 16 * 16; }
@@ -48,19 +49,24 @@ size_t beam_wt_bytes(int B, int N) {
     return chunks * kBeamSub * size_t(beam_ncols(B)) * 64;
 }
 
-// Weight ring for an MMA width: `depth` slots, copies issued `ahead` stages early.  The copy
-// of stage j reuses the slot of stage j - depth, so issuing it (at stage j - ahead) waits for
-// the MMAs of stage j - depth, depth - ahead = 3 stages back.  Up to 64 columns two CTAs fit
-// on an SM (<= 114 KB each, the 1 KB per-CTA reservation included); wider MMAs run one CTA
-// per SM and take the deeper ring.
-__host__ __device__ constexpr int beam_w_depth(int ncols) {
-    return ncols <= 48 ? 5 : ncols <= 64 ? 4 : ncols <= 128 ? 5 : 4;
-}
-__host__ __device__ constexpr int beam_w_ahead(int ncols) { return beam_w_depth(ncols) - 3; }
+// Weight ring: 5 slots, copies issued 2 stages early.  The copy of stage j reuses the slot of
+// stage j - 5, so issuing it (at stage j - 2) waits for the MMAs of stage j - 5, 3 stages
+// back.  Up to 128 columns two CTAs fit on an SM (<= 106 KB of shared memory and 256
+// tensor-memory columns each).
+constexpr int kBeamWDepth = 5, kBeamWAhead = 2;
 
 static int beam_smem_bytes(int ncols) {
-    return 1024 /*align*/ + kBeamABufs * kBeamABuf + kBeamRawDepth * kBeamRawSlot +
-           beam_w_depth(ncols) * kBeamSub * ncols * 64 + 128 /*barriers, tensor-memory slot*/;
+    return 1024 /*align*/ + kBeamRawDepth * kBeamRawSlot + kBeamWDepth * kBeamSub * ncols * 64 +
+           128 /*barriers, tensor-memory slot*/;
+}
+
+// Tensor-memory columns: the accumulator (ncols rounded up to a power of two, >= 32), then
+// the ring of A tiles; the allocation is the next power of two.
+__host__ __device__ constexpr uint32_t beam_acc_cols(int ncols) {
+    return ncols <= 32 ? 32u : ncols <= 64 ? 64u : ncols <= 128 ? 128u : 256u;
+}
+__host__ __device__ constexpr uint32_t beam_tmem_cols(int ncols) {
+    return beam_acc_cols(ncols) + kBeamABufs * kBeamACols <= 256u ? 256u : 512u;
 }
 
 // ---- weights -> B operand tiles --------------------------------------------------------
@@ -125,22 +131,44 @@ __device__ __forceinline__ void beam_cp_async16(void *dst, const void *src, uint
                  : "memory");
 }
 
+// D (tensor memory) [+]= A (tensor memory: row m in lane m, 4 e4m3 values of K per 32-bit
+// column) x B (shared-memory descriptor), kind::f8f6f4, f32 accumulation.
+__device__ __forceinline__ void mma_f8f6f4_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                                  uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate)
+        : "memory");
+}
+
+// Warp-collective store of 16 consecutive 32-bit columns: thread l writes lane
+// (taddr lane) + l, register i to column (taddr column) + i.
+__device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const uint32_t (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], "
+        "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(taddr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+        "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_st_wait() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // Roles (see the file header).  Barriers:
-//   a_full[buf]   8 converter warps arrive when A tile `buf` holds its stage
+//   a_full[buf]   8 converter warps arrive when A tile `buf` (tensor memory) holds its stage
 //   w_full[slot]  the weight tile of a stage has landed (transaction count)
 //   mma_done[buf] the MMAs that read A tile `buf` (and the stage's weight slot) completed
 __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constant__ BeamDev bd) {
     extern __shared__ uint8_t beam_smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(beam_smem_raw) + 1023) & ~uintptr_t(1023));
-    const int w_depth = beam_w_depth(bd.ncols);
     const int w_bytes = kBeamSub * bd.ncols * 64;
-    uint8_t *a_buf = smem;                                         // [3][2][128][64]
-    uint8_t *raw = smem + kBeamABufs * kBeamABuf;                  // [3][128][64], swizzled
-    uint8_t *w_buf = raw + kBeamRawDepth * kBeamRawSlot;           // [w_depth][2][ncols][64]
-    uint64_t *mma_done = reinterpret_cast<uint64_t *>(w_buf + w_depth * w_bytes);   // [3]
-    uint64_t *a_full = mma_done + kBeamABufs;                                        // [3]
-    uint64_t *w_full = a_full + kBeamABufs;                                          // [5]
-    uint64_t *drain = w_full + 5;
+    uint8_t *raw = smem;                                           // [3][128][64], swizzled
+    uint8_t *w_buf = raw + kBeamRawDepth * kBeamRawSlot;           // [5][2][ncols][64]
+    uint64_t *mma_done = reinterpret_cast<uint64_t *>(w_buf + kBeamWDepth * w_bytes);   // [4]
+    uint64_t *a_full = mma_done + kBeamABufs;                                            // [4]
+    uint64_t *w_full = a_full + kBeamABufs;                                              // [5]
+    uint64_t *drain = w_full + kBeamWDepth;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -148,7 +176,8 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
     const int c = int(blockIdx.x / tiles_per_chan);
     const int64_t t0 = (blockIdx.x % tiles_per_chan) * kBeamRows;
     volatile int *status = bd.status;
-    const uint32_t tmem_cols = bd.ncols <= 32 ? 32u : bd.ncols <= 64 ? 64u : bd.ncols <= 128 ? 128u : 256u;
+    const uint32_t tmem_cols = beam_tmem_cols(bd.ncols);
+    const uint32_t a_col0 = beam_acc_cols(bd.ncols);       // first column of the A ring
     const int nk = bd.k_hi - bd.k_lo;
 
     if (tid == 0) {
@@ -156,7 +185,7 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             mbar_init(&mma_done[i], 1);
             mbar_init(&a_full[i], kBeamConvThreads / 32);
         }
-        for (int i = 0; i < 5; ++i) mbar_init(&w_full[i], 1);
+        for (int i = 0; i < kBeamWDepth; ++i) mbar_init(&w_full[i], 1);
         mbar_init(drain, 1);
         fence_mbar_init();
     }
@@ -172,22 +201,21 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
     if (warp == 8) {
         // ---------------- weight copies + MMA issue (one thread) ----------------
         if (lane == 0) {
-            const int w_ahead = beam_w_ahead(bd.ncols);
             auto issue_w = [&](int i) {
-                const int slot = i % w_depth;
+                const int slot = i % kBeamWDepth;
                 mbar_arrive_expect_tx(&w_full[slot], uint32_t(w_bytes));
                 bulk_g2s(w_buf + slot * w_bytes, bd.wt + int64_t(bd.k_lo + i) * w_bytes, uint32_t(w_bytes),
                          &w_full[slot]);
             };
-            for (int i = 0; i < w_ahead && i < nk; ++i) issue_w(i);
+            for (int i = 0; i < kBeamWAhead && i < nk; ++i) issue_w(i);
             const uint32_t idesc = idesc_dense(kBeamRows, uint32_t(bd.ncols), 0, 0, false);
             bool ok = true;
             for (int i = 0; i < nk && ok; ++i) {
-                const int buf = i % kBeamABufs, slot = i % w_depth;
-                // The weight copy of stage j = i + w_ahead reuses the slot of stage j - w_depth.
-                const int j = i + w_ahead;
+                const int buf = i % kBeamABufs, slot = i % kBeamWDepth;
+                // The weight copy of stage j = i + 2 reuses the slot of stage j - 5.
+                const int j = i + kBeamWAhead;
                 if (j < nk) {
-                    const int prev = j - w_depth;
+                    const int prev = j - kBeamWDepth;
                     if (prev >= 0 && !mbar_wait(&mma_done[prev % kBeamABufs],
                                                 uint32_t(prev / kBeamABufs) & 1u, status)) {
                         ok = false;
@@ -196,19 +224,22 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
                     issue_w(j);
                 }
                 if (!mbar_wait(&a_full[buf], uint32_t(i / kBeamABufs) & 1u, status) ||
-                    !mbar_wait(&w_full[slot], uint32_t(i / w_depth) & 1u, status)) {
+                    !mbar_wait(&w_full[slot], uint32_t(i / kBeamWDepth) & 1u, status)) {
                     ok = false;
                     break;
                 }
                 tc_fence_after();
-                const uint32_t a0 = smem_u32(a_buf + buf * kBeamABuf), b0 = smem_u32(w_buf + slot * w_bytes);
+                // MMA (s, h) covers inputs 32 s + 16 h .. +15: A columns 16 s + 8 h .. +7 of the
+                // tile, B bytes 32 h .. +31 of weight sub-tile s.
+                const uint32_t a0 = tmem + a_col0 + uint32_t(buf * kBeamACols);
+                const uint32_t b0 = smem_u32(w_buf + slot * w_bytes);
 #pragma unroll
                 for (int s2 = 0; s2 < kBeamSub; ++s2)
 #pragma unroll
                     for (int h = 0; h < 2; ++h)
-                        mma_f8f6f4(tmem, sdesc_k_sw64(a0 + s2 * kBeamASub + 32 * h),
-                                   sdesc_k_sw64(b0 + s2 * bd.ncols * 64 + 32 * h), idesc,
-                                   (i > 0 || s2 > 0 || h > 0) ? 1u : 0u);
+                        mma_f8f6f4_tmem_a(tmem, a0 + uint32_t(16 * s2 + 8 * h),
+                                          sdesc_k_sw64(b0 + s2 * bd.ncols * 64 + 32 * h), idesc,
+                                          (i > 0 || s2 > 0 || h > 0) ? 1u : 0u);
                 mma_commit(&mma_done[buf]);
             }
             if (!ok) {
@@ -223,31 +254,32 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
         // ---------------- converters (and the epilogue) ----------------
         const bool vec = (bd.N & 15) == 0 && (reinterpret_cast<uintptr_t>(bd.in) & 15) == 0;
         const uint8_t *chan = bd.in + int64_t(c) * bd.T * bd.N;
-        // Converter warp w owns time rows 16w .. 16w + 15 end to end: it copies their bytes
-        // into the raw ring, converts them and arrives on a_full, so the warps never wait on
-        // each other.  Stage k -> raw slot: row = time sample, 64 bytes = inputs
-        // 64k..64k+63.  Vector path: the warp's 64 pieces of 16 B, piece p = lane + 32 j
-        // covers row 16w + p / 4, bytes 16 (p % 4) .. +15 (four adjacent lanes read one row's
-        // 64 contiguous bytes).  Outside [0,T) x [0,N) the slot holds zeros (value 0 + 0i).
-        const int r = 16 * warp + (lane >> 1), half = lane & 1;   // conversion: row r, sub-tile `half`
+        // Warp w serves tensor-memory lanes 32 (w % 4) .. +31 (the lane quarter it may access)
+        // and part p = w / 4 of every stage: inputs 32 p .. 32 p + 31, raw bytes 32 p .. +31 of
+        // each of its 32 sample rows.  It copies those bytes into the raw ring, converts them
+        // and stores them to tensor memory itself, so the warps never wait on each other.
+        // Copies: lane l takes rows 32 (w % 4) + (l % 16) + 16 jj, 16-byte piece 2 p + l / 16
+        // (lanes l and l + 16 read one whole 32-byte sector).  Outside [0,T) x [0,N) the bytes
+        // are zero (value 0 + 0i).
+        const int quarter = warp & 3, part = warp >> 2;
+        const int r = 32 * quarter + lane;                       // conversion: sample row r
         auto issue_raw = [&](int k, int slot) {
             uint8_t *dst = raw + slot * kBeamRawSlot;
             if (vec) {
 #pragma unroll
-                for (int j = 0; j < 2; ++j) {
-                    const int p = lane + 32 * j;
-                    const int row = 16 * warp + (p >> 2), col = (p & 3) * 16;
+                for (int jj = 0; jj < 2; ++jj) {
+                    const int row = 32 * quarter + (lane & 15) + 16 * jj, piece = 2 * part + (lane >> 4);
                     const int64_t t = t0 + row;
-                    const int64_t n = int64_t(k) * kBeamChunk + col;
+                    const int64_t n = int64_t(k) * kBeamChunk + 16 * piece;
                     const bool ok = t < bd.T && n < bd.N;
-                    beam_cp_async16(dst + row * 64 + ((col >> 4) ^ ((row >> 1) & 3)) * 16,
+                    beam_cp_async16(dst + row * 64 + ((piece ^ ((row >> 1) & 3)) << 4),
                                     ok ? static_cast<const void *>(chan + t * bd.N + n) : static_cast<const void *>(bd.in),
                                     ok ? 16u : 0u);
                 }
             } else {
                 const int64_t t = t0 + r;
                 for (int b = 0; b < 32; ++b) {
-                    const int col = 32 * half + b;
+                    const int col = 32 * part + b;
                     const int64_t n = int64_t(k) * kBeamChunk + col;
                     dst[r * 64 + ((((col >> 4) ^ ((r >> 1) & 3))) << 4) + (col & 15)] =
                         (t < bd.T && n < bd.N) ? chan[t * bd.N + n] : uint8_t(0);
@@ -260,6 +292,8 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             asm volatile("cp.async.commit_group;" ::: "memory");
         }
         bool ok = true;
+        const int sw = (r >> 1) & 3;
+        const uint32_t lane_base = uint32_t(32 * quarter) << 16;
         for (int i = 0; i < nk; ++i) {
             const int buf = i % kBeamABufs;
             asm volatile("cp.async.wait_group %0;" ::"n"(kAhead - 1) : "memory");
@@ -269,7 +303,15 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             __syncwarp();
             if (i + kAhead < nk) issue_raw(bd.k_lo + i + kAhead, (i + kAhead) % kBeamRawDepth);
             asm volatile("cp.async.commit_group;" ::: "memory");
-            // A tile `buf` is free once the MMAs of stage i - 3 have completed; the warp
+            // Row r, inputs 32 part .. +31: 8 raw words -> 16 columns of {im, re} e4m3 pairs.
+            const uint8_t *src = raw + (i % kBeamRawDepth) * kBeamRawSlot + r * 64;
+            const uint4 w0 = *reinterpret_cast<const uint4 *>(src + (((2 * part) ^ sw) << 4));
+            const uint4 w1 = *reinterpret_cast<const uint4 *>(src + (((2 * part + 1) ^ sw) << 4));
+            const uint32_t rw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+            uint32_t o[16];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) e4m3_of_bytes_nibble_order(rw[q], o[2 * q], o[2 * q + 1]);
+            // A tile `buf` is free once the MMAs of stage i - 4 have completed; the warp
             // decides together (a lane that gave up stops the whole warp).
             const bool free_ok = i < kBeamABufs ||
                                  mbar_wait(&mma_done[buf], uint32_t((i - kBeamABufs) / kBeamABufs) & 1u, status);
@@ -277,22 +319,10 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
                 ok = false;
                 break;
             }
-            // Row r, inputs 32 half .. +31: 8 raw words -> 16 words of {im, re} e4m3 pairs;
-            // 16-byte piece q = inputs 8q..8q+7, XOR-swizzled by row.
-            const uint8_t *src = raw + (i % kBeamRawDepth) * kBeamRawSlot + r * 64;
-            const int sw = (r >> 1) & 3;
-            const uint4 w0 = *reinterpret_cast<const uint4 *>(src + (((2 * half) ^ sw) << 4));
-            const uint4 w1 = *reinterpret_cast<const uint4 *>(src + (((2 * half + 1) ^ sw) << 4));
-            const uint32_t rw[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-            uint8_t *dst = a_buf + buf * kBeamABuf + half * kBeamASub + r * 64;
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                uint32_t o[4];
-#pragma unroll
-                for (int u = 0; u < 2; ++u) e4m3_of_bytes_nibble_order(rw[2 * q + u], o[2 * u], o[2 * u + 1]);
-                *reinterpret_cast<uint4 *>(dst + ((q ^ ((r >> 1) & 3)) << 4)) = make_uint4(o[0], o[1], o[2], o[3]);
-            }
-            fence_proxy_async_smem();
+            tc_fence_after();
+            tmem_st_32x32b_x16(tmem + lane_base + a_col0 + uint32_t(buf * kBeamACols + 16 * part), o);
+            tmem_st_wait();
+            tc_fence_before();
             __syncwarp();
             if (lane == 0) mbar_arrive(&a_full[buf]);
         }
@@ -307,21 +337,21 @@ __global__ void __launch_bounds__(kBeamThreads) beam_kernel(const __grid_constan
             // Tensor-memory lane = row = sample t; column 4b + {Re hi, Im hi, Re lo, Im lo}.
             // Warp w reads lanes 32 (w % 4) .. +31 (lane l: row 32 (w % 4) + l); warps w and
             // w + 4 split the 32-column groups.
-            const int64_t t = t0 + 32 * (warp & 3) + lane;
+            const int64_t t = t0 + r;
             int32_t *yrow = bd.y + ((int64_t(c) * bd.T + t) * bd.B_total + bd.b0) * 2;
-            for (int c0 = 32 * (warp >> 2); c0 < bd.ncols; c0 += 64) {
+            for (int c0 = 32 * part; c0 < bd.ncols; c0 += 64) {
                 uint32_t v[32];
-                tmem_ld_32x32b_x32(tmem + (uint32_t((warp & 3) * 32) << 16) + uint32_t(c0), v);
+                tmem_ld_32x32b_x32(tmem + lane_base + uint32_t(c0), v);
                 tmem_ld_wait();
                 if (t < bd.T) {
 #pragma unroll
-                    for (int j = 0; j < 8; ++j) {
-                        const int b = c0 / 4 + j;
+                    for (int jj = 0; jj < 8; ++jj) {
+                        const int b = c0 / 4 + jj;
                         if (b < bd.B) {
-                            yrow[2 * b] = 16 * __float2int_rn(__uint_as_float(v[4 * j + 0])) +
-                                          __float2int_rn(__uint_as_float(v[4 * j + 2]));
-                            yrow[2 * b + 1] = 16 * __float2int_rn(__uint_as_float(v[4 * j + 1])) +
-                                              __float2int_rn(__uint_as_float(v[4 * j + 3]));
+                            yrow[2 * b] = 16 * __float2int_rn(__uint_as_float(v[4 * jj + 0])) +
+                                          __float2int_rn(__uint_as_float(v[4 * jj + 2]));
+                            yrow[2 * b + 1] = 16 * __float2int_rn(__uint_as_float(v[4 * jj + 1])) +
+                                              __float2int_rn(__uint_as_float(v[4 * jj + 3]));
                         }
                     }
                 }
