@@ -411,8 +411,8 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *   "autotune"       1 = time every (tile width, schedule) candidate the first time a
  *                    batch shape is correlated and keep the fastest for that shape;
  *   "timing"         1 = record device times of each call (see xe_last_timing);
- *   "count_weight"   cost of a count job's k-iteration in schedule 5, percent of a data
- *                    job's (1 .. 100, default 50);
+ *   "count_weight"   cost of a count job's k-iteration (two sample blocks) in schedule 5,
+ *                    percent of a data job's (1 .. 100, default 75);
  *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 5, percent of
  *                    a whole tile (0 .. 100, default 2);
  *   "host_chunk_t"   samples per chunk of the host-buffer entry points' copy/correlate

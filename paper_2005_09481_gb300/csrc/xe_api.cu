@@ -54,7 +54,7 @@ struct Options {
     int inject_stall = 0;                  // test hook for the bounded-wait path (next call only)
     int64_t host_chunk_t = 8192;           // samples per pipelined chunk of xe_correlate_host
                                            // (0: one copy, then one correlation)
-    int count_weight = 50;                 // cost of a count-job k-iteration, % of a data one
+    int count_weight = 75;                 // cost of a count-job k-iteration, % of a data one
     int part_overhead = 2;                 // modelled cost of one extra tile part, % of a
                                            // whole data tile (workspace fix-up)
 };
@@ -758,8 +758,13 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 cj.accumulate = 0;
                 cj.vis = sc->cvis + cvis_off[size_t(q)];
                 cj.stage_block0 = blocks;
+                // One count k-iteration covers two sample blocks (the validity of block kb is
+                // in slot kb % 2 of iteration kb / 2): half the k-iterations, full stages.
+                cj.kblocks = (jt.jobs[k].kblocks + 1) / 2;
+                cj.plane_chan_bytes = int64_t(cj.kblocks) * 2 * cj.n_pad * kRowBytes;
                 count_of[size_t(k)] = idx;
                 shapes.push_back(shapes[size_t(k)]);
+                shapes.back().T = int64_t(cj.kblocks) * samples_per_stage(eb);
                 shapes.back().weight = g_opt.count_weight;
                 plane_off += size_t(cj.plane_chan_bytes) * size_t(cj.C);
             }
@@ -783,7 +788,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 auto it = d->tuned.find(shape_key(shapes, eb));
                 cfg = it != d->tuned.end() ? it->second : heuristic(shapes, eb, d->n_sm);
             }
-            // Count jobs run in the plain kernel only (its producer loads their re slots alone).
+            // Count jobs run in the plain kernel only (the cluster kernel splits the B planes
+            // of a stage between the pair and does not form their Re-only sums).
             if (cfg.sched == kSchedPairSplit && jt.n_jobs > ng) cfg.sched = kSchedSplit;
             if (cfg.sched == kSchedPairSplit) {
                 const int mc = tc_max_clusters();

@@ -355,9 +355,14 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
         }
         if (MASK && jb.count_planes) {
             // Validity plane of the count job: the same rows, chunks and swizzle as the re
-            // plane above, one e4m3 byte per sample (0x38 = 1.0 where valid, else 0).
-            uint8_t *cplane0 = jb.count_planes + int64_t(it.c) * jb.plane_chan_bytes +
-                               (int64_t(it.kb) * 2 * jb.n_pad + it.n0) * kRowBytes;
+            // plane above, one e4m3 byte per sample (0x38 = 1.0 where valid, else 0).  Sample
+            // block kb is plane kb of the count job, i.e. slot kb % 2 of its k-iteration kb / 2
+            // (a count k-iteration covers two sample blocks); with an odd number of blocks the
+            // last block also zeroes the unused slot after it.
+            const int64_t cchan = int64_t((jb.kblocks + 1) >> 1) * 2 * jb.n_pad * kRowBytes;
+            uint8_t *cplane0 = jb.count_planes + int64_t(it.c) * cchan +
+                               (int64_t(it.kb) * jb.n_pad + it.n0) * kRowBytes;
+            const bool zero_next = (jb.kblocks & 1) && it.kb == jb.kblocks - 1;
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const int row = 4 * g + i;
@@ -367,6 +372,8 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
                     wv[kk] = byte_mask_of_nibble((vbits[i] >> (4 * kk)) & 0xFu) & 0x38383838u;
                 uint8_t *pc = cplane0 + int64_t(row) * kRowBytes + ((q ^ ((row >> 1) & 3)) << 4);
                 *reinterpret_cast<uint4 *>(pc) = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+                if (zero_next)
+                    *reinterpret_cast<uint4 *>(pc + int64_t(jb.n_pad) * kRowBytes) = make_uint4(0u, 0u, 0u, 0u);
             }
         }
         __syncthreads();   // raw[b] is refilled by the next iteration's prefetch
@@ -548,29 +555,6 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 const JobDev &jb = jt.jobs[tl.job];
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
-                if (!MC && (jb.mode & kModeCount)) {
-                    // Count job (plain kernel only): the re plane slots alone.
-                    for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
-                        if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
-                            set_status(plan.status, kStatusTimeoutProducer);
-                            ok = false;
-                            break;
-                        }
-                        uint8_t *st = smem + stage * kStageBytes;
-                        const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
-                        mbar_arrive_expect_tx(&full[stage], kAPlane + bbytes);
-                        if (k + kPrefetchStages < sg.k_hi) {
-                            const uint8_t *fre = pre + int64_t(kPrefetchStages) * 2 * jb.n_pad * kRowBytes;
-                            bulk_prefetch_l2(fre + int64_t(tl.i0) * kRowBytes, kAPlane);
-                            bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
-                        }
-                        bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
-                        bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
-                        ++fills;
-                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-                    }
-                    continue;
-                }
                 for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
                     if (!mbar_wait(&empty[stage], ph ^ 1u, status)) {
                         set_status(plan.status, kStatusTimeoutProducer);
@@ -646,6 +630,8 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                     continue;
                 }
                 const Tile tl = plan.tiles[sg.tile];
+                // Count job (plain kernel only): its two slots hold the validity of two
+                // consecutive sample blocks, and only the Re accumulator is formed.
                 const bool re_only = !MC && (jt.jobs[tl.job].mode & kModeCount);
                 const uint32_t idesc = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, false);
                 const uint32_t idesc_neg = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, true);
@@ -656,7 +642,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 }
                 acc_ph ^= 1u;
                 tc_fence_after();
-                // The k-loop, compiled once per operand set: RO = count job (re slots only).
+                // The k-loop, compiled once per operand set: RO = count job.
                 auto mainloop = [&](auto ro_tag) {
                     constexpr bool RO = decltype(ro_tag)::value;
                     for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
@@ -676,8 +662,13 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                             const uint64_t b_im = sdesc_k_sw64(base + 2 * kAPlane + kBPlane + off);
                             const uint32_t acc = (k > sg.k_lo || s > 0) ? 1u : 0u;
                             if constexpr (RO) {
-                                if (EB == 1) mma_f8f6f4(d_re, a_re, b_re, idesc, acc);   // + F_I F_J^T
-                                else mma_f16(d_re, a_re, b_re, idesc, acc);
+                                if (EB == 1) {
+                                    mma_f8f6f4(d_re, a_re, b_re, idesc, acc);   // + F_I F_J^T, block 2k
+                                    mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);    // + block 2k + 1
+                                } else {
+                                    mma_f16(d_re, a_re, b_re, idesc, acc);
+                                    mma_f16(d_re, a_im, b_im, idesc, 1u);
+                                }
                             } else if (EB == 1) {
                                 mma_f8f6f4(d_re, a_re, b_re, idesc, acc);      // + A_I A_J^T
                                 mma_f8f6f4(d_re, a_im, b_im, idesc, 1u);       // + B_I B_J^T
