@@ -322,10 +322,11 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
             range_nib = left >= 4 ? 0xFu : left > 0 ? (1u << left) - 1u : 0u;
             use_flags = jb.flags != nullptr;
         }
+        const bool want_counts = MASK && jb.count_planes != nullptr;
         uint32_t re[4][4], im[4][4];
 #pragma unroll
         for (int kk = 0; kk < 4; ++kk) {
-            uint32_t w[4];
+            uint32_t w[4], mk[4];
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const int tl = q * 16 + kk * 4 + r;
@@ -333,11 +334,20 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
                 if (MASK) {
                     uint32_t nib = (int64_t(it.kb) * KS + tl < jb.T) ? range_nib : 0u;
                     if (use_flags) nib &= uint32_t(fl[b][raw_row(tl)][g >> 1]) >> ((g & 1) * 4);
-                    nib &= 0xFu;
-                    w[r] = (w[r] ^ key) & byte_mask_of_nibble(nib);
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) vbits[i] |= ((nib >> i) & 1u) << (kk * 4 + r);
+                    mk[r] = byte_mask_of_nibble(nib & 0xFu);    // byte i: input 4g + i valid
+                    w[r] = (w[r] ^ key) & mk[r];
                 }
+            }
+            if (want_counts) {
+                // The same 4x4 byte transpose as the samples below turns the four masks into
+                // one word per input (byte s: sample 4 kk + s); the multiply gathers the
+                // bytes' low bits into a nibble (bit s lands on bit 28 + s, no carries).
+                const uint32_t ma = __byte_perm(mk[0], mk[1], 0x5140), mb = __byte_perm(mk[2], mk[3], 0x5140);
+                const uint32_t mc = __byte_perm(mk[0], mk[1], 0x7362), md = __byte_perm(mk[2], mk[3], 0x7362);
+                const uint32_t vm[4] = {__byte_perm(ma, mb, 0x5410), __byte_perm(ma, mb, 0x7632),
+                                        __byte_perm(mc, md, 0x5410), __byte_perm(mc, md, 0x7632)};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) vbits[i] |= (((vm[i] & 0x01010101u) * 0x10204080u) >> 28) << (4 * kk);
             }
             const uint32_t a = __byte_perm(w[0], w[1], 0x5140), bb = __byte_perm(w[2], w[3], 0x5140);
             const uint32_t cc = __byte_perm(w[0], w[1], 0x7362), d = __byte_perm(w[2], w[3], 0x7362);
@@ -353,7 +363,7 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
             *reinterpret_cast<uint4 *>(pre) = make_uint4(re[i][0], re[i][1], re[i][2], re[i][3]);
             *reinterpret_cast<uint4 *>(pre + im_off) = make_uint4(im[i][0], im[i][1], im[i][2], im[i][3]);
         }
-        if (MASK && jb.count_planes) {
+        if (want_counts) {
             // Validity plane of the count job: the same rows, chunks and swizzle as the re
             // plane above, one e4m3 byte per sample (0x38 = 1.0 where valid, else 0).  Sample
             // block kb is plane kb of the count job, i.e. slot kb % 2 of its k-iteration kb / 2
