@@ -518,6 +518,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     uint64_t *drain = acc_empty + 1;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
     volatile int *epi_flag = reinterpret_cast<volatile int *>(tmem_slot + 1);
+    uint64_t *xfer = drain + 2;    // bulk copy of a partner's share into the idle stages
     int2 *epi_stage = reinterpret_cast<int2 *>(smem + kStages * kStageBytes + 256) + (threadIdx.x >> 5) * 32 * 33;
 
     const int warp = threadIdx.x >> 5;
@@ -532,6 +533,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
         mbar_init(drain, 1);
+        mbar_init(xfer, 1);
         fence_mbar_init();
     }
     if (warp == 5) {
@@ -709,7 +711,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         }
     } else {
         // ---------------- epilogue: TMEM -> int32 -> packed triangle ----------------
-        uint32_t acc_ph = 0;
+        uint32_t acc_ph = 0, xph = 0;
         const int r = warp * 32 + lane;
         const uint32_t lane_base = uint32_t(warp * 32) << 16;
         for (int q = q0; q < q1; ++q) {
@@ -777,15 +779,47 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 if (*epi_flag == 1) {
                     __threadfence();
                     const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + (1 - part)]) * kWsSlotElems;
+                    // On the CTA's last segment the operand stages are idle (its MMAs have
+                    // completed, the producer has nothing left to fetch): one pair of bulk
+                    // copies brings the partner's whole share (re and im, half x 128 int32
+                    // each) into them, so the chunks below read shared memory instead of
+                    // waiting on L2 loads chunk by chunk.
+                    const bool staged = q == q1 - 1;
+                    const int32_t *sh = reinterpret_cast<const int32_t *>(smem);
+                    if (staged) {
+                        const uint32_t bytes = uint32_t(half) * kBM * 4u;
+                        if (threadIdx.x == 0) {
+                            // The share was written through the generic proxy on another SM.
+                            asm volatile("fence.proxy.async.global;" ::: "memory");
+                            mbar_arrive_expect_tx(xfer, 2u * bytes);
+                            bulk_g2s(smem, w, bytes, xfer);
+                            bulk_g2s(smem + bytes, w + int64_t(kBN) * kBM, bytes, xfer);
+                        }
+                        // Bounded wait that does not stop on another CTA's error: the copies
+                        // must land before this CTA may exit.
+                        const long long t0 = clock64();
+                        bool got = false;
+                        while (!(got = mbar_try_wait(xfer, xph)) && clock64() - t0 < kWaitBudgetCycles) {}
+                        if (!got) set_status(plan.status, kStatusTimeoutEpilogue);
+                        xph ^= 1u;
+                    }
                     for (int cc = 0; cc < half; cc += 32) {
                         uint32_t fre[32], fim[32];
                         tmem_ld_32x32b_x32(tmem + lane_base + mine0 + cc, fre);
                         tmem_ld_32x32b_x32(tmem + lane_base + 256 + mine0 + cc, fim);
                         int re[32], im[32];
+                        if (staged) {
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            re[k] = __ldcg(w + int64_t(cc + k) * kBM + r);
-                            im[k] = __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
+                            for (int k = 0; k < 32; ++k) {
+                                re[k] = sh[(cc + k) * kBM + r];
+                                im[k] = sh[(half + cc + k) * kBM + r];
+                            }
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) {
+                                re[k] = __ldcg(w + int64_t(cc + k) * kBM + r);
+                                im[k] = __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
+                            }
                         }
                         tmem_ld_wait();
 #pragma unroll
