@@ -555,6 +555,10 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     if (warp == 4) {
         // ---------------- producer: bulk copies of plane tiles ----------------
         if (lane == 0) {
+            // The planes come from the staging kernel just before this one in the stream,
+            // which this grid may overlap (programmatic dependent launch): every read of
+            // them follows this wait.  Without the launch attribute it returns at once.
+            asm volatile("griddepcontrol.wait;" ::: "memory");
             int stage = 0;
             uint32_t ph = 0;
             int64_t fills = 0;
@@ -996,8 +1000,22 @@ cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, c
         if (elem_bytes == 1) tc_mc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
         else tc_mc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
     } else {
-        if (elem_bytes == 1) tc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
-        else tc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
+        // Programmatic dependent launch: the grid is set up while the staging kernel runs
+        // and its CTAs start on SMs as the staging blocks leave them; only the producer
+        // thread, which reads the planes, waits for the staging grid to complete.
+        cudaLaunchConfig_t cfg = {};
+        cfg.gridDim = dim3(unsigned(plan.n_cta));
+        cfg.blockDim = dim3(kTcThreads);
+        cfg.dynamicSmemBytes = size_t(kTcSmem);
+        cfg.stream = s;
+        cudaLaunchAttribute attr[1];
+        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+        attr[0].val.programmaticStreamSerializationAllowed = 1;
+        cfg.attrs = attr;
+        cfg.numAttrs = 1;
+        e = elem_bytes == 1 ? cudaLaunchKernelEx(&cfg, tc_kernel<1>, jt, plan)
+                            : cudaLaunchKernelEx(&cfg, tc_kernel<2>, jt, plan);
+        if (e != cudaSuccess) return e;
     }
     return cudaGetLastError();
 }
