@@ -229,6 +229,10 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
     auto fl = reinterpret_cast<uint8_t (*)[KS][kFlagRowBytes]>(stage_smem + kStageSmem);
     const int tid = threadIdx.x;
     const int64_t total = jt.total_stage_blocks;
+    // The correlation grid that follows may be set up now: its CTAs need more shared memory
+    // than an SM has beside even one staging block, so they only start on SMs this grid has
+    // left, and they wait for it to complete before reading the planes.
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
     auto vec_ok = [&](const JobDev &jb) { return view_vec_ok(jb); };
     // Flag rows can be copied 16 bytes at a time when every row starts 16-byte aligned.
