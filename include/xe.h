@@ -439,8 +439,9 @@ uint32_t xe_debug_operand_code(int v, int elem_bytes);
  * xe_set_timing(1).  Returns XE_OK or XE_EAGAIN if nothing was recorded. */
 int xe_set_timing(int enable);
 int xe_last_timing(float *stage_ms, float *correlate_ms);
-/* As xe_last_timing, plus the device time of the valid-sample count kernels of a masked
- * call (0 when the call computed no counts). */
+/* As xe_last_timing, plus the device time of work after the correlation kernel for the
+ * valid-sample counts of a masked call.  The count jobs run inside the correlation kernel
+ * and write the counts directly, so this is 0 (kept for callers that split the time). */
 int xe_last_timing_counts(float *stage_ms, float *correlate_ms, float *count_ms);
 
 #ifdef __cplusplus

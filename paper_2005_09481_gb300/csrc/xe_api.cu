@@ -400,8 +400,6 @@ struct Scratch {
     int *counters = nullptr;
     size_t counters_bytes = 0;
     int *status = nullptr;
-    int32_t *cvis = nullptr;      // outputs of the count jobs of masked calls ([C][B][2] each)
-    size_t cvis_bytes = 0;
     uint8_t *beam_wt = nullptr;   // beam weights as MMA operand tiles
     size_t beam_wt_bytes = 0;
     int32_t *corner_partial = nullptr;   // per-block pre-sums of the corner turn
@@ -432,13 +430,12 @@ struct HostStreams {
 constexpr int kHostSlots = XE_HOST_SLOTS + 1;   // the last one serves xe_correlate_host
 
 struct LaunchRec {
-    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor, 3 counts
+    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor
     int eb;
     bool clustered;               // kind 1: the 2-CTA clustered kernel
     bool masked;                  // kind 0: the masking variant of the staging kernel
     JobTable jt;
     PlanDev pd;
-    CountDev cd;                  // kind 3
 };
 
 struct GraphRec {
@@ -677,20 +674,6 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
     const int eb = g_opt.operand_bytes;
     if (g_job_mask && eb != 1) return fail(XE_EINVAL, "masked correlation needs 1-byte operands");
     const int64_t wt = g_opt.exact_chunk_t / samples_per_stage(eb) * samples_per_stage(eb);
-    // Outputs of the count jobs (masked jobs that ask for counts), one region per job.
-    std::vector<size_t> cvis_off(size_t(n_jobs), 0);
-    if (g_job_mask) {
-        size_t elems = 0;
-        for (int q = 0; q < n_jobs; ++q) {
-            cvis_off[size_t(q)] = elems;
-            if (g_job_mask[q].counts)
-                elems += size_t(jobs[q].n_chan) * size_t(jobs[q].N) * size_t(jobs[q].N + 1);
-        }
-        if (elems) {
-            int rc = grow(reinterpret_cast<void **>(&sc->cvis), &sc->cvis_bytes, elems * 4, false);
-            if (rc) return rc;
-        }
-    }
     // A masked group holds at most half the job slots: each job may add its count job.
     const size_t group = g_job_mask ? size_t(kMaxJobs / 2) : size_t(kMaxJobs);
     int64_t max_T = 0;
@@ -755,8 +738,10 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 cj.flags = nullptr;
                 cj.count_planes = nullptr;
                 cj.mode = kModeCount;
-                cj.accumulate = 0;
-                cj.vis = sc->cvis + cvis_off[size_t(q)];
+                // The epilogue writes (or adds) n_ij into the caller's counts directly.
+                cj.accumulate = g_job_mask[q].accumulate ? 1 : 0;
+                cj.vis = g_job_mask[q].counts;
+                cj.vis_chan_elems = int64_t(cj.N) * (cj.N + 1) / 2;
                 cj.stage_block0 = blocks;
                 // One count k-iteration covers two sample blocks (the validity of block kb is
                 // in slot kb % 2 of iteration kb / 2): half the k-iterations, full stages.
@@ -846,27 +831,12 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             }
         }
     }
-    if (g_job_mask) {
-        for (int q = 0; q < n_jobs; ++q) {
-            const xe_masked_job &mj = g_job_mask[q];
-            if (!mj.counts) continue;
-            LaunchRec cr{};
-            cr.kind = 3;
-            CountDev &cd = cr.cd;
-            cd.src = sc->cvis + cvis_off[size_t(q)];
-            cd.counts = mj.counts;
-            cd.n = int64_t(jobs[q].n_chan) * (int64_t(jobs[q].N) * (jobs[q].N + 1) / 2);
-            cd.accumulate = mj.accumulate ? 1 : 0;
-            out.push_back(cr);
-        }
-    }
     return XE_OK;
 }
 
 static cudaError_t enqueue(const LaunchRec &r, cudaStream_t s) {
     if (r.kind == 0) return launch_stage(r.jt, r.eb, s, r.masked);
     if (r.kind == 1) return launch_tc(r.jt, r.pd, r.eb, s, r.clustered);
-    if (r.kind == 3) return launch_counts(r.cd, s);
     return launch_imma(r.jt, s);
 }
 
@@ -1016,20 +986,17 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
         XE_CUDA(cudaGraphLaunch(g->exec, s));
         if (timing) XE_CUDA(cudaEventRecord(sc->ev[2], s));
     } else {
-        bool marked = false, counted = false;
+        bool marked = false;
         for (const LaunchRec &r : recs) {
             if (timing && !marked && r.kind != 0) {
                 XE_CUDA(cudaEventRecord(sc->ev[1], s));   // staging done (or none)
                 marked = true;
             }
-            if (timing && !counted && r.kind == 3) {
-                XE_CUDA(cudaEventRecord(sc->ev[2], s));   // correlation done, counts follow
-                counted = true;
-            }
             XE_CUDA(enqueue(r, s));
         }
         if (timing && !marked) XE_CUDA(cudaEventRecord(sc->ev[1], s));
-        if (timing && !counted) XE_CUDA(cudaEventRecord(sc->ev[2], s));
+        // Counts are written by the correlation kernel itself: nothing follows it.
+        if (timing) XE_CUDA(cudaEventRecord(sc->ev[2], s));
     }
     if (timing) {
         XE_CUDA(cudaEventRecord(sc->ev[3], s));

@@ -73,9 +73,12 @@ __host__ __device__ __forceinline__ int64_t view_offset(const JobDev &jb, int c,
 // each sample byte becomes (byte ^ key) & valid, where key = 0x88 for offset-binary input
 // (nibble u encodes u - 8; XOR with 8 gives the two's-complement nibble of the same value)
 // and valid = 0xFF if the sample's flag bit is set and it lies inside [0,T) x [0,N).
-// A count job correlates the 0/1 validity planes written by its masked job: only the re
-// plane slots are loaded and one MMA per K step accumulates F_I F_J^T (the Re output is the
-// valid-sample count n_ij; the Im output of a count job is meaningless and never read).
+// A count job correlates the 0/1 validity planes written by its masked job, n_ij =
+// sum_t f_i(t) f_j(t), the same contraction over real 0/1 operands (exact for the same
+// reason as the visibilities): each k-iteration holds two sample blocks in its re and im
+// slots, the MMAs accumulate F_I F_J^T of both into the Re accumulator, and the epilogue
+// writes that Re part, n_ij, straight into the caller's int32 [C][B] counts (the count
+// job's vis pointer; vis_chan_elems = B).  Its Im accumulator is never formed nor read.
 constexpr int kModeMasked = 1;
 constexpr int kModeOffsetBinary = 2;
 constexpr int kModeCount = 4;
@@ -85,15 +88,6 @@ struct JobTable {
     int accumulate;           // 1: add into vis instead of overwriting
     int64_t total_stage_blocks;
     JobDev jobs[kMaxJobs];
-};
-
-// Valid-sample counts of one masked job: counts[e] (+)= src[2e], e < n (the Re part of its
-// count job's output).
-struct CountDev {
-    const int32_t *src;       // count job output [C][B][2]
-    int32_t *counts;          // [C][B]
-    int64_t n;                // C * B
-    int accumulate;           // 1: counts += n_ij
 };
 
 // One output tile of the triangle: rows [i0, i0+128), columns [j0, j0+nj).
@@ -192,10 +186,9 @@ cudaError_t launch_corner_turn(const uint8_t *bundles, int n_cyl, int n_freq, in
                                uint8_t *frames, int32_t *partial, int32_t *presums, cudaStream_t s);
 int64_t corner_partial_elems(int n_cyl, int n_freq, int n_in, int64_t T);
 
-// Kernel launchers (xe_tc.cu, xe_imma.cu, xe_mask.cu).  `masked` selects the masking
+// Kernel launchers (xe_tc.cu, xe_imma.cu).  `masked` selects the masking
 // variant of the e4m3 staging kernel (any job with kModeMasked).
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s, bool masked = false);
-cudaError_t launch_counts(const CountDev &cd, cudaStream_t s);
 cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
                       bool clustered = false);
 int tc_max_clusters();

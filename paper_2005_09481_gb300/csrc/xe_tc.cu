@@ -461,6 +461,8 @@ __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(st
 // i0 + lane, register k = column jbase + k).  The block is transposed through the warp's
 // shared buffer so that each global access covers 32 consecutive baselines of one row
 // (256 contiguous bytes); in accumulate mode all 32 row loads are issued before any add.
+// A count job (kModeCount) writes only the Re part, n_ij, into its int32 [C][B] counts (its
+// vis pointer and vis_chan_elems = B), 128 contiguous bytes per row.
 __device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, int jbase,
                                             const int (&re)[32], const int (&im)[32], int acc,
                                             int2 *stage) {
@@ -471,7 +473,29 @@ __device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, 
     const int64_t N = jb.N;
     int32_t *vis = jb.vis + int64_t(chan) * jb.vis_chan_elems;
     const int j = jbase + lane;
-    if (acc) {
+    if (jb.mode & kModeCount) {
+        // Counts: element k of the row-major upper triangle, Re part only.
+        int old[32];
+        if (acc) {
+#pragma unroll
+            for (int r = 0; r < 32; ++r) {
+                const int i = i0 + r;
+                old[r] = 0;
+                if (i < jb.N && j >= i && j < jb.N) {
+                    const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
+                    old[r] = __ldcg(vis + k);
+                }
+            }
+        }
+#pragma unroll 8
+        for (int r = 0; r < 32; ++r) {
+            const int i = i0 + r;
+            if (i < jb.N && j >= i && j < jb.N) {
+                const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
+                vis[k] = (acc ? old[r] : 0) + stage[r * 33 + lane].x;
+            }
+        }
+    } else if (acc) {
         int2 old[32];
 #pragma unroll
         for (int r = 0; r < 32; ++r) {
