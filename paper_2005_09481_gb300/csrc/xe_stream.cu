@@ -15,6 +15,7 @@
 // Admission is by HBM budget: a channel is admitted only if its accumulators, frame ring and
 // share of staging memory fit the stream's budget.  Lost frames (sequence gaps) are counted
 // and mark their integration incomplete; nothing shifts integration boundaries.
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -341,7 +342,22 @@ bool pass(xe_stream *s) {
     int n_groups = 0;
     for (size_t gi = 0; gi < groups.size(); ++gi)
         if (!groups[gi].empty() && rc == XE_OK) {
-            rc = run_jobs_mixed(groups[gi].data(), group_acc[gi].data(), int(groups[gi].size()), s->comp_s);
+            // The jobs of a group are independent (different channels): listing them by
+            // length (longest first, then channel order) makes the batch shape depend only
+            // on how many jobs merged how many frames, so passes reuse cached plans instead
+            // of planning every new arrangement of the same jobs.
+            std::vector<size_t> order(groups[gi].size());
+            for (size_t k = 0; k < order.size(); ++k) order[k] = k;
+            std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) {
+                return groups[gi][a].T > groups[gi][b].T;
+            });
+            std::vector<xe_job> jobs_sorted(order.size());
+            std::vector<int> acc_sorted(order.size());
+            for (size_t k = 0; k < order.size(); ++k) {
+                jobs_sorted[k] = groups[gi][order[k]];
+                acc_sorted[k] = group_acc[gi][order[k]];
+            }
+            rc = run_jobs_mixed(jobs_sorted.data(), acc_sorted.data(), int(jobs_sorted.size()), s->comp_s);
             ++n_groups;
         }
     const int64_t t_l1 = now_ns();
