@@ -17,7 +17,8 @@ constexpr int kNPad = 256;         // inputs are padded to a multiple of this (z
 constexpr int kAPlane = kBM * kRowBytes;              // 8 KB
 constexpr int kBPlane = kBN * kRowBytes;              // 16 KB
 constexpr int kStageBytes = 2 * kAPlane + 2 * kBPlane;  // 48 KB
-constexpr int kTcThreads = 192;    // 4 epilogue warps, 1 producer warp, 1 MMA warp
+constexpr int kTcThreads = 256;    // 4 epilogue warps, 1 producer warp, 1 MMA warp, 2 warps that
+                                   // join the eight-warp pair-exchange epilogue
 constexpr int kEpiStageBytes = 4 * 32 * 33 * 8;  // per epilogue warp: 32 x 33 int2 transpose buffer
 constexpr int kTcSmem = kStages * kStageBytes + kEpiStageBytes + 1024 /*align*/ + 256 /*barriers*/;
 constexpr int kMaxJobs = 208;      // jobs per launch (passed by value, within the 32 KB limit)

@@ -578,6 +578,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     // This CTA's work: segments [q0, q1) of the plan, each a k-range of one tile.
     const int q0 = plan.seg_off[blockIdx.x];
     const int q1 = plan.seg_off[blockIdx.x + 1];
+    // A CTA whose only segment is one part of a pair-exchanged tile finishes it with eight
+    // warps: the producer and MMA warps are idle by then, and two more warps wait for it.
+    const bool wide = !MC && plan.pair_exchange && q1 - q0 == 1 && plan.segs[q0].slot >= 0;
     constexpr uint32_t kFmt = 0;  // E4M3 for kind::f8f6f4, F16 for kind::f16
 
     if (warp == 4) {
@@ -741,7 +744,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 while (!mbar_try_wait(drain, 0) && clock64() - t0 < kWaitBudgetCycles) {}
             }
         }
-    } else {
+    } else if (warp < 4 && !wide) {
         // ---------------- epilogue: TMEM -> int32 -> packed triangle ----------------
         uint32_t acc_ph = 0, xph = 0;
         const int r = warp * 32 + lane;
@@ -922,6 +925,104 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
             }
             tc_fence_before();
             mbar_arrive(acc_empty);
+        }
+    }
+
+    if (wide) {
+        // ---------------- eight-warp pair-exchange epilogue (see `wide`) ----------------
+        // Warp w serves tensor-memory lane quarter w % 4 (rows 32 (w % 4) ..) and column share
+        // w / 4 of each half; the eight warps meet on named barrier 2 only, every thread
+        // taking the same barriers (the conditions are flags read after a barrier).  Same
+        // steps as the four-warp pair exchange below the role split.
+        auto wbar = []() { asm volatile("bar.sync 2, 256;" ::: "memory"); };
+        const Seg sg = plan.segs[q0];
+        const Tile tl = plan.tiles[sg.tile];
+        const JobDev &jb = jt.jobs[tl.job];
+        const int quarter = warp & 3, share = warp >> 2;
+        const int r = quarter * 32 + lane;
+        const uint32_t lane_base = uint32_t(quarter * 32) << 16;
+        if (threadIdx.x == 0) {
+            const bool ok = mbar_wait(acc_full, 0, status);
+            if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
+            *epi_flag = ok ? 1 : 0;
+        }
+        wbar();
+        if (*epi_flag == 1) {
+            tc_fence_after();
+            const int part = sg.k_lo == 0 ? 0 : 1;
+            const int half = tl.nj / 2, cols = half / 2;
+            const int mine0 = part * half, theirs0 = (1 - part) * half;
+            const int c_lo = share * cols, c_hi = c_lo + cols;
+            int32_t *ws = plan.ws + int64_t(sg.slot) * kWsSlotElems;
+            for (int cc = c_lo; cc < c_hi; cc += 32) {
+                uint32_t fre[32], fim[32];
+                tmem_ld_32x32b_x32(tmem + lane_base + theirs0 + cc, fre);
+                tmem_ld_32x32b_x32(tmem + lane_base + 256 + theirs0 + cc, fim);
+                tmem_ld_wait();
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    __stcg(ws + int64_t(cc + k) * kBM + r, __float2int_rn(__uint_as_float(fre[k])));
+                    __stcg(ws + int64_t(kBN + cc + k) * kBM + r, __float2int_rn(__uint_as_float(fim[k])));
+                }
+            }
+            __threadfence();
+            wbar();
+            if (threadIdx.x == 0) {
+                atomicAdd(&plan.counters[sg.tile], 1);
+                volatile int *cnt = plan.counters + sg.tile;
+                const long long t0 = clock64();
+                bool ok = true;
+                while (*cnt < 2) {
+                    if (*status != 0 || clock64() - t0 > kWaitBudgetCycles) { ok = false; break; }
+                }
+                if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
+                *epi_flag = ok ? 1 : 0;
+            }
+            wbar();
+            if (*epi_flag == 1) {
+                __threadfence();
+                const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + (1 - part)]) * kWsSlotElems;
+                // The partner's share (re and im, half x 128 int32 each) goes into the idle
+                // operand stages in one pair of bulk copies; warps 4..7 take their transpose
+                // buffers from the stages after it.
+                const uint32_t bytes = uint32_t(half) * kBM * 4u;
+                if (threadIdx.x == 0) {
+                    asm volatile("fence.proxy.async.global;" ::: "memory");
+                    mbar_arrive_expect_tx(xfer, 2u * bytes);
+                    bulk_g2s(smem, w, bytes, xfer);
+                    bulk_g2s(smem + bytes, w + int64_t(kBN) * kBM, bytes, xfer);
+                }
+                const long long t0 = clock64();
+                bool got = false;
+                while (!(got = mbar_try_wait(xfer, 0)) && clock64() - t0 < kWaitBudgetCycles) {}
+                if (!got) set_status(plan.status, kStatusTimeoutEpilogue);
+                const int32_t *sh = reinterpret_cast<const int32_t *>(smem);
+                int2 *buf = share == 0 ? epi_stage
+                                       : reinterpret_cast<int2 *>(smem + 2 * bytes) + (warp - 4) * 32 * 33;
+                for (int cc = c_lo; cc < c_hi; cc += 32) {
+                    uint32_t fre[32], fim[32];
+                    tmem_ld_32x32b_x32(tmem + lane_base + mine0 + cc, fre);
+                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + mine0 + cc, fim);
+                    int re[32], im[32];
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        re[k] = sh[(cc + k) * kBM + r];
+                        im[k] = sh[(half + cc + k) * kBM + r];
+                    }
+                    tmem_ld_wait();
+#pragma unroll
+                    for (int k = 0; k < 32; ++k) {
+                        re[k] += __float2int_rn(__uint_as_float(fre[k]));
+                        im[k] += __float2int_rn(__uint_as_float(fim[k]));
+                    }
+                    store_block(jb, tl.chan, tl.i0 + quarter * 32, tl.j0 + mine0 + cc, re, im,
+                                jt.accumulate | jb.accumulate, buf);
+                }
+                wbar();
+                // Both parts have read each other's share: the second to finish resets the
+                // counter for the next launch.
+                if (threadIdx.x == 0 && atomicAdd(&plan.counters[sg.tile], 1) == 3) plan.counters[sg.tile] = 0;
+            }
         }
     }
 
