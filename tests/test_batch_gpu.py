@@ -83,7 +83,7 @@ def test_autotune_picks_a_plan_and_stays_exact(xe):
     xe.set_option("autotune", 1)
     got = run_batch(xe, shapes, dev)
     n_cta, tile_n, sched = xe.last_config()
-    assert tile_n in (128, 256) and 0 <= sched <= 4 and n_cta > 0
+    assert tile_n in (128, 256) and 0 <= sched <= 5 and n_cta > 0   # schedules 0..5 (xe_plan_dump)
     np.testing.assert_array_equal(got[0], oracle.correlate_dense(host[0], 640, 4096, 3))
 
 
