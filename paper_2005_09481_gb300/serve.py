@@ -9,6 +9,7 @@ correlation itself runs in the CUDA library; this module only paces and measures
 """
 from __future__ import annotations
 
+import gc
 import threading
 import time
 
@@ -30,7 +31,24 @@ def run_realtime(n_chan: int, seconds: float, N: int = 2048, frame_T: int = 8192
                  integ_T: int = 32768, rate: float = CHIME_RATE, device_source: bool = True,
                  ring_frames: int = 8, hbm_budget: int | None = None, n_distinct: int = 8,
                  seed: int = 20050948) -> dict:
-    """Stream n_chan channels in real time for `seconds`; return throughput and latency."""
+    """Stream n_chan channels in real time for `seconds`; return throughput and latency.
+
+    The producer and consumer are Python threads: the garbage collector is run first and kept
+    off while they pace the frames (a collection pause in the producer would count as a late
+    frame of the server's run)."""
+    gc.collect()
+    gc_was_enabled = gc.isenabled()
+    gc.disable()
+    try:
+        return _run_realtime(n_chan, seconds, N, frame_T, integ_T, rate, device_source, ring_frames,
+                             hbm_budget, n_distinct, seed)
+    finally:
+        if gc_was_enabled:
+            gc.enable()
+
+
+def _run_realtime(n_chan, seconds, N, frame_T, integ_T, rate, device_source, ring_frames, hbm_budget,
+                  n_distinct, seed):
     import torch
     budget = hbm_budget if hbm_budget is not None else (n_chan + 1) * per_channel_bytes(N, frame_T, ring_frames)
     frame_period = frame_T / rate
