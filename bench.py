@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import hashlib
+import re
 import json
 import os
 import statistics
@@ -50,11 +51,25 @@ def peaks():
         return 1900.0, 6800.0, "fallback"
 
 
-def kernel_hash():
+def code_of(text):
+    """Source text without comments and whitespace (a comment edit leaves the kernel as it
+    was profiled)."""
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return "".join(text.split())
+
+
+def kernel_hash(texts=None):
+    """Hash of the code of the correlation kernel's sources (xe_tc.cu, xe_ptx.cuh,
+    xe_internal.h), comments and whitespace excluded."""
     h = hashlib.sha256()
     for name in ("xe_tc.cu", "xe_ptx.cuh", "xe_internal.h"):
-        with open(os.path.join(ROOT, "paper_2005_09481_gb300", "csrc", name), "rb") as f:
-            h.update(f.read())
+        if texts is None:
+            with open(os.path.join(ROOT, "paper_2005_09481_gb300", "csrc", name), encoding="utf-8") as f:
+                text = f.read()
+        else:
+            text = texts[name]
+        h.update(code_of(text).encode())
     return h.hexdigest()[:16]
 
 

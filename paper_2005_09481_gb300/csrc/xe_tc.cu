@@ -932,8 +932,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         // ---------------- eight-warp pair-exchange epilogue (see `wide`) ----------------
         // Warp w serves tensor-memory lane quarter w % 4 (rows 32 (w % 4) ..) and column share
         // w / 4 of each half; the eight warps meet on named barrier 2 only, every thread
-        // taking the same barriers (the conditions are flags read after a barrier).  Same
-        // steps as the four-warp pair exchange below the role split.
+        // taking the same barriers (the conditions are flags read after a barrier).  The
+        // steps are those of the four-warp pair exchange in the epilogue role above, with
+        // the partner's share always staged through the idle operand stages.
         auto wbar = []() { asm volatile("bar.sync 2, 256;" ::: "memory"); };
         const Seg sg = plan.segs[q0];
         const Tile tl = plan.tiles[sg.tile];
