@@ -181,20 +181,24 @@ __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commi
 __device__ __forceinline__ void cp_async_wait2() { asm volatile("cp.async.wait_group 2;" ::: "memory"); }
 
 struct StageItem {
-    const JobDev *jb;
+    int job;                  // index into the job table (read from the kernel parameters at
+                              // each use, never through a pointer kept in a register)
     int c, kb, n0;
 };
 
+// Decode item blk (32-bit arithmetic: the host keeps every staging grid below 2^31 items).
 __device__ __forceinline__ StageItem stage_item(const JobTable &jt, int64_t blk) {
-    const JobDev &jb = jt.jobs[find_job(jt, blk)];
-    const int64_t local = blk - jb.stage_block0;
-    const int nblk = jb.n_pad / 256;
+    const int job = find_job(jt, blk);
+    const JobDev &jb = jt.jobs[job];
+    const uint32_t local = uint32_t(blk - jb.stage_block0);
+    const uint32_t nblk = uint32_t(jb.n_pad) / 256u;
     StageItem it;
-    it.jb = &jb;
-    it.n0 = int(local % nblk) * 256;
-    const int64_t rest = local / nblk;
-    it.kb = int(rest % jb.kblocks);
-    it.c = int(rest / jb.kblocks);
+    it.job = job;
+    const uint32_t rest = local / nblk;
+    it.n0 = int(local - rest * nblk) * 256;
+    const uint32_t c = rest / uint32_t(jb.kblocks);
+    it.kb = int(rest - c * uint32_t(jb.kblocks));
+    it.c = int(c);
     return it;
 }
 
@@ -240,10 +244,10 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
         const int64_t frow = (jb.N + 7) / 8;
         return (frow & 15) == 0 && (reinterpret_cast<uintptr_t>(jb.flags) & 15) == 0;
     };
-    // Issue the loads of one item into buffer b (vector path: N % 16 == 0, aligned input).
-    auto issue = [&](int64_t blk, int b) {
-        const StageItem it = stage_item(jt, blk);
-        const JobDev &jb = *it.jb;
+    // Issue the loads of one (decoded) item into buffer b (vector path: N % 16 == 0, aligned
+    // input).
+    auto issue = [&](const StageItem &it, int b) {
+        const JobDev &jb = jt.jobs[it.job];
         const int seg = tid & 15;
         const int n = it.n0 + seg * 16;
         // Inputs n..n+15 lie in one segment: one base per item row, rows s_t apart.
@@ -272,19 +276,29 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
     };
 
     // Three buffers: the tiles of the next two items are in flight while one is converted.
+    // Each item is decoded once, when its loads are issued, and carried to its conversion
+    // (it0: the item converted now, it1 and it2: the two behind it).
     int b = 0;
     int64_t blk = blockIdx.x;
-    for (int a = 0; a < 2; ++a) {
-        const int64_t pre = blk + int64_t(a) * gridDim.x;
-        if (pre < total && vec_ok(*stage_item(jt, pre).jb)) issue(pre, a);
-        cp_async_commit();
-    }
+    StageItem it0{}, it1{};
+    if (blk < total) it0 = stage_item(jt, blk);
+    if (blk + gridDim.x < total) it1 = stage_item(jt, blk + gridDim.x);
+    if (blk < total && vec_ok(jt.jobs[it0.job])) issue(it0, 0);
+    cp_async_commit();
+    if (blk + gridDim.x < total && vec_ok(jt.jobs[it1.job])) issue(it1, 1);
+    cp_async_commit();
     for (; blk < total; blk += gridDim.x) {
-        const StageItem it = stage_item(jt, blk);
-        const JobDev &jb = *it.jb;
+        const StageItem it = it0;
+        const JobDev &jb = jt.jobs[it.job];
         const int64_t next = blk + 2 * int64_t(gridDim.x);
-        if (next < total && vec_ok(*stage_item(jt, next).jb)) issue(next, b == 0 ? 2 : b - 1);
+        StageItem it2{};
+        if (next < total) {
+            it2 = stage_item(jt, next);
+            if (vec_ok(jt.jobs[it2.job])) issue(it2, b == 0 ? 2 : b - 1);
+        }
         cp_async_commit();
+        it0 = it1;
+        it1 = it2;
         if (!vec_ok(jb)) {
             // Scalar path (unaligned rows or segments, or an unaligned input): byte loads.
             const int n = it.n0 + tid;
