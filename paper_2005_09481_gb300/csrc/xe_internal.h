@@ -187,7 +187,7 @@ cudaError_t launch_corner_turn(const uint8_t *bundles, int n_cyl, int n_freq, in
                                uint8_t *frames, int32_t *partial, int32_t *presums, cudaStream_t s);
 int64_t corner_partial_elems(int n_cyl, int n_freq, int n_in, int64_t T);
 
-// Kernel launchers (xe_tc.cu, xe_imma.cu).  `masked` selects the masking
+// Kernel launchers (xe_stage.cu, xe_tc.cu, xe_imma.cu).  `masked` selects the masking
 // variant of the e4m3 staging kernel (any job with kModeMasked).
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s, bool masked = false);
 cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
