@@ -754,6 +754,9 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 plane_off += size_t(cj.plane_chan_bytes) * size_t(cj.C);
             }
             jt.total_stage_blocks = blocks;
+            // The staging kernel decodes its items in 32-bit arithmetic.  (Unreachable in
+            // practice: 2^31 items would stage 64 TB of planes.)
+            if (blocks > 0x7fffffffLL) return fail(XE_EINVAL, "batch too large for one staging grid");
             // Plane offsets within the scratch; the base is bound once every group is known
             // (the scratch is sized for the largest group: growing it per group would free
             // the buffer earlier groups' records already point into).

@@ -32,6 +32,15 @@ def test_header_declares_the_boundary():
         assert required in names
 
 
+def test_binding_constants_match_the_header():
+    src = open(os.path.join(ROOT, "include", "xe.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define\s+(XE_\w+)\s+(-?\d+)(?:LL)?\b", src)}
+    for name in ("XE_OK", "XE_EINVAL", "XE_EOVERFLOW", "XE_ENOMEM", "XE_EBUDGET", "XE_EAGAIN",
+                 "XE_ETIMEOUT", "XE_ECUDA", "XE_ENODEV", "XE_ECLOSED", "XE_MAX_T", "XE_MAX_N"):
+        assert getattr(xe, name) == defs[name], name
+    assert 128 * xe.XE_MAX_T < 2**31 <= 128 * (xe.XE_MAX_T + 1)
+
+
 def test_every_declared_symbol_is_exported():
     L = xe.load()
     missing = [n for n in _declared() if not hasattr(L, n)]

@@ -180,6 +180,32 @@ def test_full_size_masked(xe):
     check(xe, synth.to_offset_binary(p), f, N, T, 1, enc=1, dense=True)
 
 
+def test_maximum_integration_length(xe):
+    # T = XE_MAX_T = 2^24 - 1 samples of extreme offset-binary values (even inputs -8-8i,
+    # odd inputs -8+7i), inputs 3 and 12 flagged throughout: Re V reaches 128 T = 2^31 - 128,
+    # Im V +-120 T, and the valid-sample counts T.  The samples and flags do not change with t,
+    # so by linearity in time V = T * V(one sample) and n = T * n(one sample), both from the
+    # oracle.
+    N, T = 17, xe.XE_MAX_T
+    row = np.where(np.arange(N) % 2 == 0, synth.pack(-8, -8), synth.pack(-8, 7)).astype(np.uint8)
+    row = synth.to_offset_binary(row[None, None, :])
+    valid = np.ones(N, bool)
+    valid[[3, 12]] = False
+    frow = np.packbits(np.concatenate([valid, np.zeros(7, bool)])[:24].reshape(3, 8)[:, ::-1], axis=1)
+    frow = frow.reshape(1, 1, 3)
+    assert [(frow[0, 0, n // 8] >> (n % 8)) & 1 for n in range(N)] == valid.astype(int).tolist()
+    want = oracle.correlate_masked(row, frow, N, 1, 1, encoding=1).astype(np.int64) * T
+    want_n = oracle.flag_counts(frow, N, 1, 1) * T
+    assert want.max() == 128 * T and want[..., 1].min() == -120 * T and want_n.max() == T
+    x = dev(row[0, 0]).expand(T, N).contiguous()[None]
+    f = dev(frow[0, 0]).expand(T, 3).contiguous()[None]
+    vis, cnt = xe.correlate_masked(x, f, N, T, 1, encoding="offset")
+    torch.cuda.synchronize()
+    xe.device_status()
+    assert np.array_equal(vis.cpu().numpy().astype(np.int64), want)
+    assert np.array_equal(cnt.cpu().numpy().astype(np.int64), want_n)
+
+
 def test_plain_path_unchanged_after_masked(xe):
     N, T = 1024, 4096
     p = synth.uniform(N, T, 1, seed=77)

@@ -120,6 +120,30 @@ def test_extreme_magnitudes_across_windows(xe):
     assert (got[0, :, 0] == 98 * 65536).all() and (got[0, :, 1] == 0).all()
 
 
+@pytest.mark.parametrize("algo", ALGOS)
+def test_maximum_integration_length(xe, algo):
+    # T = XE_MAX_T = 2^24 - 1 samples (128 windows of the f32 accumulator) of the extreme
+    # values: even inputs hold -8-8i and odd inputs -8+7i, so Re V reaches 128 T = 2^31 - 128
+    # and Im V reaches +120 T (even i < odd j) and -120 T (odd i < even j).  The samples do not change with t, so by linearity
+    # in time V = T * V(one sample), the one-sample visibilities from the oracle.
+    N, T = 17, xe.XE_MAX_T
+    row = np.where(np.arange(N) % 2 == 0, synth.pack(-8, -8), synth.pack(-8, 7)).astype(np.uint8)
+    one = oracle.correlate(row[None, None, :], N, 1, 1).astype(np.int64)
+    want = one * T
+    assert want.max() == 128 * T and want[..., 1].max() == 120 * T and want[..., 1].min() == -120 * T
+    assert want.max() < 2**31 and want.min() >= -2**31
+    dev = torch.from_numpy(row).cuda().expand(T, N).contiguous()[None]
+    got = xe.correlate(dev, N, T, 1, algo=algo)
+    torch.cuda.synchronize()
+    xe.device_status()
+    assert_exact(got.cpu().numpy().astype(np.int64), want, f"T=XE_MAX_T {algo}")
+    del dev
+    dev = torch.zeros((1, T + 1, N), dtype=torch.uint8, device="cuda")
+    with pytest.raises(xe.XeError) as e:
+        xe.correlate(dev, N, T + 1, 1, algo=algo)
+    assert e.value.code == xe.XE_EOVERFLOW
+
+
 def test_fp8_accumulation_adversaries(xe):
     # Patterns aimed at any precision loss of the f32 tensor-memory accumulator:
     # a large partial sum followed by +-1 terms, alternating +-7 cancellations, and
