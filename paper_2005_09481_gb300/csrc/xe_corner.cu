@@ -24,6 +24,7 @@
 namespace xe {
 
 constexpr int kCornerTBlock = 256;   // samples per block
+constexpr int kCornerRows = 8;       // sample rows per copy iteration
 
 struct CornerDev {
     const uint8_t *bundles;
@@ -74,23 +75,25 @@ __global__ void __launch_bounds__(256) corner_turn_kernel(const __grid_constant_
                 a[2] += im & 0x00FF00FFu;
                 a[3] += (im >> 8) & 0x00FF00FFu;
             };
-            for (; t + 4 <= t_hi; t += 4) {
-                uint4 v[4];
+            // kCornerRows rows per iteration: 16 * kCornerRows bytes of loads in flight per
+            // thread (the blocks have 128 threads at CHIME's 4 x 512 bundle rows).
+            for (; t + kCornerRows <= t_hi; t += kCornerRows) {
+                uint4 v[kCornerRows];
 #pragma unroll
-                for (int r = 0; r < 4; ++r) v[r] = __ldcs(reinterpret_cast<const uint4 *>(src + r * in_row));
+                for (int r = 0; r < kCornerRows; ++r) v[r] = __ldcs(reinterpret_cast<const uint4 *>(src + r * in_row));
 #pragma unroll
-                for (int r = 0; r < 4; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * int64_t(N)), v[r]);
+                for (int r = 0; r < kCornerRows; ++r) __stcs(reinterpret_cast<uint4 *>(dst + r * int64_t(N)), v[r]);
                 if (sums) {
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
+                    for (int r = 0; r < kCornerRows; ++r) {
                         add_word(v[r].x, acc[0]);
                         add_word(v[r].y, acc[1]);
                         add_word(v[r].z, acc[2]);
                         add_word(v[r].w, acc[3]);
                     }
                 }
-                src += 4 * in_row;
-                dst += 4 * int64_t(N);
+                src += kCornerRows * in_row;
+                dst += kCornerRows * int64_t(N);
             }
             for (; t < t_hi; ++t) {
                 const uint4 v = __ldcs(reinterpret_cast<const uint4 *>(src));
