@@ -146,6 +146,7 @@ def cpu_oracle_rate(packed_chan, N, budget_s=12.0):
     import numpy as np
     import oracle
     oracle.build()
+    oracle.set_threads(len(os.sched_getaffinity(0)))
     T_s, el = 16, 0.0
     while True:
         sample = np.ascontiguousarray(packed_chan[:T_s])
@@ -175,6 +176,9 @@ def run_reference(args):
     if rank != 0:
         return 0
     oracle.build()
+    # The other ranks do no work: rank 0 takes every host core it may run on (a multi-process
+    # launcher sets OMP_NUM_THREADS=1 for each process).
+    oracle.set_threads(len(os.sched_getaffinity(0)))
     packed = synth.gauss_plane(N_IN, T_SAMPLES, 1)[0]
     T_s = 64
     sample = np.ascontiguousarray(packed[:T_s])

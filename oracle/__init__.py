@@ -81,6 +81,8 @@ def _load():
             lib.xe_oracle_cmac.argtypes = [i64, i64, i64]
             lib.xe_oracle_cmac.restype = ctypes.c_double
             lib.xe_oracle_threads.restype = ctypes.c_int
+            lib.xe_oracle_set_threads.argtypes = [ctypes.c_int]
+            lib.xe_oracle_set_threads.restype = ctypes.c_int
             lib.xe_oracle_correlate_masked.argtypes = [p, p, i64, i64, i64, ctypes.c_int, p]
             lib.xe_oracle_correlate_masked.restype = ctypes.c_int
             lib.xe_oracle_flag_counts.argtypes = [p, i64, i64, i64, p]
@@ -123,6 +125,11 @@ def cmac(N: int, T: int, C: int = 1) -> float:
 
 def threads() -> int:
     return int(_load().xe_oracle_threads())
+
+
+def set_threads(n: int) -> int:
+    """Threads of the OpenMP loops (timing harnesses only); returns the count in force."""
+    return int(_load().xe_oracle_set_threads(int(n)))
 
 
 def _check_in(packed: np.ndarray, N: int, T: int, C: int) -> np.ndarray:

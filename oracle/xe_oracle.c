@@ -300,3 +300,16 @@ int xe_oracle_threads(void)
     return 1;
 #endif
 }
+
+/* Set the threads of the OpenMP loops (n >= 1); returns the count now in force.  Used by a
+ * timing harness whose launcher pinned OMP_NUM_THREADS to 1 for every process. */
+int xe_oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return xe_oracle_threads();
+}

@@ -71,3 +71,24 @@ def test_two_rank_gloo_sharded_correlation():
         assert p.exitcode == 0
     assert ok
     assert slow == 1.5
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_zero():
+    # The oracle arm launched like the driver's N > 1 runs: rank 0 alone times the oracle on
+    # every host core it may use (the launcher sets OMP_NUM_THREADS=1) and prints one JSON
+    # line; the other rank exits 0 without work.
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(_free_port()), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--steps", "3", "--warmup", "3"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=300)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["cores"] == len(os.sched_getaffinity(0))
+    assert d["e2e"]["h2d_bytes_per_step"] == 0
