@@ -701,25 +701,29 @@ def main():
     # cores busy (its producer is paced on the host).
     stream = None
     if ws == 1 and not args.no_stream:
-        # The largest sustained channel count: start at --stream-channels, step down by 32
-        # while a run is not sustained (real-time pace, no overruns or drops), then try one
-        # step up.  The producer is paced on the host, so a count gets a second run before
-        # stepping down (one late host wake-up can fail an otherwise sustained run); the
-        # step up comes last because an overloaded run leaves the plan cache full of batch
-        # shapes that later runs would rebuild.
+        # The largest sustained channel count (real-time pace, no overruns or drops), found
+        # the way channels come on line: start at --stream-channels - 64 and add 32 while
+        # the runs are sustained; the last sustained run is reported.  The producer is paced
+        # on the host, so a count gets a second run before it counts as failed (one late
+        # host wake-up can fail an otherwise sustained run).  A start that is not sustained
+        # steps down by 32 instead.
         from paper_2005_09481_gb300 import serve
-        c = args.stream_channels
-        while True:
-            stream = serve.run_realtime(c, args.stream_seconds)
-            if not stream["sustained"]:
-                stream = serve.run_realtime(c, args.stream_seconds)
-            if stream["sustained"] or c <= 64:
-                break
+
+        def sustained_run(n):
+            r = serve.run_realtime(n, args.stream_seconds)
+            return r if r["sustained"] else serve.run_realtime(n, args.stream_seconds)
+
+        c = max(32, args.stream_channels - 64)
+        stream = sustained_run(c)
+        while not stream["sustained"] and c > 64:
             c -= 32
-        if stream["sustained"]:
-            up = serve.run_realtime(c + 32, args.stream_seconds)
-            if up["sustained"]:
-                stream = up
+            stream = sustained_run(c)
+        while stream["sustained"] and c < 1024:
+            up = sustained_run(c + 32)
+            if not up["sustained"]:
+                break
+            c += 32
+            stream = up
 
     masked = None
     if ws == 1 and not args.no_masked:

@@ -490,7 +490,7 @@ static std::vector<int64_t> shape_key(const std::vector<JobShape> &jobs, int eb)
     return key;
 }
 
-constexpr size_t kMaxCachedPlans = 1024;
+constexpr size_t kMaxCachedPlans = 4096;   // a plan blob holds a few KB to ~100 KB
 
 // Bounded plan cache: a stream of ever-new batch shapes (e.g. merged stream frames) would
 // otherwise keep one device blob per shape forever.  Called before a batch builds its launch
@@ -574,7 +574,9 @@ static int grow(void **ptr, size_t *have, size_t need, bool zero) {
         *ptr = nullptr;
         *have = 0;
     }
-    size_t sz = need + need / 8 + 256;
+    // Regrowing synchronises the device, so leave room for batches half as large again
+    // (a stream's batches grow a few jobs at a time while its load ramps up).
+    size_t sz = need + need / 2 + 256;
     if (cudaMalloc(ptr, sz) != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
