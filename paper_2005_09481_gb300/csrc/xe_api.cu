@@ -9,7 +9,6 @@
 #include <cstring>
 #include <map>
 #include <mutex>
-#include <queue>
 #include <string>
 #include <vector>
 
@@ -116,6 +115,20 @@ static void enumerate_tiles(const std::vector<JobShape> &jobs, int eb, int tile_
     }
 }
 
+// The number of tiles enumerate_tiles makes for one channel of N inputs.
+static int64_t count_tiles(int N, int tile_n) {
+    int64_t n = 0;
+    for (int i0 = 0; i0 < N; i0 += kBM) {
+        int j0 = i0;
+        if (j0 % tile_n != 0) {
+            ++n;
+            j0 += kBM;
+        }
+        if (j0 < N) n += (N - j0 + tile_n - 1) / tile_n;
+    }
+    return n;
+}
+
 // Equal contiguous ranges of the concatenated k-iterations of tiles [t_lo, t_hi), dealt to
 // CTAs 0..G-1 (appended to their lists).
 static void stream_k(const std::vector<Tile> &tiles, int t_lo, int t_hi, int G,
@@ -141,6 +154,35 @@ static void stream_k(const std::vector<Tile> &tiles, int t_lo, int t_hi, int G,
     }
 }
 
+// The least-loaded CTA (the lowest index among equal loads) as a tournament tree over the
+// CTAs: top() is the CTA a greedy schedule deals the next part to, add() charges it the part.
+// The same choice as popping the smallest (load, CTA) pair from a heap, at a fixed cost of
+// log2(G) comparisons per part.
+template <typename L>
+struct LeastLoaded {
+    int G, n_leaf = 1;
+    std::vector<L> load;
+    std::vector<int> win;     // node i: the winning CTA of its subtree (leaves n_leaf + b; -1: none)
+    explicit LeastLoaded(int g) : G(g), load(static_cast<size_t>(g), L(0)) {
+        while (n_leaf < G) n_leaf <<= 1;
+        win.assign(static_cast<size_t>(2 * n_leaf), -1);
+        for (int b = 0; b < G; ++b) win[size_t(n_leaf + b)] = b;
+        for (int i = n_leaf - 1; i >= 1; --i) win[size_t(i)] = better(win[size_t(2 * i)], win[size_t(2 * i + 1)]);
+    }
+    int better(int a, int b) const {
+        if (a < 0) return b;
+        if (b < 0) return a;
+        const L la = load[size_t(a)], lb = load[size_t(b)];
+        return (lb < la || (lb == la && b < a)) ? b : a;
+    }
+    int top() const { return win[1]; }
+    void add(int b, L d) {
+        load[size_t(b)] += d;
+        for (int i = (n_leaf + b) >> 1; i >= 1; i >>= 1)
+            win[size_t(i)] = better(win[size_t(2 * i)], win[size_t(2 * i + 1)]);
+    }
+};
+
 // Weighted schedule: every tile is cut into the same number s of equal k-parts, and the
 // parts are dealt in k-phase order (all first parts, then all second parts, ...; heavier
 // jobs first within a phase) each to the CTA with the least weighted load so far, so that
@@ -157,13 +199,12 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
     }
     std::vector<int> order(static_cast<size_t>(n));
     for (int t = 0; t < n; ++t) order[size_t(t)] = t;
-    std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
+    auto heavier = [&](int a, int b) {
         return weight[size_t(p.tiles[size_t(a)].job)] > weight[size_t(p.tiles[size_t(b)].job)];
-    });
-    using Load = std::pair<double, int>;
+    };
+    if (!std::is_sorted(order.begin(), order.end(), heavier)) std::stable_sort(order.begin(), order.end(), heavier);
     auto deal = [&](int s, std::vector<std::vector<Seg>> *out) {
-        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-        for (int b = 0; b < G; ++b) heap.push(Load{0.0, b});
+        LeastLoaded<double> ll(G);
         const double over = s > 1 ? g_opt.part_overhead / 100.0 * max_kb : 0.0;
         double makespan = 0;
         for (int k = 0; k < s; ++k)
@@ -171,12 +212,10 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
                 const Tile &tl = p.tiles[size_t(t)];
                 const int lo = int(int64_t(k) * tl.kblocks / s), hi = int(int64_t(k + 1) * tl.kblocks / s);
                 if (hi <= lo) continue;
-                Load l = heap.top();
-                heap.pop();
-                l.first += double(hi - lo) * weight[size_t(tl.job)] / 100.0 + over;
-                makespan = std::max(makespan, l.first);
-                if (out) (*out)[size_t(l.second)].push_back(Seg{t, lo, hi, -1});
-                heap.push(l);
+                const int b = ll.top();
+                ll.add(b, double(hi - lo) * weight[size_t(tl.job)] / 100.0 + over);
+                makespan = std::max(makespan, ll.load[size_t(b)]);
+                if (out) (*out)[size_t(b)].push_back(Seg{t, lo, hi, -1});
             }
         return makespan;
     };
@@ -218,23 +257,23 @@ static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weig
             per[size_t(t % G)].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
         stream_k(p.tiles, full, n, G, per);
     } else if (sched == kSchedLPT) {
+        // Longest tile first to the least-loaded CTA; every CTA then walks its tiles in tile
+        // order.  (Batches whose jobs arrive longest first are already in order.)
         std::vector<int> order(static_cast<size_t>(n));
         for (int t = 0; t < n; ++t) order[size_t(t)] = t;
-        std::stable_sort(order.begin(), order.end(), [&](int a, int b) {
-            return p.tiles[size_t(a)].kblocks > p.tiles[size_t(b)].kblocks;
-        });
-        using Load = std::pair<int64_t, int>;
-        std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
-        for (int b = 0; b < G; ++b) heap.push(Load{0, b});
+        auto longer = [&](int a, int b) { return p.tiles[size_t(a)].kblocks > p.tiles[size_t(b)].kblocks; };
+        if (!std::is_sorted(order.begin(), order.end(), longer)) std::stable_sort(order.begin(), order.end(), longer);
+        LeastLoaded<int64_t> ll(G);
+        std::vector<int> cta_of(static_cast<size_t>(n)), count(static_cast<size_t>(G), 0);
         for (int t : order) {
-            Load l = heap.top();
-            heap.pop();
-            per[size_t(l.second)].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
-            l.first += p.tiles[size_t(t)].kblocks;
-            heap.push(l);
+            const int b = ll.top();
+            cta_of[size_t(t)] = b;
+            ++count[size_t(b)];
+            ll.add(b, p.tiles[size_t(t)].kblocks);
         }
-        for (auto &v : per)
-            std::sort(v.begin(), v.end(), [](const Seg &a, const Seg &b) { return a.tile < b.tile; });
+        for (int b = 0; b < G; ++b) per[size_t(b)].reserve(size_t(count[size_t(b)]));
+        for (int t = 0; t < n; ++t)
+            per[size_t(cta_of[size_t(t)])].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
     } else if (sched == kSchedPairSplit) {
         // Pairs of tiles that share (job, channel, column block, width, length) run on the two
         // CTAs of a cluster and share their B planes; the remaining tiles pair up without
@@ -308,41 +347,44 @@ static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weig
 // Returns false if the segments do not partition every tile's k-range exactly.
 static bool finalize_parts(HostPlan &p) {
     const int n = int(p.tiles.size());
-    std::vector<std::vector<int>> by_tile(static_cast<size_t>(n));
-    for (int q = 0; q < int(p.segs.size()); ++q)
-        if (p.segs[size_t(q)].tile >= 0) by_tile[size_t(p.segs[size_t(q)].tile)].push_back(q);
+    const int ns = int(p.segs.size());
+    // The segments of every tile, in segment order (a counting sort by tile), then each
+    // tile's list by k_lo.
+    std::vector<int> first(static_cast<size_t>(n) + 1, 0), qs(static_cast<size_t>(ns));
+    for (const Seg &s : p.segs)
+        if (s.tile >= 0) ++first[size_t(s.tile) + 1];
+    for (int t = 0; t < n; ++t) first[size_t(t) + 1] += first[size_t(t)];
+    {
+        std::vector<int> fill(first.begin(), first.end() - 1);
+        for (int q = 0; q < ns; ++q)
+            if (p.segs[size_t(q)].tile >= 0) qs[size_t(fill[size_t(p.segs[size_t(q)].tile)]++)] = q;
+    }
     p.tile_slots.clear();
     p.n_partial = 0;
     p.total_iters = 0;
     for (int t = 0; t < n; ++t) {
         Tile &tl = p.tiles[size_t(t)];
-        std::vector<int> &qs = by_tile[size_t(t)];
-        std::sort(qs.begin(), qs.end(),
-                  [&](int a, int b) { return p.segs[size_t(a)].k_lo < p.segs[size_t(b)].k_lo; });
+        int *q0 = qs.data() + first[size_t(t)], *q1 = qs.data() + first[size_t(t) + 1];
+        if (q1 - q0 > 1)
+            std::sort(q0, q1, [&](int a, int b) { return p.segs[size_t(a)].k_lo < p.segs[size_t(b)].k_lo; });
         int k = 0;
-        for (int q : qs) {
-            if (p.segs[size_t(q)].k_lo != k) return false;
-            k = p.segs[size_t(q)].k_hi;
+        for (const int *q = q0; q != q1; ++q) {
+            if (p.segs[size_t(*q)].k_lo != k) return false;
+            k = p.segs[size_t(*q)].k_hi;
         }
         if (k != tl.kblocks) return false;
         p.total_iters += tl.kblocks;
         tl.n_parts = 0;
         tl.part_off = int(p.tile_slots.size());
-        if (qs.size() > 1) {
-            for (int q : qs) {
-                p.segs[size_t(q)].slot = p.n_partial;
+        if (q1 - q0 > 1) {
+            for (const int *q = q0; q != q1; ++q) {
+                p.segs[size_t(*q)].slot = p.n_partial;
                 p.tile_slots.push_back(p.n_partial);
                 ++p.n_partial;
             }
-            tl.n_parts = int(qs.size());
+            tl.n_parts = int(q1 - q0);
         }
     }
-    return true;
-}
-
-static bool uniform_kblocks(const std::vector<Tile> &tiles) {
-    for (const Tile &t : tiles)
-        if (t.kblocks != tiles[0].kblocks) return false;
     return true;
 }
 
@@ -353,13 +395,19 @@ static bool uniform_kblocks(const std::vector<Tile> &tiles) {
 static TuneCfg heuristic(const std::vector<JobShape> &jobs, int eb, int n_sm) {
     TuneCfg c{g_opt.n_cta > 0 ? g_opt.n_cta : n_sm, g_opt.tile_n > 0 ? g_opt.tile_n : 256, g_opt.sched};
     if (c.sched < 0) {
-        std::vector<Tile> tiles;
-        enumerate_tiles(jobs, eb, c.tile_n, tiles);
-        bool weighted = false;
-        for (const JobShape &j : jobs) weighted = weighted || j.weight != 100;
+        // Decided from the job shapes alone (every job has at least one tile, all of them
+        // with the job's k-block count), without enumerating the tiles.
+        bool weighted = false, uniform = true;
+        int64_t n_tiles = 0;
+        const int64_t kb0 = kblocks_of(jobs[0].T, eb);
+        for (const JobShape &j : jobs) {
+            weighted = weighted || j.weight != 100;
+            uniform = uniform && kblocks_of(j.T, eb) == kb0;
+            n_tiles += count_tiles(j.N, c.tile_n) * j.C;
+        }
         if (weighted) c.sched = kSchedWeighted;
-        else if (!uniform_kblocks(tiles)) c.sched = kSchedLPT;
-        else if (int(tiles.size()) < c.n_cta) c.sched = kSchedSplit;
+        else if (!uniform) c.sched = kSchedLPT;
+        else if (n_tiles < c.n_cta) c.sched = kSchedSplit;
         else c.sched = kSchedHybrid;
     }
     return c;

@@ -251,6 +251,32 @@ def test_schedules_cover_every_tile_and_k_once(sched, tile_n):
         _check_plan(shapes, n_cta, sched, tile_n)
 
 
+@pytest.mark.parametrize("seed", range(6))
+def test_lpt_schedule_is_the_greedy_longest_first(seed):
+    # The uneven-batch schedule against a plain heap greedy: tiles longest first (ties in tile
+    # order), each to the CTA with the least load (lowest index among equals); every CTA then
+    # walks its tiles in tile order, each whole.
+    import heapq
+    rng = np.random.default_rng(seed)
+    shapes = [(int(rng.choice([64, 130, 256, 700, 2048])), int(rng.choice([64, 1000, 8192, 16384, 32768])), 1)
+              for _ in range(int(rng.integers(2, 30)))]
+    if rng.integers(2):
+        shapes.sort(key=lambda s: -s[1])
+    n_cta = int(rng.choice([7, 148, 152, 304]))
+    d = xe.plan_dump(shapes, n_cta, xe.SCHEDULES["lpt"], 256)
+    kb = d["tiles"][:, 5]
+    order = sorted(range(len(kb)), key=lambda t: -kb[t])          # stable: ties keep tile order
+    heap = [(0, b) for b in range(n_cta)]
+    per = [[] for _ in range(n_cta)]
+    for t in order:
+        load, b = heapq.heappop(heap)
+        per[b].append(t)
+        heapq.heappush(heap, (load + int(kb[t]), b))
+    want = [(b, t, 0, int(kb[t])) for b in range(n_cta) for t in sorted(per[b])]
+    got = [tuple(int(v) for v in s[:4]) for s in d["segs"]]
+    assert got == want
+
+
 def test_split_schedule_aligns_parts_for_the_headline():
     d = _check_plan([(2048, 32768, 1)], 152, 1, 256)
     assert d["n_cta"] == 144                       # 72 tiles x 2 equal k-parts
