@@ -51,11 +51,13 @@ def peaks():
         return 1900.0, 6800.0, "fallback"
 
 
+_TOKENS = re.compile(r'("(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\')|/\*.*?\*/|//[^\n]*', re.S)
+
+
 def code_of(text):
     """Source text without comments and whitespace (a comment edit leaves the kernel as it
-    was profiled)."""
-    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
-    text = re.sub(r"//[^\n]*", " ", text)
+    was profiled); string and character literals are kept whole, "//" inside them included."""
+    text = _TOKENS.sub(lambda mo: mo.group(1) if mo.group(1) is not None else " ", text)
     return "".join(text.split())
 
 
