@@ -112,6 +112,11 @@ int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int3
  * up). */
 #define XE_HOST_SLOTS 4
 int xe_correlate_host_async(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis, int slot);
+
+/* Wait until slot `slot`'s visibilities are in its host_vis (blocking the calling thread).
+ * Returns XE_OK (also for a slot with nothing in flight), XE_EINVAL for a slot outside
+ * [0, XE_HOST_SLOTS), XE_ETIMEOUT if a kernel of the slot gave up on a bounded device wait
+ * (its output is then invalid; the status is cleared), XE_ECUDA or XE_ENODEV. */
 int xe_host_wait(int slot);
 
 /* ---- batched correlation (one persistent launch over many jobs) ------------------- */
@@ -434,10 +439,15 @@ int xe_device_info(int *n_sm, int *max_clusters);
  * elem_bytes == 1, f16 when elem_bytes == 2.  Host-only; for tests of the encoder. */
 uint32_t xe_debug_operand_code(int v, int elem_bytes);
 
+/* Record CUDA events around the kernels of the following calls of this process (enable
+ * = 1) or not (0, the default: the events and the host waits on them add a few
+ * microseconds to every call).  Returns XE_OK. */
+int xe_set_timing(int enable);
+
 /* Device time in milliseconds of the kernels of the last xe_correlate* call on this
  * thread, split as {stage, correlate}; filled only when timing was enabled with
- * xe_set_timing(1).  Returns XE_OK or XE_EAGAIN if nothing was recorded. */
-int xe_set_timing(int enable);
+ * xe_set_timing(1).  Waits for that call's events.  Returns XE_OK or XE_EAGAIN if nothing
+ * was recorded. */
 int xe_last_timing(float *stage_ms, float *correlate_ms);
 /* As xe_last_timing, plus the device time of work after the correlation kernel for the
  * valid-sample counts of a masked call.  The count jobs run inside the correlation kernel

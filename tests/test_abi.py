@@ -41,6 +41,25 @@ def test_binding_constants_match_the_header():
     assert 128 * xe.XE_MAX_T < 2**31 <= 128 * (xe.XE_MAX_T + 1)
 
 
+def test_every_entry_point_has_its_own_comment():
+    # Each declaration in include/*.h follows a comment block (at most a #define between).
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if not h.endswith(".h"):
+            continue
+        lines = open(os.path.join(ROOT, "include", h)).read().split("\n")
+        depth = 0
+        for i, line in enumerate(lines):
+            s = line.strip()
+            if s.startswith("/*") or depth:
+                depth = 0 if s.endswith("*/") else 1
+                continue
+            if re.match(r"^[A-Za-z_][\w\s\*]*?\b(xe_\w+)\s*\(", s) and not s.startswith("#"):
+                j = i - 1
+                while j >= 0 and (not lines[j].strip() or lines[j].strip().startswith("#define")):
+                    j -= 1
+                assert lines[j].strip().endswith("*/"), f"{h}:{i + 1} {s[:50]}"
+
+
 def test_every_declared_symbol_is_exported():
     L = xe.load()
     missing = [n for n in _declared() if not hasattr(L, n)]
