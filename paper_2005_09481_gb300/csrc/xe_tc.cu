@@ -24,7 +24,11 @@
 //                 upper triangle.  A tile split into several segments is summed exactly
 //                 through a workspace by the last segment to finish (arrival counter, no
 //                 spinning on other CTAs), or, for two parts, by a symmetric exchange of
-//                 column halves.
+//                 column halves.  When a CTA's only segment is one part of such a pair,
+//                 all eight warps (the producer, the MMA warp and warps 6-7 join after the
+//                 mainloop) run its epilogue, two warps per tensor-memory lane quarter.  The
+//                 launch may overlap the staging kernel (programmatic dependent launch):
+//                 only the producer waits for it before reading planes.
 #include <cstdint>
 #include <type_traits>
 #include <cuda_runtime.h>
