@@ -182,7 +182,14 @@ def run_reference(args):
     # launcher sets OMP_NUM_THREADS=1 for each process).
     oracle.set_threads(len(os.sched_getaffinity(0)))
     packed = synth.gauss_plane(N_IN, T_SAMPLES, 1)[0]
+    # Samples per step: 64, fewer (a power of two, at least 8) when K + W steps of 64 would
+    # take more than about a minute on this host; every step still covers all baselines.
     T_s = 64
+    t0 = time.perf_counter()
+    oracle.correlate64(np.ascontiguousarray(packed[:T_s]), N_IN, T_s, 1)
+    d64 = time.perf_counter() - t0
+    while T_s > 8 and (args.steps + args.warmup) * d64 * T_s / 64 > 60.0:
+        T_s //= 2
     sample = np.ascontiguousarray(packed[:T_s])
     for _ in range(args.warmup):
         oracle.correlate64(sample, N_IN, T_s, 1)
