@@ -29,9 +29,21 @@ def _deps():
             + glob.glob(os.path.join(INCLUDE, "*.h")))
 
 
+SOURCES_STAMP = os.path.join(OUT_DIR, "sources.txt")
+
+
+def _source_list() -> str:
+    return "\n".join(os.path.basename(s) for s in _sources()) + "\n"
+
+
 def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+    """The library exists, is newer than every source and header, and was linked from the
+    current set of sources (a removed source forces a relink without its object)."""
+    if not os.path.exists(LIB) or not os.path.exists(SOURCES_STAMP):
         return False
+    with open(SOURCES_STAMP) as f:
+        if f.read() != _source_list():
+            return False
     t = os.path.getmtime(LIB)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
@@ -43,6 +55,10 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     os.makedirs(OUT_DIR, exist_ok=True)
     extra = list(extra or [])
     srcs = _sources()
+    keep = {os.path.basename(s) + ".o" for s in srcs}
+    for obj in glob.glob(os.path.join(OUT_DIR, "*.o")):
+        if os.path.basename(obj) not in keep:
+            os.remove(obj)                      # the object of a source that no longer exists
 
     def compile_one(src):
         obj = os.path.join(OUT_DIR, os.path.basename(src) + ".o")
@@ -64,6 +80,8 @@ def build(force: bool = False, verbose: bool = False, extra: list[str] | None = 
     if r.returncode != 0:
         raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, LIB)
+    with open(SOURCES_STAMP, "w") as f:
+        f.write(_source_list())
     return LIB
 
 

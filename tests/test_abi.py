@@ -333,3 +333,35 @@ def test_clustered_schedule_pairs_walk_in_lockstep(shapes, n_cta):
     if shapes == [(2048, 32768, 1)]:
         assert d["n_cta"] == 144                                        # 36 units x 2 k-parts
         assert (segs[:, 5] == 1).sum() == 112                          # 28 shared pairs
+
+
+def test_plain_c_program_links_and_calls_the_library(tmp_path):
+    # The boundary is a C ABI: a C11 program includes xe.h, links libxe.so and calls the
+    # host-only entry points (no GPU needed).
+    import shutil
+    import subprocess
+    if shutil.which("gcc") is None:
+        pytest.skip("gcc not available")
+    lib = xe.lib_path()
+    src = tmp_path / "use_xe.c"
+    src.write_text(r"""
+#include <stdio.h>
+#include "xe.h"
+int main(void) {
+    const int N[1] = {2048};
+    const int64_t T[1] = {32768};
+    const int C[1] = {1};
+    int64_t tiles = 0, iters = 0, split = 0;
+    int rc = xe_plan_stats(N, T, C, 1, 152, &tiles, &iters, &split);
+    printf("%d %.0f %d %d %d %lld %lld %s\n", xe_version() >= 100, xe_cmac(2048, 32768, 1),
+           xe_correlate(NULL, 4, 4, 1, NULL), xe_correlate(NULL, 4, 16777216, 1, NULL), rc,
+           (long long)tiles, (long long)split, xe_strerror(XE_OK));
+    return 0;
+}
+""")
+    exe = tmp_path / "use_xe"
+    libdir = os.path.dirname(lib)
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", "-pedantic", f"-I{os.path.join(ROOT, 'include')}",
+                    str(src), f"-L{libdir}", "-lxe", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
+    assert out == ["1", str(2_098_176 * 32768), str(xe.XE_EINVAL), str(xe.XE_EINVAL), "0", "72", "72", "ok"]
