@@ -365,3 +365,24 @@ int main(void) {
                     str(src), f"-L{libdir}", "-lxe", f"-Wl,-rpath,{libdir}", "-o", str(exe)], check=True)
     out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout.split()
     assert out == ["1", str(2_098_176 * 32768), str(xe.XE_EINVAL), str(xe.XE_EINVAL), "0", "72", "72", "ok"]
+
+
+def test_error_detail_is_per_thread():
+    # xe_last_error reports the last failure of the calling thread only.
+    import threading
+    L = xe.load()
+    buf = (ctypes.c_uint8 * 64)()
+    out = (ctypes.c_int32 * 64)()
+    barrier = threading.Barrier(2)
+    seen = {}
+
+    def worker(name, args, code):
+        assert L.xe_correlate(*args) == code
+        barrier.wait()                      # both threads have failed before either reads
+        seen[name] = L.xe_last_error().decode()
+
+    a = threading.Thread(target=worker, args=("overflow", (buf, 4, 16777216, 1, out), xe.XE_EOVERFLOW))
+    b = threading.Thread(target=worker, args=("n", (buf, 0, 4, 1, out), xe.XE_EINVAL))
+    a.start(), b.start()
+    a.join(), b.join()
+    assert "16777216" in seen["overflow"] and "N=0" in seen["n"]
