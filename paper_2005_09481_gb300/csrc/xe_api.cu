@@ -508,7 +508,12 @@ static thread_local TuneCfg g_last_cfg{0, 0, -1};
 
 static int get_device(Device **out) {
     int dev = 0;
-    XE_CUDA(cudaGetDevice(&dev));
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaErrorNoDevice || ge == cudaErrorInsufficientDriver) {
+        cudaGetLastError();
+        return fail(XE_ENODEV, "no usable CUDA device: %s", cudaGetErrorString(ge));
+    }
+    XE_CUDA(ge);
     auto it = g_devs.find(dev);
     if (it != g_devs.end()) {
         *out = it->second;

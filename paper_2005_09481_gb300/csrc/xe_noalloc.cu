@@ -88,7 +88,10 @@ static int64_t na_tile_count(int N, int C) {
 // Device address of the array on the current device (looked up once per device).
 static int na_scratch(uint8_t **out) {
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return na_fail(XE_ECUDA, "cudaGetDevice failed");
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaErrorNoDevice || ge == cudaErrorInsufficientDriver)
+        return na_fail(XE_ENODEV, "no usable CUDA device (no device or no driver)");
+    if (ge != cudaSuccess) return na_fail(XE_ECUDA, "cudaGetDevice failed");
     if (dev < 0 || dev >= kMaxDevices) return na_fail(XE_ENODEV, "device index out of range");
     std::lock_guard<std::mutex> lk(g_na_mu);
     if (!g_na_ptr[dev]) {

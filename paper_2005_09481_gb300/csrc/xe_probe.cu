@@ -182,7 +182,10 @@ using namespace xe;
 extern "C" int xe_peak_probe(int kind, double *tflops_out, double *aux_out) {
     if (!tflops_out || kind < 0 || kind > 3) return record_error(XE_EINVAL, "bad probe request");
     int dev = 0, n_sm = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return record_error(XE_ECUDA, "cudaGetDevice failed");
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaErrorNoDevice || ge == cudaErrorInsufficientDriver)
+        return record_error(XE_ENODEV, "no usable CUDA device (no device or no driver)");
+    if (ge != cudaSuccess) return record_error(XE_ECUDA, "cudaGetDevice failed");
     cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     int *status = nullptr;
     uint8_t *src = nullptr;

@@ -471,7 +471,10 @@ int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
     if (c.max_chan < 1 || c.max_chan > 65536) return sfail(XE_EINVAL, "max_chan out of range");
     if (c.ring_frames < 2 || c.ring_frames > 64) return sfail(XE_EINVAL, "ring_frames must lie in [2, 64]");
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return sfail(XE_ECUDA, "cudaGetDevice failed");
+    const cudaError_t ge = cudaGetDevice(&dev);
+    if (ge == cudaErrorNoDevice || ge == cudaErrorInsufficientDriver)
+        return sfail(XE_ENODEV, "no usable CUDA device (no device or no driver)");
+    if (ge != cudaSuccess) return sfail(XE_ECUDA, "cudaGetDevice failed");
     xe_stream *s = new xe_stream;
     s->cfg = c;
     s->dev = dev;

@@ -386,3 +386,35 @@ def test_error_detail_is_per_thread():
     a.start(), b.start()
     a.join(), b.join()
     assert "16777216" in seen["overflow"] and "N=0" in seen["n"]
+
+
+def test_compute_calls_without_a_device_fail_with_enodev():
+    # No CPU fallback: on a machine without a usable CUDA device every compute entry point
+    # returns XE_ENODEV (and the binding raises), for valid arguments.
+    torch = pytest.importorskip("torch")
+    if torch.cuda.is_available():
+        pytest.skip("a CUDA device is present")
+    L = xe.load()
+    N, T = 64, 128
+    inp = (ctypes.c_uint8 * (N * T))()
+    vis = (ctypes.c_int32 * (N * (N + 1)))()
+    w = (ctypes.c_int8 * (2 * N))()
+    y = (ctypes.c_int32 * (2 * T))()
+    frames = (ctypes.c_uint8 * (N * T))()
+    d = ctypes.c_double()
+    calls = {
+        "xe_correlate": lambda: L.xe_correlate(inp, N, T, 1, vis),
+        "xe_correlate_host": lambda: L.xe_correlate_host(inp, N, T, 1, vis, 0),
+        "xe_correlate_noalloc": lambda: L.xe_correlate_noalloc(inp, N, T, 1, vis, None),
+        "xe_beamform": lambda: L.xe_beamform(inp, N, T, 1, w, 1, y, None),
+        "xe_corner_turn": lambda: L.xe_corner_turn(inp, 2, 1, N // 2, T, frames, None, None),
+        "xe_peak_probe": lambda: L.xe_peak_probe(0, ctypes.byref(d), ctypes.byref(d)),
+    }
+    for name, call in calls.items():
+        assert call() == xe.XE_ENODEV, (name, L.xe_last_error())
+    with pytest.raises(xe.XeError) as e:
+        xe.correlate_host(torch.zeros((1, T, N), dtype=torch.uint8), N, T, 1)
+    assert e.value.code == xe.XE_ENODEV
+    with pytest.raises(xe.XeError) as e:
+        xe.Stream(N, 8192, 32768, max_chan=1, hbm_budget=1 << 30)
+    assert e.value.code == xe.XE_ENODEV
