@@ -431,6 +431,14 @@ int xe_set_option(const char *key, int64_t value);
  * is then invalid). */
 int xe_device_status(void *stream);
 
+/* The library keeps scratch memory (staged operand planes, workspace, counters, a status
+ * word) per CUDA stream it has run on.  Call this before destroying a stream the library
+ * was used on, to free that memory: it waits for the stream's work first.  A later call on
+ * a stream with the same handle allocates afresh.  The streaming server does this for its
+ * own streams.  Returns XE_OK (also for a stream the library never used), XE_ECUDA or
+ * XE_ENODEV. */
+int xe_release_stream(void *stream);
+
 /* Streaming multiprocessors of the current device, and how many 2-CTA clusters of the
  * clustered correlation kernel can be resident at once (0 if none).  Returns an XE_* code. */
 int xe_device_info(int *n_sm, int *max_clusters);

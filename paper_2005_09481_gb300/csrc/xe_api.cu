@@ -15,6 +15,7 @@
 #include <cuda_runtime.h>
 
 #include "xe.h"
+#include "xe_host.h"
 #include "xe_internal.h"
 
 namespace xe {
@@ -1068,6 +1069,28 @@ int run_jobs_accumulate(const xe_job *jobs, int n_jobs, cudaStream_t s) {
     return run_jobs(jobs, n_jobs, XE_ALGO_TC, s, 1);
 }
 
+int release_stream_scratch(cudaStream_t s) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    Device *d = nullptr;
+    int rc = get_device(&d);
+    if (rc) return rc;
+    auto it = d->scratch.find(s);
+    if (it == d->scratch.end()) return XE_OK;
+    XE_CUDA(cudaStreamSynchronize(s));
+    Scratch *sc = it->second;
+    d->scratch.erase(it);
+    cudaFree(sc->planes);
+    cudaFree(sc->ws);
+    cudaFree(sc->counters);
+    cudaFree(sc->status);
+    cudaFree(sc->beam_wt);
+    cudaFree(sc->corner_partial);
+    for (cudaEvent_t e : sc->ev)
+        if (e) cudaEventDestroy(e);
+    delete sc;
+    return XE_OK;
+}
+
 int run_jobs_mixed(const xe_job *jobs, const int *accumulate, int n_jobs, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_job_acc = accumulate;
@@ -1566,6 +1589,8 @@ int xe_device_status(void *stream) {
     }
     return XE_OK;
 }
+
+int xe_release_stream(void *stream) { return release_stream_scratch(reinterpret_cast<cudaStream_t>(stream)); }
 
 uint32_t xe_debug_operand_code(int v, int elem_bytes) { return operand_code(v, elem_bytes); }
 

@@ -32,6 +32,7 @@
 #include <cuda_runtime.h>
 
 #include "xe.h"
+#include "xe_host.h"
 #include "xe_internal.h"
 
 namespace xe {
@@ -714,6 +715,7 @@ void xe_stream_close(xe_stream *s) {
     cudaStreamSynchronize(s->copy_s);
     cudaStreamSynchronize(s->comp_s);
     cudaStreamSynchronize(s->d2h_s);
+    release_stream_scratch(s->comp_s);     // the correlation's scratch for this stream
     for (Chan &ch : s->chans) {
         for (Slot &sl : ch.ring) cudaEventDestroy(sl.copy_ev);
         if (ch.ring_base) cudaFree(ch.ring_base);

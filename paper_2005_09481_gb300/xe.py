@@ -81,6 +81,7 @@ def load():
             "xe_correlate_view": ([p, p, i32, i64, i32, p, p], i32),
             "xe_corner_turn": ([p, i32, i32, i32, i64, p, p, p], i32),
             "xe_device_status": ([p], i32),
+            "xe_release_stream": ([p], i32),
             "xe_debug_operand_code": ([i32, i32], ctypes.c_uint32),
             "xe_plan_dump": ([p, p, p, i32, i32, i32, i32, p, i64], i64),
             "xe_last_config": ([p, p, p], i32),
@@ -151,6 +152,12 @@ def last_timing_counts() -> tuple[float, float, float]:
 
 def device_status(stream=None):
     _check(load().xe_device_status(_stream_handle(stream)), "xe_device_status")
+
+
+def release_stream(stream=None):
+    """Free the library's scratch memory for `stream` (a torch.cuda.Stream, or None for the
+    current stream); call before the stream is destroyed."""
+    _check(load().xe_release_stream(_stream_handle(stream)), "xe_release_stream")
 
 
 def peak_probe(kind: str, with_aux: bool = False):

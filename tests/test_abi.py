@@ -409,6 +409,7 @@ def test_compute_calls_without_a_device_fail_with_enodev():
         "xe_beamform": lambda: L.xe_beamform(inp, N, T, 1, w, 1, y, None),
         "xe_corner_turn": lambda: L.xe_corner_turn(inp, 2, 1, N // 2, T, frames, None, None),
         "xe_peak_probe": lambda: L.xe_peak_probe(0, ctypes.byref(d), ctypes.byref(d)),
+        "xe_release_stream": lambda: L.xe_release_stream(None),
     }
     for name, call in calls.items():
         assert call() == xe.XE_ENODEV, (name, L.xe_last_error())

@@ -186,3 +186,22 @@ def test_later_launch_group_needing_more_scratch(xe):
         n, t = shapes[q]
         want = oracle.correlate_dense(ins[q], n, t, 1) if n > 256 else oracle.correlate(ins[q], n, t, 1)
         np.testing.assert_array_equal(outs[q].cpu().numpy(), want)
+
+
+def test_release_stream_frees_scratch_and_reallocates(xe):
+    # Scratch is kept per stream; releasing it waits for the stream's work, and the next call
+    # on the same stream allocates afresh and stays exact.
+    N, T = 256, 4096
+    p = synth.uniform(N, T, 1, seed=91)
+    want = oracle.correlate_dense(p, N, T, 1)
+    d = torch.from_numpy(p).cuda()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    for _ in range(2):
+        with torch.cuda.stream(s):
+            out = xe.empty_vis(N, 1)
+            xe.correlate(d, N, T, 1, out=out, stream=s)
+        xe.device_status(s)
+        xe.release_stream(s)
+        assert np.array_equal(out.cpu().numpy(), want)
+    xe.release_stream(s)                    # nothing left to free: still XE_OK
