@@ -791,7 +791,9 @@ def main():
             "sampled_exact": sampled_exact,
             "p99_frame_latency_ms": stream["p99_latency_ms"] if stream else None,
             "stream": ({k: stream[k] for k in ("channels", "sustained", "cmac_per_s", "p50_latency_ms",
-                                               "p99_latency_ms", "frame_T", "integ_T", "device_source")}
+                                               "p99_latency_ms", "max_latency_ms", "frame_T", "integ_T",
+                                               "device_source", "producer_late_frames", "push_overruns",
+                                               "frames_dropped", "drain_s", "counters")}
                        if stream else None),
             "masked": masked,
             "beams": beams,
