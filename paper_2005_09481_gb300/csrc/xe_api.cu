@@ -619,7 +619,7 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
     return XE_OK;
 }
 
-static int grow(void **ptr, size_t *have, size_t need, bool zero) {
+static int grow(void **ptr, size_t *have, size_t need, bool zero, bool headroom = true) {
     if (*have >= need && *ptr) return XE_OK;
     if (*ptr) {
         cudaError_t e = cudaDeviceSynchronize();  // nothing may still use the old buffer
@@ -630,7 +630,7 @@ static int grow(void **ptr, size_t *have, size_t need, bool zero) {
     }
     // Regrowing synchronises the device, so leave room for batches half as large again
     // (a stream's batches grow a few jobs at a time while its load ramps up).
-    size_t sz = need + need / 2 + 256;
+    size_t sz = headroom ? need + need / 2 + 256 : need;
     if (cudaMalloc(ptr, sz) != cudaSuccess) {
         cudaGetLastError();
         *ptr = nullptr;
@@ -1089,6 +1089,32 @@ int release_stream_scratch(cudaStream_t s) {
         if (e) cudaEventDestroy(e);
     delete sc;
     return XE_OK;
+}
+
+int reserve_stream_scratch(cudaStream_t s, int max_jobs, int N, int64_t max_T) {
+    if (max_jobs < 1 || N < 1 || N > XE_MAX_N || max_T < 1) return XE_OK;
+    std::lock_guard<std::mutex> lk(g_mu);
+    Device *d = nullptr;
+    int rc = get_device(&d);
+    if (rc) return rc;
+    Scratch *sc = nullptr;
+    rc = get_scratch(d, s, &sc);
+    if (rc) return rc;
+    // The bounds build_launches meets for such batches: one launch group holds at most
+    // kMaxJobs jobs, each staged over one exact window at most; 128-wide tiles are the most
+    // numerous; the schedules give at most two partial segments per CTA (whole tiles for
+    // uneven lengths).
+    const int eb = g_opt.operand_bytes;
+    const int64_t wt = g_opt.exact_chunk_t / samples_per_stage(eb) * samples_per_stage(eb);
+    const size_t jobs = size_t(std::min(max_jobs, kMaxJobs));
+    const size_t planes = jobs * size_t(kblocks_of(std::min(max_T, wt), eb)) * 2 * size_t(n_pad_of(N)) * kRowBytes;
+    const size_t counters = jobs * size_t(count_tiles(N, 128)) * sizeof(int);
+    const size_t ws = size_t(2 * d->n_sm) * size_t(kWsSlotElems) * sizeof(int32_t);
+    rc = grow(reinterpret_cast<void **>(&sc->planes), &sc->planes_bytes, planes, false, false);
+    if (rc) return rc;
+    rc = grow(reinterpret_cast<void **>(&sc->ws), &sc->ws_bytes, ws, false, false);
+    if (rc) return rc;
+    return grow(reinterpret_cast<void **>(&sc->counters), &sc->counters_bytes, counters, true, false);
 }
 
 int run_jobs_mixed(const xe_job *jobs, const int *accumulate, int n_jobs, cudaStream_t s) {

@@ -1,6 +1,7 @@
 // xe_host.h -- host runtime functions shared between translation units (no kernel
 // includes this header).
 #pragma once
+#include <cstdint>
 #include <cuda_runtime.h>
 
 namespace xe {
@@ -10,5 +11,12 @@ namespace xe {
 // for the stream's work, and a later call on a stream with the same handle starts afresh.
 // Used by the streaming server when it closes its compute stream.  Returns an XE_* code.
 int release_stream_scratch(cudaStream_t s);
+
+// Size the scratch of stream `s` now for launch groups of up to `max_jobs` jobs of one
+// channel each, N inputs and at most `max_T` samples (staged planes, tile counters and the
+// split-tile workspace), so that no such batch has to regrow it later: a regrowth
+// synchronises the device.  Returns an XE_* code; a buffer that could not be allocated is
+// left empty and is allocated by the first batch that needs it.
+int reserve_stream_scratch(cudaStream_t s, int max_jobs, int N, int64_t max_T);
 
 }  // namespace xe

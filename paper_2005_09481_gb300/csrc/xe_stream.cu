@@ -498,6 +498,14 @@ int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
         delete s;
         return sfail(XE_ECUDA, "stream creation failed");
     }
+    // Size the correlation's scratch now for the largest batch the budget can admit (every
+    // channel contributes at most one job of at most `merge` frames to a launch group), so
+    // that no batch regrows it, which would synchronise the device, while frames stream in.
+    // Best effort: if the memory is not there, batches grow the scratch as they need it.
+    const int64_t fit = c.hbm_budget / int64_t(s->per_chan_bytes);
+    const int max_jobs = int(std::min<int64_t>(std::min<int64_t>(c.max_chan, fit), kMaxJobs));
+    if (reserve_stream_scratch(s->comp_s, max_jobs, c.N, int64_t(merge) * c.frame_T) != XE_OK)
+        cudaGetLastError();
     s->sched = std::thread(scheduler_main, s);
     *out = s;
     return XE_OK;
