@@ -471,6 +471,16 @@ int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
     if (c.integ_T > XE_MAX_T) return sfail(XE_EOVERFLOW, "integ_T too long for int32 visibilities");
     if (c.max_chan < 1 || c.max_chan > 65536) return sfail(XE_EINVAL, "max_chan out of range");
     if (c.ring_frames < 2 || c.ring_frames > 64) return sfail(XE_EINVAL, "ring_frames must lie in [2, 64]");
+    // One channel slot: two accumulators, the frame ring and a share of the staged planes
+    // (up to `merge` frames of a channel are correlated as one job).
+    const int64_t B = int64_t(c.N) * (c.N + 1) / 2;
+    const size_t frame_bytes = size_t(c.frame_T) * size_t(c.N);
+    const size_t acc_bytes = size_t(B) * 2 * sizeof(int32_t);
+    const size_t n_pad = size_t((c.N + kNPad - 1) / kNPad * kNPad);
+    const size_t merge = size_t(c.ring_frames < kMaxMerge ? c.ring_frames : kMaxMerge);
+    const size_t stage_bytes = merge * 2 * n_pad * size_t((c.frame_T + 63) / 64 * 64);
+    const size_t per_chan_bytes = 2 * acc_bytes + size_t(c.ring_frames) * frame_bytes + stage_bytes;
+    if (c.hbm_budget < int64_t(per_chan_bytes)) return sfail(XE_EBUDGET, "the HBM budget does not fit one channel slot");
     int dev = 0;
     const cudaError_t ge = cudaGetDevice(&dev);
     if (ge == cudaErrorNoDevice || ge == cudaErrorInsufficientDriver)
@@ -479,18 +489,11 @@ int xe_stream_open(const xe_stream_cfg *cfg, xe_stream **out) {
     xe_stream *s = new xe_stream;
     s->cfg = c;
     s->dev = dev;
-    s->B = int64_t(c.N) * (c.N + 1) / 2;
-    s->frame_bytes = size_t(c.frame_T) * size_t(c.N);
-    s->acc_bytes = size_t(s->B) * 2 * sizeof(int32_t);
+    s->B = B;
+    s->frame_bytes = frame_bytes;
+    s->acc_bytes = acc_bytes;
     s->frames_per_integ = c.integ_T / c.frame_T;
-    const size_t n_pad = size_t((c.N + kNPad - 1) / kNPad * kNPad);
-    const size_t merge = size_t(c.ring_frames < kMaxMerge ? c.ring_frames : kMaxMerge);
-    const size_t stage_bytes = merge * 2 * n_pad * size_t((c.frame_T + 63) / 64 * 64);
-    s->per_chan_bytes = 2 * s->acc_bytes + size_t(c.ring_frames) * s->frame_bytes + stage_bytes;
-    if (c.hbm_budget < int64_t(s->per_chan_bytes)) {
-        delete s;
-        return sfail(XE_EBUDGET, "the HBM budget does not fit one channel slot");
-    }
+    s->per_chan_bytes = per_chan_bytes;
     s->chans.resize(size_t(c.max_chan));
     if (cudaStreamCreateWithFlags(&s->copy_s, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&s->comp_s, cudaStreamNonBlocking) != cudaSuccess ||

@@ -419,3 +419,21 @@ def test_compute_calls_without_a_device_fail_with_enodev():
     with pytest.raises(xe.XeError) as e:
         xe.Stream(N, 8192, 32768, max_chan=1, hbm_budget=1 << 30)
     assert e.value.code == xe.XE_ENODEV
+
+
+def test_stream_slot_bytes_match_the_serving_loop():
+    # The serving loop sizes HBM budgets with serve.per_channel_bytes; the library admits a
+    # channel only if its slot fits.  Both count the same bytes: one byte less than a slot
+    # is refused before any device work (XE_EBUDGET), a whole slot passes that check.
+    from paper_2005_09481_gb300 import serve
+    L = xe.load()
+    for N, frame_T, ring in ((2048, 8192, 8), (64, 1000, 2), (300, 4096, 3), (17, 64, 5)):
+        per = serve.per_channel_bytes(N, frame_T, ring)
+        h = ctypes.c_void_p()
+        cfg = xe.StreamCfg(N, frame_T, 4 * frame_T, 4, per - 1, ring, 390625.0, 0)
+        assert L.xe_stream_open(ctypes.byref(cfg), ctypes.byref(h)) == xe.XE_EBUDGET
+        cfg.hbm_budget = per
+        rc = L.xe_stream_open(ctypes.byref(cfg), ctypes.byref(h))
+        assert rc != xe.XE_EBUDGET, (N, frame_T, ring)
+        if rc == xe.XE_OK:
+            L.xe_stream_close(h)
