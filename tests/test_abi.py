@@ -437,3 +437,15 @@ def test_stream_slot_bytes_match_the_serving_loop():
         assert rc != xe.XE_EBUDGET, (N, frame_T, ring)
         if rc == xe.XE_OK:
             L.xe_stream_close(h)
+
+
+def test_noalloc_limits_refused_before_any_device_call():
+    # The allocation-free entry point refuses requests beyond its fixed scratch on the host:
+    # one exact window at most, the staged planes, the tile table.
+    L = xe.load()
+    buf = (ctypes.c_uint8 * 64)()
+    out = (ctypes.c_int32 * 64)()
+    for (N, T, C, what) in [(64, 131073, 1, b"131072"), (2048, 131072, 1, b"staged operands"),
+                            (2048, 4096, 3, b"staged operands"), (16384, 64, 1, b"tiles")]:
+        assert L.xe_correlate_noalloc(buf, N, T, C, out, None) == xe.XE_EINVAL
+        assert what in L.xe_last_error(), (N, T, C, L.xe_last_error())
