@@ -449,3 +449,27 @@ def test_noalloc_limits_refused_before_any_device_call():
                             (2048, 4096, 3, b"staged operands"), (16384, 64, 1, b"tiles")]:
         assert L.xe_correlate_noalloc(buf, N, T, C, out, None) == xe.XE_EINVAL
         assert what in L.xe_last_error(), (N, T, C, L.xe_last_error())
+
+
+@pytest.mark.parametrize("n_cyl,n_freq,n_in,T", [(4, 4, 512, 7), (3, 2, 5, 9), (1, 1, 16, 3), (4, 2, 128, 2)])
+def test_bundle_view_addresses_every_sample_of_the_bundles(n_cyl, n_freq, n_in, T):
+    # The view's address of sample (c, t, n), c*s_c + t*s_t + (n // seg)*s_seg + n % seg, is
+    # where the cylinder bundles [n_cyl][T][n_freq][n_in] hold that sample of channel c.
+    from paper_2005_09481_gb300 import synth
+    N = n_cyl * n_in
+    v = xe.bundle_view(n_cyl, n_freq, n_in, T)
+    assert v.seg_inputs == n_in
+    frames = synth.uniform(N, T, n_freq, seed=5)                    # [n_freq][T][N]
+    flat = synth.bundles_of(frames, n_cyl).reshape(-1)
+    c, t, n = np.meshgrid(np.arange(n_freq), np.arange(T), np.arange(N), indexing="ij")
+    addr = c * v.chan_stride + t * v.time_stride + (n // v.seg_inputs) * v.seg_stride + n % v.seg_inputs
+    assert addr.min() >= 0 and addr.max() < flat.size
+    assert np.array_equal(flat[addr], frames)
+    assert len(np.unique(addr)) == addr.size                         # one byte per sample
+
+
+def test_bundle_view_rejects_bad_shapes():
+    L = xe.load()
+    v = xe.View()
+    for args in [(0, 4, 512, 10), (4, 0, 512, 10), (4, 4, 0, 10), (4, 4, 512, 0), (200, 1, 512, 10)]:
+        assert L.xe_bundle_view(*args, ctypes.byref(v)) == xe.XE_EINVAL, args
