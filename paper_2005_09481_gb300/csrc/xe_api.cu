@@ -638,7 +638,12 @@ static int grow(void **ptr, size_t *have, size_t need, bool zero, bool headroom 
         cudaMemGetInfo(&fr, &tot);
         return fail(XE_ENOMEM, "cannot allocate %zu bytes of scratch (%zu of %zu bytes free)", sz, fr, tot);
     }
-    if (zero) XE_CUDA(cudaMemset(*ptr, 0, sz));
+    if (zero) {
+        // cudaMemset runs on the legacy stream, which does not order work on non-blocking
+        // streams: finish it before any kernel reads the buffer.
+        XE_CUDA(cudaMemset(*ptr, 0, sz));
+        XE_CUDA(cudaStreamSynchronize(0));
+    }
     *have = sz;
     return XE_OK;
 }
@@ -655,6 +660,7 @@ static int get_scratch(Device *d, cudaStream_t s, Scratch **out) {
         return fail(XE_ENOMEM, "cannot allocate the status word");
     }
     XE_CUDA(cudaMemset(sc->status, 0, sizeof(int)));
+    XE_CUDA(cudaStreamSynchronize(0));          // (see grow)
     for (auto &e : sc->ev) XE_CUDA(cudaEventCreate(&e));
     d->scratch[s] = sc;
     *out = sc;
@@ -1337,6 +1343,7 @@ static int host_finish(Device *d, int slot) {
         if (st != 0) {
             XE_CUDA(cudaMemset(it->second->status, 0, sizeof(int)));
             if (it->second->counters) XE_CUDA(cudaMemset(it->second->counters, 0, it->second->counters_bytes));
+            XE_CUDA(cudaStreamSynchronize(0));
             return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
         }
     }
@@ -1611,6 +1618,7 @@ int xe_device_status(void *stream) {
         XE_CUDA(cudaMemset(it->second->status, 0, sizeof(int)));
         if (it->second->counters)
             XE_CUDA(cudaMemset(it->second->counters, 0, it->second->counters_bytes));
+        XE_CUDA(cudaStreamSynchronize(0));
         return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
     }
     return XE_OK;
