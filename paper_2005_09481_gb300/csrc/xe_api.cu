@@ -603,7 +603,10 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
     memcpy(host.data() + o_s, h.segs.data(), b_s);
     memcpy(host.data() + o_o, h.seg_off.data(), b_o);
     if (!h.tile_slots.empty()) memcpy(host.data() + o_l, h.tile_slots.data(), b_l - sizeof(int));
+    // A copy from pageable memory may return before it has landed, and it is ordered on the
+    // legacy stream only: wait for it, so that kernels on any stream read the whole plan.
     cudaError_t e = cudaMemcpy(p->blob, host.data(), total, cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
     if (e != cudaSuccess) {
         cudaFree(p->blob);
         delete p;
