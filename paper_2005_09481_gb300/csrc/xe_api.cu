@@ -1562,6 +1562,7 @@ int xe_correlate_masked(const uint8_t *in, const uint8_t *flags, int N, int64_t 
 
 int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
                   int64_t *n_tiles, int64_t *n_iters, int64_t *n_split_tiles) {
+    std::lock_guard<std::mutex> lk(g_mu);      // the planner reads the options
     HostPlan p;
     int rc = plan_from_args(N, T, n_chan, n_jobs, n_cta, -1, 0, p);
     if (rc) return rc;
@@ -1575,6 +1576,7 @@ int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs,
 
 int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
                      int sched, int tile_n, int32_t *out, int64_t cap) {
+    std::lock_guard<std::mutex> lk(g_mu);      // the planner reads the options
     HostPlan p;
     int rc = plan_from_args(N, T, n_chan, n_jobs, n_cta, sched, tile_n, p);
     if (rc) return rc;
