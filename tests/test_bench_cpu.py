@@ -62,3 +62,18 @@ def test_reference_arm_line_has_the_contract_keys():
     assert set(d["cpu_baseline"]) >= {"value", "unit", "cores", "kind", "sample"}
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_main_arm_fails_loudly_without_a_gpu():
+    # No CPU fallback: without a CUDA device the benchmark prints no result line and exits
+    # with an error.
+    import subprocess
+    import sys
+    torch = __import__("pytest").importorskip("torch")
+    if torch.cuda.is_available():
+        __import__("pytest").skip("a CUDA device is present")
+    r = subprocess.run([sys.executable, "bench.py", "--steps", "3", "--warmup", "3", "--no-stream",
+                        "--no-masked", "--no-beams", "--no-corner", "--no-cpu-baseline"],
+                       cwd=bench.ROOT, capture_output=True, text=True, timeout=300)
+    assert r.returncode != 0
+    assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
