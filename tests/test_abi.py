@@ -473,3 +473,24 @@ def test_bundle_view_rejects_bad_shapes():
     v = xe.View()
     for args in [(0, 4, 512, 10), (4, 0, 512, 10), (4, 4, 0, 10), (4, 4, 512, 0), (200, 1, 512, 10)]:
         assert L.xe_bundle_view(*args, ctypes.byref(v)) == xe.XE_EINVAL, args
+
+
+def test_binding_checks_tensors_before_calling_the_library():
+    # The binding refuses wrong dtypes, layouts, sizes and devices itself (no library call).
+    torch = pytest.importorskip("torch")
+    N, T = 8, 16
+    x = torch.zeros((1, T, N), dtype=torch.uint8)
+    with pytest.raises(TypeError):
+        xe.correlate(x.to(torch.int8), N, T, 1)
+    with pytest.raises(ValueError):
+        xe.correlate(torch.zeros((1, T, 2 * N), dtype=torch.uint8)[:, :, ::2], N, T, 1)   # not contiguous
+    with pytest.raises(ValueError):
+        xe.correlate(x, N, T + 1, 1)                                                       # wrong size
+    with pytest.raises(ValueError):
+        xe.correlate(x, N, T, 1)                                                           # host tensor
+    with pytest.raises(ValueError):
+        xe.correlate_host(x.cuda() if torch.cuda.is_available() else x[:, :1], N, T, 1)
+    with pytest.raises(ValueError):
+        xe.beamform(x, torch.zeros((1, N, 2), dtype=torch.int8), N, T, 1)                # host weights
+    with pytest.raises(ValueError):
+        xe.correlate_masked(x, torch.zeros((1, T, 1), dtype=torch.uint8), N, T, 1)       # host flags
