@@ -234,6 +234,20 @@ def _shape(inp, N, T, C):
         raise ValueError(f"input has {inp.numel()} bytes, expected C*T*N = {C * T * N}")
 
 
+def _device_input(inp, what="input"):
+    if not inp.is_cuda:
+        raise ValueError(f"{what} must be a CUDA tensor")
+
+
+def _int32_out(out, n, on_device, what):
+    """`out` must be a contiguous int32 tensor of n elements on the device (or on the host)."""
+    import torch
+    if out.dtype != torch.int32 or not out.is_contiguous() or bool(out.is_cuda) != on_device:
+        raise ValueError(f"{what} must be a contiguous int32 {'CUDA' if on_device else 'host'} tensor")
+    if out.numel() != n:
+        raise ValueError(f"{what} has {out.numel()} elements, expected {n}")
+
+
 def empty_vis(N: int, C: int = 1, device="cuda"):
     import torch
     return torch.empty((C, n_baselines(N), 2), dtype=torch.int32, device=device)
@@ -246,6 +260,7 @@ def correlate(inp, N: int, T: int, C: int = 1, out=None, algo: str = "auto", str
         raise ValueError("input must be a CUDA tensor (use correlate_host for host buffers)")
     if out is None:
         out = empty_vis(N, C, inp.device)
+    _int32_out(out, C * n_baselines(N) * 2, True, "out")
     rc = load().xe_correlate_async(ctypes.c_void_p(inp.data_ptr()), N, T, C,
                                    ctypes.c_void_p(out.data_ptr()), ALGOS[algo],
                                    _stream_handle(stream))
@@ -262,6 +277,7 @@ def correlate_host(inp, N: int, T: int, C: int = 1, out=None, algo: str = "auto"
     if out is None:
         out = torch.empty((C, n_baselines(N), 2), dtype=torch.int32,
                           pin_memory=inp.is_pinned())
+    _int32_out(out, C * n_baselines(N) * 2, False, "out")
     rc = load().xe_correlate_host(ctypes.c_void_p(inp.data_ptr()), N, T, C,
                                   ctypes.c_void_p(out.data_ptr()), ALGOS[algo])
     _check(rc, "xe_correlate_host")
@@ -281,6 +297,7 @@ def correlate_host_async(inp, N: int, T: int, C: int = 1, out=None, slot: int = 
         raise ValueError("correlate_host_async takes host tensors")
     if out is None:
         out = torch.empty((C, n_baselines(N), 2), dtype=torch.int32, pin_memory=True)
+    _int32_out(out, C * n_baselines(N) * 2, False, "out")
     rc = load().xe_correlate_host_async(ctypes.c_void_p(inp.data_ptr()), N, T, C,
                                         ctypes.c_void_p(out.data_ptr()), slot)
     _check(rc, "xe_correlate_host_async")
@@ -296,6 +313,8 @@ def correlate_batch(jobs, use_graph: bool = False, stream=None):
     arr = (Job * len(jobs))()
     for k, (inp, out, N, T, C) in enumerate(jobs):
         _shape(inp, N, T, C)
+        _device_input(inp)
+        _int32_out(out, C * n_baselines(N) * 2, True, "out")
         arr[k] = Job(inp.data_ptr(), out.data_ptr(), N, C, T)
     rc = load().xe_correlate_batch(arr, len(jobs), 1 if use_graph else 0, _stream_handle(stream))
     _check(rc, "xe_correlate_batch")
@@ -307,6 +326,8 @@ def correlate_accumulate(jobs, stream=None):
     arr = (Job * len(jobs))()
     for k, (inp, out, N, T, C) in enumerate(jobs):
         _shape(inp, N, T, C)
+        _device_input(inp)
+        _int32_out(out, C * n_baselines(N) * 2, True, "out")
         arr[k] = Job(inp.data_ptr(), out.data_ptr(), N, C, T)
     _check(load().xe_correlate_accumulate(arr, len(jobs), _stream_handle(stream)),
            "xe_correlate_accumulate")
@@ -317,8 +338,10 @@ def correlate_noalloc(inp, N: int, T: int, C: int = 1, out=None, stream=None):
     """As correlate(algo="tc"), through the entry point that allocates nothing (its scratch
     is a fixed array inside the library; see include/xe.h for the limits)."""
     _shape(inp, N, T, C)
+    _device_input(inp)
     if out is None:
         out = empty_vis(N, C, inp.device)
+    _int32_out(out, C * n_baselines(N) * 2, True, "out")
     rc = load().xe_correlate_noalloc(ctypes.c_void_p(inp.data_ptr()), N, T, C,
                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(rc, "xe_correlate_noalloc")
@@ -353,6 +376,7 @@ def correlate_masked(inp, flags, N: int, T: int, C: int = 1, encoding: str = "tw
     valid-sample counts n_ij.  flags: uint8 [C, T, ceil(N/8)] validity bits or None (all
     valid); encoding 'twos' or 'offset'.  Returns (vis, counts or None)."""
     _shape(inp, N, T, C)
+    _device_input(inp)
     _flags_shape(flags, N, T, C)
     if out is None:
         out = empty_vis(N, C, inp.device)
@@ -360,6 +384,9 @@ def correlate_masked(inp, flags, N: int, T: int, C: int = 1, encoding: str = "tw
         counts = empty_counts(N, C, inp.device)
     if not with_counts:
         counts = None
+    _int32_out(out, C * n_baselines(N) * 2, True, "out")
+    if counts is not None:
+        _int32_out(counts, C * n_baselines(N), True, "counts")
     rc = load().xe_correlate_masked(
         ctypes.c_void_p(inp.data_ptr()), ctypes.c_void_p(flags.data_ptr() if flags is not None else 0),
         N, T, C, ENCODINGS[encoding], ctypes.c_void_p(out.data_ptr()),
@@ -375,8 +402,12 @@ def correlate_masked_batch(jobs, stream=None):
     arr = (MaskedJob * len(jobs))()
     for k, j in enumerate(jobs):
         _shape(j["in"], j["N"], j["T"], j["C"])
+        _device_input(j["in"])
         _flags_shape(j.get("flags"), j["N"], j["T"], j["C"])
         f, c = j.get("flags"), j.get("counts")
+        _int32_out(j["vis"], j["C"] * n_baselines(j["N"]) * 2, True, "vis")
+        if c is not None:
+            _int32_out(c, j["C"] * n_baselines(j["N"]), True, "counts")
         arr[k] = MaskedJob(j["in"].data_ptr(), f.data_ptr() if f is not None else None,
                            j["vis"].data_ptr(), c.data_ptr() if c is not None else None,
                            j["N"], j["C"], j["T"], ENCODINGS[j.get("encoding", "twos")],
@@ -406,6 +437,7 @@ def correlate_view(inp, view: View, N: int, T: int, C: int = 1, out=None, stream
         raise ValueError("input must be a uint8 CUDA tensor")
     if out is None:
         out = empty_vis(N, C, inp.device)
+    _int32_out(out, C * n_baselines(N) * 2, True, "out")
     rc = load().xe_correlate_view(ctypes.c_void_p(inp.data_ptr()), ctypes.byref(view), N, T, C,
                                   ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(rc, "xe_correlate_view")
@@ -433,6 +465,9 @@ def corner_turn(bundles, n_cyl: int, n_freq: int, n_in: int, T: int, frames=None
     N = n_cyl * n_in
     if frames is None:
         frames = torch.empty((n_freq, T, N), dtype=torch.uint8, device=bundles.device)
+    if frames.dtype != torch.uint8 or not frames.is_cuda or not frames.is_contiguous() or \
+            frames.numel() != bundles.numel():
+        raise ValueError("frames must be a contiguous uint8 CUDA tensor of n_freq * T * N bytes")
     ps = torch.empty((n_freq, N, 2), dtype=torch.int32, device=bundles.device) if presums else None
     rc = load().xe_corner_turn(ctypes.c_void_p(bundles.data_ptr()), n_cyl, n_freq, n_in, T,
                                ctypes.c_void_p(frames.data_ptr()),
@@ -451,6 +486,7 @@ def beamform(inp, weights, N: int, T: int, C: int = 1, out=None, stream=None):
     weights [B, N, 2] -> int32 [C, T, B, 2] (async on stream)."""
     import torch
     _shape(inp, N, T, C)
+    _device_input(inp)
     if weights.dtype != torch.int8 or not weights.is_cuda or not weights.is_contiguous():
         raise ValueError("weights must be a contiguous int8 CUDA tensor [B, N, 2]")
     if weights.numel() % (2 * N) != 0:
@@ -458,6 +494,7 @@ def beamform(inp, weights, N: int, T: int, C: int = 1, out=None, stream=None):
     B = weights.numel() // (2 * N)
     if out is None:
         out = empty_beams(T, B, C, inp.device)
+    _int32_out(out, C * T * B * 2, True, "out")
     rc = load().xe_beamform(ctypes.c_void_p(inp.data_ptr()), N, T, C, ctypes.c_void_p(weights.data_ptr()),
                             B, ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(rc, "xe_beamform")

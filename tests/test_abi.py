@@ -494,3 +494,10 @@ def test_binding_checks_tensors_before_calling_the_library():
         xe.beamform(x, torch.zeros((1, N, 2), dtype=torch.int8), N, T, 1)                # host weights
     with pytest.raises(ValueError):
         xe.correlate_masked(x, torch.zeros((1, T, 1), dtype=torch.uint8), N, T, 1)       # host flags
+    B = N * (N + 1) // 2
+    for bad in (torch.zeros(2 * B - 1, dtype=torch.int32), torch.zeros(2 * B, dtype=torch.int64),
+                torch.zeros((2, B), dtype=torch.int32).t()):
+        with pytest.raises(ValueError):
+            xe.correlate_host(x, N, T, 1, out=bad)                                         # bad outputs
+    with pytest.raises(ValueError):
+        xe.correlate_batch([(x, torch.zeros((1, B, 2), dtype=torch.int32), N, T, 1)])      # host input
