@@ -200,11 +200,11 @@ int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs,
 
 /* Dump the plan the scheduler builds for a batch, for a given CTA count, schedule
  * (-1 = the default choice; 0 stream-K, 1 equal k-split, 2 full waves + stream-K tail,
- * 3 longest-first, 4 tile pairs sharing a column block on 2-CTA clusters with equal k-split,
- * 5 k-aligned parts of about equal weighted cost, longest first; the default for masked
- * calls with counts, whose count jobs weigh less) and tile width (0 = default, 128 or 256).  Writes into out[0..cap):
+ * 3 longest-first, 4 k-aligned parts of about equal weighted cost, longest first; the
+ * default for masked calls with counts, whose count jobs weigh less) and tile width
+ * (0 = default, 128 or 256).  Writes into out[0..cap):
  * {n_tiles, n_segments, n_cta, n_partial}, then per tile {job, chan, i0, j0, nj, kblocks},
- * then per segment {cta, tile (-1: partner-only), k_lo, k_hi, slot, multicast}.  Returns the number of int32 values the
+ * then per segment {cta, tile, k_lo, k_hi, slot}.  Returns the number of int32 values the
  * dump needs (nothing is written when cap is smaller), or a negative XE_* code.
  * Pure host computation. */
 int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int n_cta,
@@ -411,14 +411,14 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *   "exact_chunk_t"  samples summed by one f32 tensor-memory accumulation before the
  *                    partial sum is moved to int32 (64 .. 131072, default 131072);
  *   "n_cta"          persistent CTAs per launch (0 = one per SM, the default);
- *   "sched"          triangle schedule, -1 = automatic (default), 0..5 as in xe_plan_dump;
+ *   "sched"          triangle schedule, -1 = automatic (default), 0..4 as in xe_plan_dump;
  *   "tile_n"         tile width 0 = automatic (default), 128 or 256;
  *   "autotune"       1 = time every (tile width, schedule) candidate the first time a
  *                    batch shape is correlated and keep the fastest for that shape;
  *   "timing"         1 = record device times of each call (see xe_last_timing);
- *   "count_weight"   cost of a count job's k-iteration (two sample blocks) in schedule 5,
+ *   "count_weight"   cost of a count job's k-iteration (two sample blocks) in schedule 4,
  *                    percent of a data job's (1 .. 100, default 75);
- *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 5, percent of
+ *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 4, percent of
  *                    a whole tile (0 .. 100, default 2);
  *   "host_chunk_t"   samples per chunk of the host-buffer entry points' copy/correlate
  *                    pipeline (0 = one copy then one correlation; else a multiple of 64;
@@ -439,9 +439,8 @@ int xe_device_status(void *stream);
  * XE_ENODEV. */
 int xe_release_stream(void *stream);
 
-/* Streaming multiprocessors of the current device, and how many 2-CTA clusters of the
- * clustered correlation kernel can be resident at once (0 if none).  Returns an XE_* code. */
-int xe_device_info(int *n_sm, int *max_clusters);
+/* Streaming multiprocessors of the current device.  Returns an XE_* code. */
+int xe_device_info(int *n_sm);
 
 /* Bit pattern of the small integer v in [-16, 16] as an MMA operand: e4m3 when
  * elem_bytes == 1, f16 when elem_bytes == 2.  Host-only; for tests of the encoder. */

@@ -77,7 +77,6 @@ struct TuneCfg {
 };
 
 struct HostPlan {
-    bool clustered = false;       // segments are laid out for the 2-CTA clustered kernel
     bool pair_exchange = false;   // every split tile has 2 parts and every CTA 1 segment
     std::vector<Tile> tiles;
     std::vector<Seg> segs;
@@ -233,7 +232,6 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
 }
 
 static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weight) {
-    p.clustered = false;
     const int n = int(p.tiles.size());
     std::vector<std::vector<Seg>> per(static_cast<size_t>(G));
     if (sched == kSchedWeighted) {
@@ -275,65 +273,12 @@ static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weig
         for (int b = 0; b < G; ++b) per[size_t(b)].reserve(size_t(count[size_t(b)]));
         for (int t = 0; t < n; ++t)
             per[size_t(cta_of[size_t(t)])].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
-    } else if (sched == kSchedPairSplit) {
-        // Pairs of tiles that share (job, channel, column block, width, length) run on the two
-        // CTAs of a cluster and share their B planes; the remaining tiles pair up without
-        // sharing (equal lengths), and a last odd tile runs beside a partner-only segment.
-        std::map<std::vector<int>, std::vector<int>> groups;
-        std::vector<std::vector<int>> order;
-        for (int t = 0; t < n; ++t) {
-            const Tile &tl = p.tiles[size_t(t)];
-            std::vector<int> key{tl.job, tl.chan, tl.j0, tl.nj, tl.kblocks};
-            auto it = groups.find(key);
-            if (it == groups.end()) {
-                order.push_back(key);
-                groups[key] = {t};
-            } else {
-                it->second.push_back(t);
-            }
-        }
-        struct Unit { int a, b, mc; };
-        std::vector<Unit> units;
-        std::map<int, std::vector<int>> singles;   // by kblocks
-        for (const auto &key : order) {
-            const std::vector<int> &g = groups[key];
-            size_t k = 0;
-            for (; k + 1 < g.size(); k += 2) units.push_back(Unit{g[k], g[k + 1], 1});
-            if (k < g.size()) singles[p.tiles[size_t(g[k])].kblocks].push_back(g[k]);
-        }
-        for (auto &kv : singles) {
-            size_t k = 0;
-            for (; k + 1 < kv.second.size(); k += 2) units.push_back(Unit{kv.second[k], kv.second[k + 1], 0});
-            if (k < kv.second.size()) units.push_back(Unit{kv.second[k], -1, 0});
-        }
-        std::sort(units.begin(), units.end(), [](const Unit &x, const Unit &y) { return x.a < y.a; });
-        const int n_cl = std::max(1, G / 2);
-        const int U = int(units.size());
-        int s = U < n_cl ? std::max(1, n_cl / U) : 1;
-        int min_kb = 1 << 30;
-        for (const Tile &t : p.tiles) min_kb = std::min(min_kb, t.kblocks);
-        s = std::min(s, std::max(1, min_kb));
-        const int64_t n_items = int64_t(U) * s;
-        const int g = int(std::min<int64_t>(n_cl, n_items));
-        int64_t item = 0;
-        for (const Unit &u : units)
-            for (int k = 0; k < s; ++k, ++item) {
-                const int kb = p.tiles[size_t(u.a)].kblocks;
-                const int lo = int(int64_t(k) * kb / s), hi = int(int64_t(k + 1) * kb / s);
-                if (hi <= lo) continue;
-                const int cl = int(item % g);
-                per[size_t(2 * cl)].push_back(Seg{u.a, lo, hi, -1, u.mc});
-                per[size_t(2 * cl + 1)].push_back(Seg{u.b, lo, hi, -1, u.mc});
-            }
-        p.clustered = true;
-        G = 2 * g;
     } else {
         stream_k(p.tiles, 0, n, G, per);
     }
-    // Drop trailing CTAs without work (clusters stay whole); build the CSR lists.
+    // Drop trailing CTAs without work; build the CSR lists.
     int used = G;
-    if (!p.clustered)
-        while (used > 1 && per[size_t(used - 1)].empty()) --used;
+    while (used > 1 && per[size_t(used - 1)].empty()) --used;
     p.n_cta = used;
     p.segs.clear();
     p.seg_off.assign(size_t(used) + 1, 0);
@@ -417,15 +362,14 @@ static TuneCfg heuristic(const std::vector<JobShape> &jobs, int eb, int n_sm) {
 static bool build_plan(const std::vector<JobShape> &jobs, int eb, const TuneCfg &cfg, HostPlan &p) {
     enumerate_tiles(jobs, eb, cfg.tile_n, p.tiles);
     if (p.tiles.empty()) return false;
-    int G = std::max(1, cfg.n_cta);
-    if (cfg.sched == kSchedPairSplit) G = std::max(2, G & ~1);
+    const int G = std::max(1, cfg.n_cta);
     std::vector<int> weight;
     for (const JobShape &j : jobs) weight.push_back(std::max(1, j.weight));
     schedule(p, G, cfg.sched, weight);
     if (!finalize_parts(p)) return false;
     // The symmetric two-part exchange waits for the partner part, so it is used only when
     // both parts are the only work of their CTAs (all of them resident at once).
-    bool pe = !p.clustered;
+    bool pe = true;
     for (const Tile &t : p.tiles) pe = pe && (t.n_parts == 0 || t.n_parts == 2);
     for (int b = 0; b < p.n_cta && pe; ++b) pe = p.seg_off[size_t(b) + 1] - p.seg_off[size_t(b)] == 1;
     p.pair_exchange = pe;
@@ -481,7 +425,6 @@ constexpr int kHostSlots = XE_HOST_SLOTS + 1;   // the last one serves xe_correl
 struct LaunchRec {
     int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor
     int eb;
-    bool clustered;               // kind 1: the 2-CTA clustered kernel
     bool masked;                  // kind 0: the masking variant of the staging kernel
     JobTable jt;
     PlanDev pd;
@@ -841,14 +784,6 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 auto it = d->tuned.find(shape_key(shapes, eb));
                 cfg = it != d->tuned.end() ? it->second : heuristic(shapes, eb, d->n_sm);
             }
-            // Count jobs run in the plain kernel only (the cluster kernel splits the B planes
-            // of a stage between the pair and does not form their Re-only sums).
-            if (cfg.sched == kSchedPairSplit && jt.n_jobs > ng) cfg.sched = kSchedSplit;
-            if (cfg.sched == kSchedPairSplit) {
-                const int mc = tc_max_clusters();
-                if (mc <= 0) cfg.sched = kSchedSplit;              // clusters unavailable
-                else cfg.n_cta = std::min(cfg.n_cta, 2 * mc);
-            }
             g_last_cfg = cfg;
             DevPlan *p = nullptr;
             const int rc = get_plan(d, shapes, eb, cfg, &p);
@@ -859,7 +794,6 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             max_counters = std::max(max_counters, p->host.tiles.size() * sizeof(int));
             LaunchRec tc = st;
             tc.kind = 1;
-            tc.clustered = p->host.clustered;
             PlanDev &pd = tc.pd;
             pd.tiles = p->d_tiles;
             pd.segs = p->d_segs;
@@ -904,7 +838,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
 
 static cudaError_t enqueue(const LaunchRec &r, cudaStream_t s) {
     if (r.kind == 0) return launch_stage(r.jt, r.eb, s, r.masked);
-    if (r.kind == 1) return launch_tc(r.jt, r.pd, r.eb, s, r.clustered);
+    if (r.kind == 1) return launch_tc(r.jt, r.pd, r.eb, s);
     return launch_imma(r.jt, s);
 }
 
@@ -920,7 +854,7 @@ static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
         p.blockDim = dim3(256);
         p.sharedMemBytes = unsigned(stage_smem_bytes(r.eb, r.masked));
     } else if (r.kind == 1) {
-        p.func = const_cast<void *>(tc_kernel_fn(r.eb, r.clustered));
+        p.func = const_cast<void *>(tc_kernel_fn(r.eb));
         p.gridDim = dim3(unsigned(r.pd.n_cta));
         p.blockDim = dim3(kTcThreads);
         p.sharedMemBytes = unsigned(tc_smem_bytes());
@@ -1580,7 +1514,7 @@ int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jo
     HostPlan p;
     int rc = plan_from_args(N, T, n_chan, n_jobs, n_cta, sched, tile_n, p);
     if (rc) return rc;
-    const int64_t need = 4 + 6 * int64_t(p.tiles.size()) + 6 * int64_t(p.segs.size());
+    const int64_t need = 4 + 6 * int64_t(p.tiles.size()) + 5 * int64_t(p.segs.size());
     if (!out || cap < need) return need;
     int64_t k = 0;
     out[k++] = int32_t(p.tiles.size());
@@ -1603,7 +1537,6 @@ int64_t xe_plan_dump(const int *N, const int64_t *T, const int *n_chan, int n_jo
             out[k++] = s.k_lo;
             out[k++] = s.k_hi;
             out[k++] = s.slot;
-            out[k++] = s.multicast;
         }
     return need;
 }
@@ -1633,13 +1566,12 @@ int xe_release_stream(void *stream) { return release_stream_scratch(reinterpret_
 
 uint32_t xe_debug_operand_code(int v, int elem_bytes) { return operand_code(v, elem_bytes); }
 
-int xe_device_info(int *n_sm, int *max_clusters) {
+int xe_device_info(int *n_sm) {
     std::lock_guard<std::mutex> lk(g_mu);
     Device *d = nullptr;
     int rc = get_device(&d);
     if (rc) return rc;
     if (n_sm) *n_sm = d->n_sm;
-    if (max_clusters) *max_clusters = tc_max_clusters();
     return XE_OK;
 }
 

@@ -103,16 +103,12 @@ struct Tile {
     int part_off;             // their workspace slots: tile_slots[part_off .. part_off + n_parts)
 };
 
-// A contiguous k-range of one tile processed by one CTA.  In the clustered kernel the two
-// CTAs of a cluster walk segment lists of equal shape in lockstep: `multicast` segments of
-// the pair share their column block (each CTA fetches one B plane for both), and a segment
-// with tile < 0 only keeps the pipeline handshake going for the partner (k_hi - k_lo stages).
+// A contiguous k-range of one tile processed by one CTA.
 struct Seg {
     int tile;
     int k_lo;
     int k_hi;
     int slot;                 // workspace slot if the segment is partial, else -1
-    int multicast;            // clustered kernel only: 1 = B planes shared with the partner
 };
 
 // Device-resident plan of one persistent launch: CTA b processes segs[seg_off[b] ..
@@ -138,11 +134,10 @@ enum Sched : int {
     kSchedSplit = 1,          // each tile split into s equal k-parts, parts dealt round-robin
     kSchedHybrid = 2,         // whole tiles in full waves, the last partial wave stream-K
     kSchedLPT = 3,            // whole tiles, longest first, to the least-loaded CTA
-    kSchedPairSplit = 4,      // clustered kernel: tile pairs sharing a column block, k-split
-    kSchedWeighted = 5,       // tiles cut into k-aligned parts of about equal weighted cost
+    kSchedWeighted = 4,       // tiles cut into k-aligned parts of about equal weighted cost
                               // (count jobs weigh less than data jobs), longest part first
                               // to the least-loaded CTA
-    kNumSched = 6,
+    kNumSched = 5,
 };
 
 constexpr int64_t kWsSlotElems = 2LL * kBN * kBM;  // re and im planes, [col][row] int32
@@ -190,9 +185,7 @@ int64_t corner_partial_elems(int n_cyl, int n_freq, int n_in, int64_t T);
 // Kernel launchers (xe_stage.cu, xe_tc.cu, xe_imma.cu).  `masked` selects the masking
 // variant of the e4m3 staging kernel (any job with kModeMasked).
 cudaError_t launch_stage(const JobTable &jt, int elem_bytes, cudaStream_t s, bool masked = false);
-cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
-                      bool clustered = false);
-int tc_max_clusters();
+cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s);
 cudaError_t launch_imma(const JobTable &jt, cudaStream_t s);
 int64_t imma_blocks(int N, int C);
 int tc_smem_bytes();
@@ -200,7 +193,7 @@ const void *stage_kernel_fn(int elem_bytes, bool masked = false);
 unsigned stage_grid(const JobTable &jt, int elem_bytes, bool masked = false);
 int stage_smem_bytes(int elem_bytes, bool masked = false);
 cudaError_t stage_prepare();
-const void *tc_kernel_fn(int elem_bytes, bool clustered = false);
+const void *tc_kernel_fn(int elem_bytes);
 const void *imma_kernel_fn();
 cudaError_t tc_prepare();
 

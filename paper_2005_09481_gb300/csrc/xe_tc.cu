@@ -115,13 +115,7 @@ __device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, 
     __syncwarp();
 }
 
-// MC = the clustered variant: the two CTAs of a cluster walk equally shaped segment lists
-// in lockstep; for `multicast` segments CTA rank r fetches B plane r (re or im) of the shared
-// column block for both CTAs, so each CTA reads 2/3 of the B bytes it would read alone.
-// Each CTA's MMA completion for a stage arrives on the stage's `empty` barrier of BOTH CTAs
-// (multicast commit, barrier count 2), so a producer refills a stage -- its own copies and
-// its multicast into the partner -- only after both tensor cores have finished reading it.
-template <int EB, bool MC>
+template <int EB>
 __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan) {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>(
@@ -143,7 +137,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {
             mbar_init(&full[s], 1);
-            mbar_init(&empty[s], MC ? 2 : 1);
+            mbar_init(&empty[s], 1);
         }
         mbar_init(acc_full, 1);
         mbar_init(acc_empty, 128);
@@ -158,16 +152,14 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     tc_fence_before();
     __syncthreads();
     tc_fence_after();
-    if (MC) cluster_sync();     // the partner's barriers are initialised before any remote use
     const uint32_t tmem = *tmem_slot;
-    const uint32_t rank = MC ? cluster_ctarank() : 0u;   // which B plane this CTA multicasts
 
     // This CTA's work: segments [q0, q1) of the plan, each a k-range of one tile.
     const int q0 = plan.seg_off[blockIdx.x];
     const int q1 = plan.seg_off[blockIdx.x + 1];
     // A CTA whose only segment is one part of a pair-exchanged tile finishes it with eight
     // warps: the producer and MMA warps are idle by then, and two more warps wait for it.
-    const bool wide = !MC && plan.pair_exchange && q1 - q0 == 1 && plan.segs[q0].slot >= 0;
+    const bool wide = plan.pair_exchange && q1 - q0 == 1 && plan.segs[q0].slot >= 0;
     constexpr uint32_t kFmt = 0;  // E4M3 for kind::f8f6f4, F16 for kind::f16
 
     if (warp == 4) {
@@ -182,10 +174,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
             int64_t fills = 0;
             bool ok = true;
             // Test hook: issue nothing, so the MMA warp's bounded wait runs out.
-            for (int q = (!MC && plan.inject_stall) ? q1 : q0; ok && q < q1; ++q) {
+            for (int q = plan.inject_stall ? q1 : q0; ok && q < q1; ++q) {
                 const Seg sg = plan.segs[q];
-                const bool null_seg = MC && sg.tile < 0;
-                const Tile tl = plan.tiles[null_seg ? 0 : sg.tile];
+                const Tile tl = plan.tiles[sg.tile];
                 const JobDev &jb = jt.jobs[tl.job];
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
@@ -194,12 +185,6 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                         set_status(plan.status, kStatusTimeoutProducer);
                         ok = false;
                         break;
-                    }
-                    if (null_seg) {
-                        mbar_arrive(&full[stage]);     // nothing to load: complete the phase
-                        ++fills;
-                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-                        continue;
                     }
                     uint8_t *st = smem + stage * kStageBytes;
                     const uint8_t *pre = pl + (k * 2 + 0) * jb.n_pad * int64_t(kRowBytes);
@@ -211,20 +196,13 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                         const uint8_t *fim = fre + int64_t(jb.n_pad) * kRowBytes;
                         bulk_prefetch_l2(fre + int64_t(tl.i0) * kRowBytes, kAPlane);
                         bulk_prefetch_l2(fim + int64_t(tl.i0) * kRowBytes, kAPlane);
-                        if (!(MC && sg.multicast) || rank == 0) bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
-                        if (!(MC && sg.multicast) || rank == 1) bulk_prefetch_l2(fim + int64_t(tl.j0) * kRowBytes, bbytes);
+                        bulk_prefetch_l2(fre + int64_t(tl.j0) * kRowBytes, bbytes);
+                        bulk_prefetch_l2(fim + int64_t(tl.j0) * kRowBytes, bbytes);
                     }
                     bulk_g2s(st, pre + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
                     bulk_g2s(st + kAPlane, pim + int64_t(tl.i0) * kRowBytes, kAPlane, &full[stage]);
-                    if (MC && sg.multicast) {
-                        // B plane `rank` of the shared column block, into both CTAs.
-                        const uint8_t *pb = (rank == 0 ? pre : pim) + int64_t(tl.j0) * kRowBytes;
-                        bulk_g2s_multicast(st + 2 * kAPlane + rank * kBPlane, pb, bbytes, &full[stage], 0x3);
-                    } else {
-                        bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
-                        bulk_g2s(st + 2 * kAPlane + kBPlane, pim + int64_t(tl.j0) * kRowBytes, bbytes,
-                                 &full[stage]);
-                    }
+                    bulk_g2s(st + 2 * kAPlane, pre + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
+                    bulk_g2s(st + 2 * kAPlane + kBPlane, pim + int64_t(tl.j0) * kRowBytes, bbytes, &full[stage]);
                     ++fills;
                     if (++stage == kStages) { stage = 0; ph ^= 1u; }
                 }
@@ -250,23 +228,10 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
             const uint32_t d_re = tmem, d_im = tmem + 256;
             for (int q = q0; ok && q < q1; ++q) {
                 const Seg sg = plan.segs[q];
-                if (MC && sg.tile < 0) {
-                    // Partner-only segment: pass each stage straight back to the producer.
-                    for (int64_t k = sg.k_lo; k < sg.k_hi; ++k) {
-                        if (!mbar_wait(&full[stage], ph, status)) {
-                            set_status(plan.status, kStatusTimeoutMma);
-                            ok = false;
-                            break;
-                        }
-                        mma_commit_multicast(&empty[stage], 0x3);
-                        if (++stage == kStages) { stage = 0; ph ^= 1u; }
-                    }
-                    continue;
-                }
                 const Tile tl = plan.tiles[sg.tile];
-                // Count job (plain kernel only): its two slots hold the validity of two
-                // consecutive sample blocks, and only the Re accumulator is formed.
-                const bool re_only = !MC && (jt.jobs[tl.job].mode & kModeCount);
+                // Count job: its two slots hold the validity of two consecutive sample
+                // blocks, and only the Re accumulator is formed.
+                const bool re_only = (jt.jobs[tl.job].mode & kModeCount) != 0;
                 const uint32_t idesc = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, false);
                 const uint32_t idesc_neg = idesc_dense(kBM, uint32_t(tl.nj), kFmt, kFmt, true);
                 if (!mbar_wait(acc_empty, acc_ph ^ 1u, status)) {
@@ -315,8 +280,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                                 mma_f16(d_im, a_re, b_im, idesc_neg, 1u);
                             }
                         }
-                        if (MC) mma_commit_multicast(&empty[stage], 0x3);
-                        else mma_commit(&empty[stage]);
+                        mma_commit(&empty[stage]);
                         if (++stage == kStages) { stage = 0; ph ^= 1u; }
                     }
                 };
@@ -338,7 +302,6 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         const uint32_t lane_base = uint32_t(warp * 32) << 16;
         for (int q = q0; q < q1; ++q) {
             const Seg sg = plan.segs[q];
-            if (MC && sg.tile < 0) continue;      // partner-only segment: nothing to drain
             const Tile tl = plan.tiles[sg.tile];
             const JobDev &jb = jt.jobs[tl.job];
             if (threadIdx.x == 0) {
@@ -365,7 +328,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                     }
                     store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + cc, re, im, jt.accumulate | jb.accumulate, epi_stage);
                 }
-            } else if (!MC && plan.pair_exchange) {
+            } else if (plan.pair_exchange) {
                 // Two-part tile, both parts running now on two CTAs: part p finalises column
                 // half p.  Publish my share of the partner's half, count myself in, wait
                 // (bounded) for the partner's share of mine, then add it to my own sums.
@@ -616,16 +579,6 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
 
     tc_fence_before();
     __syncthreads();
-    if (MC) {
-        // Both CTAs are done with each other's barriers and shared memory before either exits;
-        // after an abort, give multicast copies already in flight time to land.
-        cluster_sync();
-        if (*status != 0) {
-            const long long t0 = clock64();
-            while (clock64() - t0 < 4000000LL) {}
-            cluster_sync();
-        }
-    }
     if (warp == 5) {
         tc_fence_after();
         tmem_dealloc(tmem, 512);
@@ -635,22 +588,13 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
 template <int EB>
 __global__ void __launch_bounds__(kTcThreads, 1)
     tc_kernel(const __grid_constant__ JobTable jt, const __grid_constant__ PlanDev plan) {
-    tc_body<EB, false>(jt, plan);
-}
-
-template <int EB>
-__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kTcThreads, 1)
-    tc_mc_kernel(const __grid_constant__ JobTable jt, const __grid_constant__ PlanDev plan) {
-    tc_body<EB, true>(jt, plan);
+    tc_body<EB>(jt, plan);
 }
 
 int tc_smem_bytes() { return kTcSmem; }
 
 
-const void *tc_kernel_fn(int elem_bytes, bool clustered) {
-    if (clustered)
-        return elem_bytes == 1 ? reinterpret_cast<const void *>(tc_mc_kernel<1>)
-                               : reinterpret_cast<const void *>(tc_mc_kernel<2>);
+const void *tc_kernel_fn(int elem_bytes) {
     return elem_bytes == 1 ? reinterpret_cast<const void *>(tc_kernel<1>)
                            : reinterpret_cast<const void *>(tc_kernel<2>);
 }
@@ -666,68 +610,30 @@ cudaError_t tc_prepare() {
     if (e != cudaSuccess) return e;
     e = cudaFuncSetAttribute(tc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
     if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(tc_mc_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(tc_mc_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmem);
-    if (e != cudaSuccess) return e;
     if (dev >= 0 && dev < 64) done_dev[dev] = 1;
     return cudaSuccess;
 }
 
-// Clusters of two tensor-core CTAs that can be resident at once (0 if the query fails).
-int tc_max_clusters() {
-    static int cached[64] = {0};
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return 0;
-    if (dev >= 0 && dev < 64 && cached[dev] > 0) return cached[dev];
-    if (tc_prepare() != cudaSuccess) return 0;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2 * 256);
-    cfg.blockDim = dim3(kTcThreads);
-    cfg.dynamicSmemBytes = kTcSmem;
-    cudaLaunchAttribute attr;
-    attr.id = cudaLaunchAttributeClusterDimension;
-    attr.val.clusterDim.x = 2;
-    attr.val.clusterDim.y = 1;
-    attr.val.clusterDim.z = 1;
-    cfg.attrs = &attr;
-    cfg.numAttrs = 1;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, reinterpret_cast<const void *>(tc_mc_kernel<1>), &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    if (dev >= 0 && dev < 64) cached[dev] = n;
-    return n;
-}
-
-cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s,
-                      bool clustered) {
+cudaError_t launch_tc(const JobTable &jt, const PlanDev &plan, int elem_bytes, cudaStream_t s) {
     if (plan.n_cta <= 0 || plan.n_tiles <= 0) return cudaSuccess;
-    if (clustered && (plan.n_cta & 1)) return cudaErrorInvalidValue;
     cudaError_t e = tc_prepare();
     if (e != cudaSuccess) return e;
-    if (clustered) {
-        if (elem_bytes == 1) tc_mc_kernel<1><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
-        else tc_mc_kernel<2><<<plan.n_cta, kTcThreads, kTcSmem, s>>>(jt, plan);
-    } else {
-        // Programmatic dependent launch: the grid is set up while the staging kernel runs
-        // and its CTAs start on SMs as the staging blocks leave them; only the producer
-        // thread, which reads the planes, waits for the staging grid to complete.
-        cudaLaunchConfig_t cfg = {};
-        cfg.gridDim = dim3(unsigned(plan.n_cta));
-        cfg.blockDim = dim3(kTcThreads);
-        cfg.dynamicSmemBytes = size_t(kTcSmem);
-        cfg.stream = s;
-        cudaLaunchAttribute attr[1];
-        attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-        attr[0].val.programmaticStreamSerializationAllowed = 1;
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-        e = elem_bytes == 1 ? cudaLaunchKernelEx(&cfg, tc_kernel<1>, jt, plan)
-                            : cudaLaunchKernelEx(&cfg, tc_kernel<2>, jt, plan);
-        if (e != cudaSuccess) return e;
-    }
+    // Programmatic dependent launch: the grid is set up while the staging kernel runs and its
+    // CTAs start on SMs as the staging blocks leave them; only the producer thread, which
+    // reads the planes, waits for the staging grid to complete.
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(unsigned(plan.n_cta));
+    cfg.blockDim = dim3(kTcThreads);
+    cfg.dynamicSmemBytes = size_t(kTcSmem);
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    e = elem_bytes == 1 ? cudaLaunchKernelEx(&cfg, tc_kernel<1>, jt, plan)
+                        : cudaLaunchKernelEx(&cfg, tc_kernel<2>, jt, plan);
+    if (e != cudaSuccess) return e;
     return cudaGetLastError();
 }
 

@@ -86,7 +86,7 @@ def load():
             "xe_plan_dump": ([p, p, p, i32, i32, i32, i32, p, i64], i64),
             "xe_last_config": ([p, p, p], i32),
             "xe_peak_probe": ([i32, p, p], i32),
-            "xe_device_info": ([p, p], i32),
+            "xe_device_info": ([p], i32),
             "xe_stream_open": ([p, p], i32),
             "xe_stream_admit": ([p, i32], i32),
             "xe_stream_evict": ([p, i32], i32),
@@ -171,10 +171,10 @@ def peak_probe(kind: str, with_aux: bool = False):
 
 
 def device_info():
-    """(SM count, resident 2-CTA clusters of the clustered kernel)."""
-    a, b = ctypes.c_int(), ctypes.c_int()
-    _check(load().xe_device_info(ctypes.byref(a), ctypes.byref(b)), "xe_device_info")
-    return a.value, b.value
+    """SM count of the current device."""
+    a = ctypes.c_int()
+    _check(load().xe_device_info(ctypes.byref(a)), "xe_device_info")
+    return a.value
 
 
 def operand_code(v: int, elem_bytes: int) -> int:
@@ -193,12 +193,12 @@ def plan_stats(shapes, n_cta: int):
     return a.value, b.value, c.value
 
 
-SCHEDULES = {"stream_k": 0, "split": 1, "hybrid": 2, "lpt": 3, "pair_split": 4}
+SCHEDULES = {"stream_k": 0, "split": 1, "hybrid": 2, "lpt": 3, "weighted": 4}
 
 
 def plan_dump(shapes, n_cta: int, sched: int = -1, tile_n: int = 0):
     """Host-side plan for shapes [(N, T, C), ...]: dict with 'tiles' (job, chan, i0, j0, nj,
-    kblocks) rows, 'segs' (cta, tile, k_lo, k_hi, slot, multicast) rows, 'n_cta', 'n_partial'."""
+    kblocks) rows, 'segs' (cta, tile, k_lo, k_hi, slot) rows, 'n_cta', 'n_partial'."""
     import numpy as np
     n = len(shapes)
     Ns = (ctypes.c_int * n)(*[s[0] for s in shapes])
@@ -213,7 +213,7 @@ def plan_dump(shapes, n_cta: int, sched: int = -1, tile_n: int = 0):
     _check(0 if got == need else int(got), "xe_plan_dump")
     nt, ns = int(buf[0]), int(buf[1])
     tiles = buf[4:4 + 6 * nt].reshape(nt, 6)
-    segs = buf[4 + 6 * nt:4 + 6 * nt + 6 * ns].reshape(ns, 6)
+    segs = buf[4 + 6 * nt:4 + 6 * nt + 5 * ns].reshape(ns, 5)
     return {"tiles": tiles, "segs": segs, "n_cta": int(buf[2]), "n_partial": int(buf[3])}
 
 

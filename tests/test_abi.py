@@ -243,10 +243,8 @@ def _check_plan(shapes, n_cta, sched, tile_n):
     seen = {t: np.zeros(int(tiles[t][5]), np.int32) for t in range(len(tiles))}
     slots = []
     per_tile = {}
-    for (cta, t, lo, hi, slot, mc) in segs:
-        assert 0 <= cta < d["n_cta"] <= n_cta and lo < hi
-        if t < 0:
-            continue                                   # partner-only segment
+    for (cta, t, lo, hi, slot) in segs:
+        assert 0 <= cta < d["n_cta"] <= n_cta and lo < hi and 0 <= t < len(tiles)
         seen[int(t)][lo:hi] += 1
         per_tile.setdefault(int(t), []).append(int(slot))
     for t, v in seen.items():
@@ -261,7 +259,7 @@ def _check_plan(shapes, n_cta, sched, tile_n):
     return d
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("tile_n", [128, 256])
 def test_schedules_cover_every_tile_and_k_once(sched, tile_n):
     for shapes, n_cta in [([(2048, 32768, 1)], 152), ([(300, 1000, 3)], 7), ([(100, 64, 1)], 152),
@@ -308,31 +306,15 @@ def test_hybrid_schedule_full_waves_whole():
     assert whole >= (1152 // 152) * 152            # full waves are whole tiles
 
 
-@pytest.mark.parametrize("shapes,n_cta", [([(2048, 32768, 1)], 152), ([(300, 1000, 3)], 8),
-                                          ([(256, 4096, 2), (512, 8192, 1), (130, 700, 1)], 20),
-                                          ([(1024, 8192, 1)] * 4, 152), ([(100, 64, 1)], 152)])
-def test_clustered_schedule_pairs_walk_in_lockstep(shapes, n_cta):
-    d = _check_plan(shapes, n_cta, 4, 256)
-    tiles, segs = d["tiles"], d["segs"]
-    assert d["n_cta"] % 2 == 0
-    by_cta = {}
-    for row in segs:
-        by_cta.setdefault(int(row[0]), []).append(row)
-    for c in range(0, d["n_cta"], 2):
-        a, b = by_cta.get(c, []), by_cta.get(c + 1, [])
-        assert len(a) == len(b)
-        for sa, sb in zip(a, b):
-            assert (sa[2], sa[3], sa[5]) == (sb[2], sb[3], sb[5])     # same k-range, same sharing
-            assert sa[1] >= 0
-            if sa[5]:                                                   # shared column block
-                ta, tb = tiles[sa[1]], tiles[sb[1]]
-                assert (ta[0], ta[1], ta[3], ta[4], ta[5]) == (tb[0], tb[1], tb[3], tb[4], tb[5])
-                assert ta[2] != tb[2]
-            elif sb[1] >= 0:
-                assert tiles[sa[1]][5] == tiles[sb[1]][5]
-    if shapes == [(2048, 32768, 1)]:
-        assert d["n_cta"] == 144                                        # 36 units x 2 k-parts
-        assert (segs[:, 5] == 1).sum() == 112                          # 28 shared pairs
+def test_schedule_options_are_the_five_single_cta_schedules():
+    # Schedules 0..4 exist; there is no clustered (multi-CTA) variant any more.
+    for sched in range(5):
+        xe.set_option("sched", sched)
+    xe.set_option("sched", -1)
+    with pytest.raises(xe.XeError):
+        xe.set_option("sched", 5)
+    with pytest.raises(xe.XeError):
+        xe.plan_dump([(256, 1024, 1)], 8, 5, 256)
 
 
 def test_plain_c_program_links_and_calls_the_library(tmp_path):

@@ -55,7 +55,7 @@ def test_uneven_batch_equals_oracle_and_solo(xe):
         np.testing.assert_array_equal(g, solo.cpu().numpy())
 
 
-@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4, 5])
+@pytest.mark.parametrize("sched", [0, 1, 2, 3, 4])
 @pytest.mark.parametrize("tile_n", [128, 256])
 def test_every_schedule_and_tile_width_is_exact(xe, sched, tile_n):
     shapes = [(300, 1000, 2), (520, 2000, 1), (64, 64, 1)]
@@ -83,7 +83,7 @@ def test_autotune_picks_a_plan_and_stays_exact(xe):
     xe.set_option("autotune", 1)
     got = run_batch(xe, shapes, dev)
     n_cta, tile_n, sched = xe.last_config()
-    assert tile_n in (128, 256) and 0 <= sched <= 5 and n_cta > 0   # schedules 0..5 (xe_plan_dump)
+    assert tile_n in (128, 256) and 0 <= sched <= 4 and n_cta > 0   # schedules 0..4 (xe_plan_dump)
     np.testing.assert_array_equal(got[0], oracle.correlate_dense(host[0], 640, 4096, 3))
 
 
@@ -155,20 +155,6 @@ def test_accumulate_adds_into_outputs(xe):
     for (N, T, C), ha, hb, o in zip(shapes, host_a, host_b, outs):
         both = np.concatenate([ha, hb], axis=1)
         np.testing.assert_array_equal(o.cpu().numpy(), oracle.correlate_dense(both, N, 2 * T, C))
-
-
-@pytest.mark.parametrize("N,T,C", [(2048, 32768, 1), (700, 5000, 3), (129, 640, 1), (64, 64, 2)])
-def test_clustered_kernel_matches_oracle(xe, N, T, C):
-    # 2-CTA clusters sharing B planes (multicast), plus unshared pairs and partner-only
-    # segments for the leftovers.
-    p = synth.gauss_plane(N, T, C, seed=N + T)
-    xe.set_option("sched", 4)
-    dev = torch.from_numpy(p).cuda()
-    out = xe.correlate(dev, N, T, C)
-    torch.cuda.synchronize()
-    xe.device_status()
-    assert xe.last_config()[2] == 4
-    np.testing.assert_array_equal(out.cpu().numpy(), oracle.correlate_dense(p, N, T, C))
 
 
 def test_later_launch_group_needing_more_scratch(xe):
