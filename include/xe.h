@@ -378,22 +378,38 @@ void xe_stream_close(xe_stream *s);
 /* xe_correlate_noalloc: as xe_correlate_async with XE_ALGO_TC, for callers that cannot
  * call cudaMalloc (a real-time pipeline that forbids allocation once running, or a host
  * application whose own pool owns all device memory).  It allocates nothing: its scratch
- * (staged operands, tile table, status word) lives in one fixed 32 MiB device array
+ * (staged operands, tile table, status words) lives in one fixed 32 MiB device array
  * compiled into the library.  There is no counterpart in the paper; this is an interface
  * for constrained callers.
  *
  * in, vis: caller-owned device pointers, formats as above; enqueued on `stream`.
- * Limits: T <= 131072, 2 * n_chan * ceil(N/256)*256 * ceil(T/64)*64 bytes of staged
- * operands must fit the array (e.g. N=2048, T=4096, one channel uses 16 MiB), and at most
- * XE_NOALLOC_MAX_TILES tiles; larger requests return XE_EINVAL with a message in
+ * The integration runs in windows of as many 64-sample blocks as the array holds staged
+ * operands for (2 * n_chan * ceil(N/256)*256 bytes per sample; e.g. 8128 samples for N=2048
+ * and one channel), at most option "exact_chunk_t" samples each; every window after the
+ * first adds into vis.  Operands are always FP8 e4m3 (option "operand_bytes" is not used
+ * here; the result is the same exact integers).
+ * Limits: T <= XE_MAX_T (else XE_EOVERFLOW); the staged operands of one 64-sample block,
+ * 2 * n_chan * ceil(N/256)*256 * 64 bytes, must fit the array; at most
+ * XE_NOALLOC_MAX_TILES triangle tiles.  Larger requests return XE_EINVAL with a message in
  * xe_last_error() and enqueue nothing.
  * The first call on a device (with that device current) looks up the array's device
- * address with cudaGetSymbolAddress; make that first call before any stream capture.
+ * address with cudaGetSymbolAddress and clears its status words; make that first call
+ * before any stream capture.
  * Every call shares the one array, which keeps the previous call's contents: calls that
  * overlap on the GPU (other streams, unordered threads) race and give wrong results.
- * Returns XE_OK, XE_EINVAL, XE_ECUDA or XE_ENODEV. */
+ * A device-side bounded wait that gives up leaves that call's visibilities invalid; this
+ * call does not wait for its kernels, so it cannot return XE_ETIMEOUT itself: the timeout
+ * is kept in the array (a later call latches it instead of erasing it) until
+ * xe_noalloc_status reports it.
+ * Returns XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ECUDA or XE_ENODEV. */
 int xe_correlate_noalloc(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis,
                          void *stream);
+
+/* Synchronise `stream`, then read and clear the status words of xe_correlate_noalloc's
+ * fixed array on the current device.  Returns XE_ETIMEOUT if any xe_correlate_noalloc call
+ * since the last status query gave up on a bounded device wait (its visibilities are
+ * invalid), else XE_OK; or XE_ECUDA / XE_ENODEV.  Allocates nothing. */
+int xe_noalloc_status(void *stream);
 
 /* ---- diagnostics -------------------------------------------------------------------- */
 
@@ -425,6 +441,39 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *                    default 8192).
  * Returns XE_OK or XE_EINVAL. */
 int xe_set_option(const char *key, int64_t value);
+
+/* ---- autotuning cache ------------------------------------------------------------- */
+
+/* With option "autotune" on, the first call of each batch shape times the candidate plans
+ * (tile width x schedule) and keeps the fastest.  A tuning cache file keeps those choices
+ * across processes: entries are keyed by the GPU (device name with blanks as '_', and SM
+ * count), the operand width, and per job N, the channel count, the schedule weight and a T
+ * bucket (64-sample blocks rounded up to a power of two).  A later process that sets the
+ * same file takes a cached shape's plan configuration without timing anything.
+ * File format: one text line per entry,
+ *   xe-tune 1 <gpu> <n_sm> <operand_bytes> <n_jobs> {<N> <T bucket> <C> <weight>}... <n_cta> <tile_n> <sched>
+ * (weight 100 for plain jobs); malformed lines are skipped, later lines win. */
+
+/* Use `path` as the tuning cache (NULL or "" = none): reads its entries now (a missing file
+ * is empty) and appends every configuration tuned from now on.  Without this call the
+ * environment variable XE_TUNE_CACHE names the file.  Returns XE_OK. */
+int xe_tune_cache(const char *path);
+
+/* Record a plan configuration for a batch shape of plain jobs on GPU `gpu` (no blanks) with
+ * `n_sm` SMs, in memory and (with a cache file set) in the file: lets a deployment seed
+ * tuned plans.  n_cta in [1, 4096], tile_n 128 or 256, sched 0..4.  Host-only.  Returns
+ * XE_OK or XE_EINVAL. */
+int xe_tune_store(const char *gpu, int n_sm, const int *N, const int64_t *T, const int *n_chan, int n_jobs,
+                  int operand_bytes, int n_cta, int tile_n, int sched);
+
+/* The cached configuration of a batch shape for GPU `gpu` with `n_sm` SMs.  Host-only.
+ * Returns XE_OK, XE_EAGAIN if none is cached, or XE_EINVAL. */
+int xe_tune_lookup(const char *gpu, int n_sm, const int *N, const int64_t *T, const int *n_chan, int n_jobs,
+                   int operand_bytes, int *n_cta, int *tile_n, int *sched);
+
+/* Candidate plans the autotuner has timed in this process, and tuned shapes it took from
+ * the cache file instead.  Returns XE_OK. */
+int xe_tune_stats(int64_t *timed_candidates, int64_t *from_cache);
 
 /* Synchronise `stream`, then read and clear the device status word of the scratch bound
  * to it.  Returns XE_OK, or XE_ETIMEOUT if a kernel gave up on a bounded wait (its output

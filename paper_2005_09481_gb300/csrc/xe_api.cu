@@ -439,6 +439,7 @@ struct GraphRec {
 struct Device {
     int id = -1;
     int n_sm = 0;
+    std::string name;             // device name with blanks as '_' (the tuning cache's key)
     HostIO io[kHostSlots];
     HostStreams hs;
     std::map<std::vector<int64_t>, DevPlan *> plans;
@@ -471,6 +472,9 @@ static int get_device(Device **out) {
     Device *d = new Device;
     d->id = dev;
     d->n_sm = prop.multiProcessorCount;
+    d->name = prop.name;
+    for (char &ch : d->name)
+        if (ch == ' ' || ch == '\t') ch = '_';
     g_devs[dev] = d;
     *out = d;
     return XE_OK;
@@ -485,6 +489,118 @@ static std::vector<int64_t> shape_key(const std::vector<JobShape> &jobs, int eb)
         key.push_back(j.weight);
     }
     return key;
+}
+
+// ---- autotuning cache ------------------------------------------------------------------
+//
+// Tuned plan configurations are keyed by the batch shape with T bucketed: the number of
+// 64-sample blocks of each job, rounded up to a power of two (a plan is built for the exact
+// shape; only its CTA count, tile width and schedule are reused within a bucket).  With a
+// cache file set (xe_tune_cache, or XE_TUNE_CACHE in the environment), entries for this GPU
+// (name, SM count) are read from it and every newly tuned configuration is appended to it, so
+// a later process reuses it without timing candidates.  One line per entry:
+//   xe-tune 1 <gpu> <n_sm> <eb> <n_jobs> {<N> <T bucket> <C> <weight>}*n_jobs <n_cta> <tile_n> <sched>
+
+static int64_t t_bucket(int64_t T) {
+    const int64_t kb = (T + 63) / 64;
+    int64_t b = 1;
+    while (b < kb) b <<= 1;
+    return b;
+}
+
+static std::vector<int64_t> tune_key(const std::vector<JobShape> &jobs, int eb) {
+    std::vector<int64_t> key{eb};
+    for (const JobShape &j : jobs) {
+        key.push_back(j.N);
+        key.push_back(t_bucket(j.T));
+        key.push_back(j.C);
+        key.push_back(j.weight);
+    }
+    return key;
+}
+
+struct TuneStats {
+    int64_t timed = 0;            // candidate plans the autotuner timed in this process
+    int64_t from_file = 0;        // tuned shapes taken from the cache file
+};
+static TuneStats g_tune_stats;
+static std::string g_tune_path;
+static bool g_tune_env_read = false;
+// Entries read from (or written to) the cache file: (gpu, n_sm, key) -> configuration.
+static std::map<std::pair<std::string, std::vector<int64_t>>, TuneCfg> g_tune_file;
+
+static std::string gpu_id(const std::string &name, int n_sm) { return name + "/" + std::to_string(n_sm); }
+
+static bool valid_cfg(const TuneCfg &c) {
+    return c.n_cta >= 1 && c.n_cta <= 4096 && (c.tile_n == 128 || c.tile_n == 256) && c.sched >= 0 &&
+           c.sched < kNumSched;
+}
+
+// Read every well-formed entry of `path` into g_tune_file; a missing file is empty.
+static int load_tune_file(const std::string &path) {
+    FILE *f = fopen(path.c_str(), "r");
+    if (!f) return XE_OK;
+    char line[8192];
+    while (fgets(line, sizeof line, f)) {
+        char tag[16], gpu[256];
+        int ver = 0, n_sm = 0, eb = 0, n_jobs = 0, used = 0;
+        const char *q = line;
+        if (sscanf(q, "%15s %d %255s %d %d %d%n", tag, &ver, gpu, &n_sm, &eb, &n_jobs, &used) != 6) continue;
+        if (strcmp(tag, "xe-tune") != 0 || ver != 1 || n_jobs < 1 || n_jobs > kMaxJobs) continue;
+        q += used;
+        std::vector<int64_t> key{eb};
+        bool ok = true;
+        for (int k = 0; k < n_jobs && ok; ++k) {
+            long long v[4];
+            if (sscanf(q, "%lld %lld %lld %lld%n", &v[0], &v[1], &v[2], &v[3], &used) != 4) ok = false;
+            else {
+                q += used;
+                for (long long x : v) key.push_back(x);
+            }
+        }
+        TuneCfg c{0, 0, -1};
+        if (!ok || sscanf(q, "%d %d %d", &c.n_cta, &c.tile_n, &c.sched) != 3 || !valid_cfg(c)) continue;
+        g_tune_file[{gpu_id(gpu, n_sm), key}] = c;
+    }
+    fclose(f);
+    return XE_OK;
+}
+
+static void read_tune_env() {
+    if (g_tune_env_read) return;
+    g_tune_env_read = true;
+    const char *p = getenv("XE_TUNE_CACHE");
+    if (p && *p && g_tune_path.empty()) {
+        g_tune_path = p;
+        load_tune_file(g_tune_path);
+    }
+}
+
+// Record a tuned configuration in memory and, with a cache file set, append it there.
+static int store_tune(const std::string &gpu, int n_sm, const std::vector<int64_t> &key, const TuneCfg &c) {
+    g_tune_file[{gpu_id(gpu, n_sm), key}] = c;
+    if (g_tune_path.empty()) return XE_OK;
+    std::string line = "xe-tune 1 " + gpu + " " + std::to_string(n_sm) + " " + std::to_string(key[0]) + " " +
+                       std::to_string((key.size() - 1) / 4);
+    for (size_t k = 1; k < key.size(); ++k) line += " " + std::to_string(key[k]);
+    line += " " + std::to_string(c.n_cta) + " " + std::to_string(c.tile_n) + " " + std::to_string(c.sched) + "\n";
+    FILE *f = fopen(g_tune_path.c_str(), "a");
+    if (!f) return fail(XE_EINVAL, "cannot append to the tuning cache %s", g_tune_path.c_str());
+    const bool ok = fputs(line.c_str(), f) >= 0;
+    fclose(f);
+    return ok ? XE_OK : fail(XE_EINVAL, "cannot write the tuning cache %s", g_tune_path.c_str());
+}
+
+// The tuned configuration of a batch shape on device d: tuned in this process, else read
+// from the cache file (then kept in the device's table).
+static const TuneCfg *find_tuned(Device *d, const std::vector<int64_t> &key) {
+    auto it = d->tuned.find(key);
+    if (it != d->tuned.end()) return &it->second;
+    read_tune_env();
+    auto f = g_tune_file.find({gpu_id(d->name, d->n_sm), key});
+    if (f == g_tune_file.end()) return nullptr;
+    ++g_tune_stats.from_file;
+    return &(d->tuned[key] = f->second);
 }
 
 constexpr size_t kMaxCachedPlans = 4096;   // a plan blob holds a few KB to ~100 KB
@@ -781,8 +897,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             if (forced) {
                 cfg = *forced;
             } else {
-                auto it = d->tuned.find(shape_key(shapes, eb));
-                cfg = it != d->tuned.end() ? it->second : heuristic(shapes, eb, d->n_sm);
+                const TuneCfg *t = find_tuned(d, tune_key(shapes, eb));
+                cfg = t ? *t : heuristic(shapes, eb, d->n_sm);
             }
             g_last_cfg = cfg;
             DevPlan *p = nullptr;
@@ -894,8 +1010,8 @@ static int autotune(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, cuda
         shapes.push_back(JobShape{jobs[q].N, jobs[q].T, jobs[q].n_chan});
     }
     for (JobShape &j : shapes) j.T = std::min<int64_t>(j.T, g_opt.exact_chunk_t);
-    const std::vector<int64_t> key = shape_key(shapes, eb);
-    if (d->tuned.count(key)) return XE_OK;
+    const std::vector<int64_t> key = tune_key(shapes, eb);
+    if (find_tuned(d, key)) return XE_OK;
     const int n_cta = g_opt.n_cta > 0 ? g_opt.n_cta : d->n_sm;
     TuneCfg best = heuristic(shapes, eb, d->n_sm);
     float best_ms = 1e30f;
@@ -909,6 +1025,7 @@ static int autotune(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, cuda
             int rc = build_launches(d, sc, jobs, n_jobs, XE_ALGO_TC, 0, &c, recs);
             if (rc) return rc;
             const float ms = time_launches(recs, s, sc, 3);
+            ++g_tune_stats.timed;
             if (ms < best_ms) {
                 best_ms = ms;
                 best = c;
@@ -917,7 +1034,7 @@ static int autotune(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, cuda
     }
     XE_CUDA(cudaGetLastError());
     d->tuned[key] = best;
-    return XE_OK;
+    return store_tune(d->name, d->n_sm, key, best);
 }
 
 // Enqueue a batch of jobs (all validated) on stream s.
@@ -1060,6 +1177,18 @@ int reserve_stream_scratch(cudaStream_t s, int max_jobs, int N, int64_t max_T) {
     return grow(reinterpret_cast<void **>(&sc->counters), &sc->counters_bytes, counters, true, false);
 }
 
+int64_t option_exact_chunk_t() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    return g_opt.exact_chunk_t;
+}
+
+int take_inject_stall() {
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int v = g_opt.inject_stall;
+    g_opt.inject_stall = 0;
+    return v;
+}
+
 int run_jobs_mixed(const xe_job *jobs, const int *accumulate, int n_jobs, cudaStream_t s) {
     std::lock_guard<std::mutex> lk(g_mu);
     g_job_acc = accumulate;
@@ -1185,6 +1314,72 @@ int xe_last_config(int *n_cta, int *tile_n, int *sched) {
     if (tile_n) *tile_n = g_last_cfg.tile_n;
     if (sched) *sched = g_last_cfg.sched;
     return g_last_cfg.sched < 0 ? XE_EAGAIN : XE_OK;
+}
+
+static int tune_shapes(const int *N, const int64_t *T, const int *n_chan, int n_jobs, int eb,
+                       std::vector<int64_t> *key) {
+    if (!N || !T || !n_chan || n_jobs < 1 || n_jobs > kMaxJobs) return fail(XE_EINVAL, "bad batch shape");
+    if (eb != 1 && eb != 2) return fail(XE_EINVAL, "operand bytes must be 1 or 2");
+    std::vector<JobShape> shapes;
+    for (int q = 0; q < n_jobs; ++q) {
+        if (N[q] < 1 || N[q] > XE_MAX_N || T[q] < 1 || n_chan[q] < 1) return fail(XE_EINVAL, "bad job %d", q);
+        shapes.push_back(JobShape{N[q], std::min<int64_t>(T[q], kExactChunkT), n_chan[q]});
+    }
+    *key = tune_key(shapes, eb);
+    return XE_OK;
+}
+
+static int check_gpu_name(const char *gpu, int n_sm) {
+    if (!gpu || !*gpu || strlen(gpu) > 200 || n_sm < 1) return fail(XE_EINVAL, "bad GPU name or SM count");
+    for (const char *c = gpu; *c; ++c)
+        if (*c == ' ' || *c == '\t' || *c == '\n') return fail(XE_EINVAL, "GPU name must not contain blanks");
+    return XE_OK;
+}
+
+int xe_tune_cache(const char *path) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_tune_env_read = true;                    // an explicit choice overrides XE_TUNE_CACHE
+    g_tune_path = path ? path : "";
+    if (g_tune_path.empty()) return XE_OK;
+    return load_tune_file(g_tune_path);
+}
+
+int xe_tune_store(const char *gpu, int n_sm, const int *N, const int64_t *T, const int *n_chan, int n_jobs,
+                  int operand_bytes, int n_cta, int tile_n, int sched) {
+    int rc = check_gpu_name(gpu, n_sm);
+    if (rc) return rc;
+    std::vector<int64_t> key;
+    rc = tune_shapes(N, T, n_chan, n_jobs, operand_bytes, &key);
+    if (rc) return rc;
+    const TuneCfg c{n_cta, tile_n, sched};
+    if (!valid_cfg(c)) return fail(XE_EINVAL, "bad plan configuration");
+    std::lock_guard<std::mutex> lk(g_mu);
+    read_tune_env();
+    return store_tune(gpu, n_sm, key, c);
+}
+
+int xe_tune_lookup(const char *gpu, int n_sm, const int *N, const int64_t *T, const int *n_chan, int n_jobs,
+                   int operand_bytes, int *n_cta, int *tile_n, int *sched) {
+    int rc = check_gpu_name(gpu, n_sm);
+    if (rc) return rc;
+    std::vector<int64_t> key;
+    rc = tune_shapes(N, T, n_chan, n_jobs, operand_bytes, &key);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> lk(g_mu);
+    read_tune_env();
+    auto it = g_tune_file.find({gpu_id(gpu, n_sm), key});
+    if (it == g_tune_file.end()) return fail(XE_EAGAIN, "no tuned configuration for this shape");
+    if (n_cta) *n_cta = it->second.n_cta;
+    if (tile_n) *tile_n = it->second.tile_n;
+    if (sched) *sched = it->second.sched;
+    return XE_OK;
+}
+
+int xe_tune_stats(int64_t *timed_candidates, int64_t *from_cache) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (timed_candidates) *timed_candidates = g_tune_stats.timed;
+    if (from_cache) *from_cache = g_tune_stats.from_file;
+    return XE_OK;
 }
 
 int xe_correlate_async(const uint8_t *in, int N, int64_t T, int n_chan, int32_t *vis, int algo,

@@ -19,4 +19,10 @@ int release_stream_scratch(cudaStream_t s);
 // left empty and is allocated by the first batch that needs it.
 int reserve_stream_scratch(cudaStream_t s, int max_jobs, int N, int64_t max_T);
 
+// Samples one f32 tensor-memory accumulation may sum (option "exact_chunk_t").
+int64_t option_exact_chunk_t();
+
+// The "inject_stall" test hook: returns it and clears it (it applies to one call only).
+int take_inject_stall();
+
 }  // namespace xe

@@ -68,6 +68,7 @@ def load():
             "xe_host_wait": ([i32], i32),
             "xe_correlate_batch": ([p, i32, i32, p], i32),
             "xe_correlate_noalloc": ([p, i32, i64, i32, p, p], i32),
+            "xe_noalloc_status": ([p], i32),
             "xe_correlate_accumulate": ([p, i32, p], i32),
             "xe_plan_stats": ([p, p, p, i32, i32, p, p, p], i32),
             "xe_set_option": ([ctypes.c_char_p, i64], i32),
@@ -87,6 +88,10 @@ def load():
             "xe_last_config": ([p, p, p], i32),
             "xe_peak_probe": ([i32, p, p], i32),
             "xe_device_info": ([p], i32),
+            "xe_tune_cache": ([ctypes.c_char_p], i32),
+            "xe_tune_store": ([ctypes.c_char_p, i32, p, p, p, i32, i32, i32, i32, i32], i32),
+            "xe_tune_lookup": ([ctypes.c_char_p, i32, p, p, p, i32, i32, p, p, p], i32),
+            "xe_tune_stats": ([p, p], i32),
             "xe_stream_open": ([p, p], i32),
             "xe_stream_admit": ([p, i32], i32),
             "xe_stream_evict": ([p, i32], i32),
@@ -215,6 +220,44 @@ def plan_dump(shapes, n_cta: int, sched: int = -1, tile_n: int = 0):
     tiles = buf[4:4 + 6 * nt].reshape(nt, 6)
     segs = buf[4 + 6 * nt:4 + 6 * nt + 5 * ns].reshape(ns, 5)
     return {"tiles": tiles, "segs": segs, "n_cta": int(buf[2]), "n_partial": int(buf[3])}
+
+
+def _shape_arrays(shapes):
+    n = len(shapes)
+    return ((ctypes.c_int * n)(*[s[0] for s in shapes]), (ctypes.c_int64 * n)(*[s[1] for s in shapes]),
+            (ctypes.c_int * n)(*[s[2] for s in shapes]), n)
+
+
+def tune_cache(path):
+    """Use `path` as the tuning cache file (None: none)."""
+    _check(load().xe_tune_cache(path.encode() if path else None), "xe_tune_cache")
+
+
+def tune_store(gpu: str, n_sm: int, shapes, n_cta: int, tile_n: int, sched: int, operand_bytes: int = 1):
+    """Record a plan configuration for shapes [(N, T, C), ...] on GPU `gpu` (no blanks)."""
+    Ns, Ts, Cs, n = _shape_arrays(shapes)
+    _check(load().xe_tune_store(gpu.encode(), n_sm, Ns, Ts, Cs, n, operand_bytes, n_cta, tile_n, sched),
+           "xe_tune_store")
+
+
+def tune_lookup(gpu: str, n_sm: int, shapes, operand_bytes: int = 1):
+    """(n_cta, tile_n, sched) cached for shapes on GPU `gpu`, or None."""
+    Ns, Ts, Cs, n = _shape_arrays(shapes)
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    L = load()
+    rc = L.xe_tune_lookup(gpu.encode(), n_sm, Ns, Ts, Cs, n, operand_bytes, ctypes.byref(a), ctypes.byref(b),
+                          ctypes.byref(c))
+    if rc == XE_EAGAIN:
+        return None
+    _check(rc, "xe_tune_lookup")
+    return a.value, b.value, c.value
+
+
+def tune_stats():
+    """(candidate plans timed by the autotuner in this process, shapes taken from the cache)."""
+    a, b = ctypes.c_int64(), ctypes.c_int64()
+    _check(load().xe_tune_stats(ctypes.byref(a), ctypes.byref(b)), "xe_tune_stats")
+    return a.value, b.value
 
 
 def last_config():
@@ -346,6 +389,11 @@ def correlate_noalloc(inp, N: int, T: int, C: int = 1, out=None, stream=None):
                                      ctypes.c_void_p(out.data_ptr()), _stream_handle(stream))
     _check(rc, "xe_correlate_noalloc")
     return out
+
+
+def noalloc_status(stream=None):
+    """Raise XeError(XE_ETIMEOUT) if an allocation-free call since the last query timed out."""
+    _check(load().xe_noalloc_status(_stream_handle(stream)), "xe_noalloc_status")
 
 
 def flag_bytes(N: int) -> int:

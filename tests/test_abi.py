@@ -388,6 +388,7 @@ def test_compute_calls_without_a_device_fail_with_enodev():
         "xe_correlate": lambda: L.xe_correlate(inp, N, T, 1, vis),
         "xe_correlate_host": lambda: L.xe_correlate_host(inp, N, T, 1, vis, 0),
         "xe_correlate_noalloc": lambda: L.xe_correlate_noalloc(inp, N, T, 1, vis, None),
+        "xe_noalloc_status": lambda: L.xe_noalloc_status(None),
         "xe_beamform": lambda: L.xe_beamform(inp, N, T, 1, w, 1, y, None),
         "xe_corner_turn": lambda: L.xe_corner_turn(inp, 2, 1, N // 2, T, frames, None, None),
         "xe_peak_probe": lambda: L.xe_peak_probe(0, ctypes.byref(d), ctypes.byref(d)),
@@ -423,13 +424,15 @@ def test_stream_slot_bytes_match_the_serving_loop():
 
 def test_noalloc_limits_refused_before_any_device_call():
     # The allocation-free entry point refuses requests beyond its fixed scratch on the host:
-    # one exact window at most, the staged planes, the tile table.
+    # the integration length, the staged planes of one 64-sample block, the tile table.
     L = xe.load()
     buf = (ctypes.c_uint8 * 64)()
     out = (ctypes.c_int32 * 64)()
-    for (N, T, C, what) in [(64, 131073, 1, b"131072"), (2048, 131072, 1, b"staged operands"),
-                            (2048, 4096, 3, b"staged operands"), (16384, 64, 1, b"tiles")]:
-        assert L.xe_correlate_noalloc(buf, N, T, C, out, None) == xe.XE_EINVAL
+    for (N, T, C, code, what) in [(64, xe.XE_MAX_T + 1, 1, xe.XE_EOVERFLOW, b"XE_MAX_T"),
+                                  (2048, 64, 200, xe.XE_EINVAL, b"staged operands"),
+                                  (65536, 64, 4, xe.XE_EINVAL, b"staged operands"),
+                                  (16384, 64, 1, xe.XE_EINVAL, b"tiles")]:
+        assert L.xe_correlate_noalloc(buf, N, T, C, out, None) == code
         assert what in L.xe_last_error(), (N, T, C, L.xe_last_error())
 
 
