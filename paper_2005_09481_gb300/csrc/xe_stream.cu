@@ -1,7 +1,7 @@
 // xe_stream.cu -- the streaming X-engine server: frames in, integrated visibilities out.
 //
 // The CHIME X-engine integrates visibilities on the GPU and exports them at a fixed cadence
-// (Denman et al. 2020, sections 2.1 and 3.2: per-block GPU processing, time integration,
+// (Denman et al. 2020, sections 2.1 and 3.1: per-block GPU processing, time integration,
 // export of correlated visibilities, Table tab:data-flow).  Here each admitted channel owns
 // two device-resident int32 accumulators (one filling, one being exported) and a ring of
 // device frame slots.  Producers push frames (host or device memory).  One scheduler thread

@@ -16,7 +16,7 @@ Workload recipes (the CHIME shapes: N = 2048 inputs, 390625 samples/s per channe
   term A * s(t) * exp(i (2 pi k n / N + phi0)) with s(t) a unit complex Gaussian,
   A = 3, k = 3, phi0 drawn from the seed; round half to even, clip to [-7, 7].  The
   linear phase ramp across inputs makes off-diagonal visibilities nonzero (it mirrors
-  the linear phase evolution of a transiting source, section 3.1).
+  the linear phase evolution of a transiting source, section 3, first light).
 * ``uneven_batch``: instance shapes drawn from N in {256, 512, 1024, 2048} and
   T in {4096, 8192, 32768, 65536}, uniform values.
 """

@@ -87,19 +87,10 @@ def test_autotune_picks_a_plan_and_stays_exact(xe):
     np.testing.assert_array_equal(got[0], oracle.correlate_dense(host[0], 640, 4096, 3))
 
 
-def _sample_pairs(rng, N, n):
-    i = rng.integers(0, N, n)
-    j = np.array([rng.integers(a, N) for a in i])
-    # always include the corners and tile edges
-    extra_i = np.array([0, 0, N - 1, min(127, N - 1), min(128, N - 1), min(255, N - 1)])
-    extra_j = np.array([0, N - 1, N - 1, min(128, N - 1), min(255, N - 1), N - 1])
-    return np.concatenate([i, extra_i]), np.concatenate([j, np.maximum(extra_i, extra_j)])
-
-
 def test_config3_sixteen_channels_batched(xe):
     # 16 channels x N=2048 x T=16384, quantised Gaussian + plane wave, one persistent launch
-    # (channels as one 16-channel job, and as 16 jobs in a graph): equal to each other, to
-    # per-channel solo launches, and to the oracle on sampled baselines.
+    # (channels as one 16-channel job, and as 16 jobs in a graph): every channel's full output
+    # equals the oracle, and the two batch forms and per-channel solo launches agree.
     N, T, C = 2048, 16384, 16
     host = synth.gauss_plane(N, T, C)
     d = torch.from_numpy(host).cuda()
@@ -107,23 +98,20 @@ def test_config3_sixteen_channels_batched(xe):
     jobs = [(d[c], xe.empty_vis(N, 1), N, T, 1) for c in range(C)]
     xe.correlate_batch(jobs, use_graph=True)
     torch.cuda.synchronize()
+    xe.device_status()
     a = out_a.cpu().numpy()
     for c in range(C):
-        np.testing.assert_array_equal(a[c], jobs[c][1].cpu().numpy()[0])
-    rng = np.random.default_rng(0)
+        np.testing.assert_array_equal(a[c], oracle.correlate_dense(host[c], N, T, 1)[0])
+        np.testing.assert_array_equal(jobs[c][1].cpu().numpy()[0], a[c])
     for c in (0, 7, 15):
         solo = xe.correlate(d[c].contiguous(), N, T, 1)
         torch.cuda.synchronize()
         np.testing.assert_array_equal(a[c], solo.cpu().numpy()[0])
-        ii, jj = _sample_pairs(rng, N, 150)
-        want = oracle.pairs(host, N, T, C, np.full(ii.size, c), ii, jj)
-        idx = ii * N - ii * (ii - 1) // 2 + (jj - ii)
-        np.testing.assert_array_equal(a[c][idx], want)
 
 
 def test_config4_uneven_64_instances_batched(xe):
-    # 64 instances, N in {256..2048}, T in {4096..65536} (seeded), one persistent launch,
-    # against 64 plain launches (exact) and the oracle on sampled baselines.
+    # 64 instances, N in {256..2048}, T in {4096..65536} (seeded), one persistent launch:
+    # every instance's full output equals the oracle and its own plain launch.
     shapes = synth.uneven_shapes(64)
     host = [synth.uniform(N, T, 1, seed=synth.BASE_SEED + 1 + q) for q, (N, T) in enumerate(shapes)]
     dev = [torch.from_numpy(h).cuda() for h in host]
@@ -131,17 +119,12 @@ def test_config4_uneven_64_instances_batched(xe):
     xe.correlate_batch([(d, o, N, T, 1) for d, o, (N, T) in zip(dev, outs, shapes)])
     torch.cuda.synchronize()
     xe.device_status()
-    rng = np.random.default_rng(1)
     for q, ((N, T), h, d, o) in enumerate(zip(shapes, host, dev, outs)):
         solo = xe.correlate(d, N, T, 1)
         torch.cuda.synchronize()
         g = o.cpu().numpy()
         np.testing.assert_array_equal(g, solo.cpu().numpy())
-        if q % 8 == 0:
-            ii, jj = _sample_pairs(rng, N, 40)
-            want = oracle.pairs(h, N, T, 1, np.zeros(ii.size, np.int64), ii, jj)
-            idx = ii * N - ii * (ii - 1) // 2 + (jj - ii)
-            np.testing.assert_array_equal(g[0][idx], want)
+        np.testing.assert_array_equal(g, oracle.correlate_dense(h, N, T, 1))
 
 
 def test_accumulate_adds_into_outputs(xe):
