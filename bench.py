@@ -576,6 +576,8 @@ def main():
     ap.add_argument("--stream-step", type=int, default=32)
     ap.add_argument("--stream-max", type=int, default=1024)
     ap.add_argument("--host-source", action="store_true")
+    ap.add_argument("--no-host-stream", dest="host_stream", action="store_false",
+                    help="skip the host-source streaming ramp of the default workload")
     ap.add_argument("--stream-integ-frames", type=int, default=4,
                     help="frames per integration (4 = 83.9 ms; 477 = the paper's 10 s cadence)")
     args = ap.parse_args()
@@ -708,7 +710,8 @@ def main():
 
     # The real-time stream leg runs before the legs whose exactness checks keep the host's
     # cores busy (its producer is paced on the host).
-    stream = None
+    stream = host_stream = None
+    stream_runs = []
     if ws == 1 and not args.no_stream:
         # The largest sustained channel count (real-time pace, no overruns or drops), found
         # the way channels come on line: start at --stream-channels - 64 and add 32 while
@@ -718,21 +721,41 @@ def main():
         # steps down by 32 instead.
         from paper_2005_09481_gb300 import serve
 
-        def sustained_run(n):
-            r = serve.run_realtime(n, args.stream_seconds)
-            return r if r["sustained"] else serve.run_realtime(n, args.stream_seconds)
+        def one_run(n, device_source=True):
+            rc0 = xe.runtime_counters()
+            r = serve.run_realtime(n, args.stream_seconds, device_source=device_source)
+            rc1 = xe.runtime_counters()
+            summary = {k: r[k] for k in ("channels", "device_source", "sustained", "cmac_per_s", "p50_latency_ms",
+                                         "p99_latency_ms", "producer_late_frames", "push_overruns",
+                                         "frames_dropped", "drain_s")}
+            summary["server"] = {k: r["counters"][k] for k in ("launch_passes", "launch_groups", "held_passes",
+                                                                "launch_host_ns")}
+            summary["runtime"] = {k: rc1[k] - rc0[k] for k in rc1}
+            stream_runs.append(summary)
+            print(json.dumps(dict(summary, counters=r["counters"])), file=sys.stderr, flush=True)
+            return r
 
-        c = max(32, args.stream_channels - 64)
-        stream = sustained_run(c)
-        while not stream["sustained"] and c > 64:
-            c -= 32
-            stream = sustained_run(c)
-        while stream["sustained"] and c < 1024:
-            up = sustained_run(c + 32)
-            if not up["sustained"]:
-                break
-            c += 32
-            stream = up
+        def sustained_run(n, device_source=True):
+            r = one_run(n, device_source)
+            return r if r["sustained"] else one_run(n, device_source)
+
+        def ramp(start, device_source):
+            c = start
+            best = sustained_run(c, device_source)
+            while not best["sustained"] and c > 64:
+                c -= 32
+                best = sustained_run(c, device_source)
+            while best["sustained"] and c < 1024:
+                up = sustained_run(c + 32, device_source)
+                if not up["sustained"]:
+                    break
+                c += 32
+                best = up
+            return best
+
+        stream = ramp(max(32, args.stream_channels - 64), True)
+        # Frames from pinned host memory cross the host link (about 0.8 GB/s per channel).
+        host_stream = ramp(max(32, min(args.stream_channels - 64, 224)), False) if args.host_stream else None
 
     masked = None
     if ws == 1 and not args.no_masked:
@@ -795,6 +818,12 @@ def main():
                                                "device_source", "producer_late_frames", "push_overruns",
                                                "frames_dropped", "drain_s", "counters")}
                        if stream else None),
+            "stream_host_source": ({k: host_stream[k] for k in ("channels", "sustained", "cmac_per_s", "p50_latency_ms",
+                                                                 "p99_latency_ms", "max_latency_ms", "device_source",
+                                                                 "producer_late_frames", "push_overruns",
+                                                                 "frames_dropped")}
+                                   if host_stream else None),
+            "stream_runs": stream_runs,
             "masked": masked,
             "beams": beams,
             "corner": corner,

@@ -436,6 +436,9 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *                    percent of a data job's (1 .. 100, default 75);
  *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 4, percent of
  *                    a whole tile (0 .. 100, default 2);
+ *   "implicit_plans" 1 = batches of the streaming server run whole tiles dealt round-robin
+ *                    over the CTAs, decoded in the kernel from the job table, with no plan
+ *                    built on the host (default); 0 = host-built plans as for other calls;
  *   "host_chunk_t"   samples per chunk of the host-buffer entry points' copy/correlate
  *                    pipeline (0 = one copy then one correlation; else a multiple of 64;
  *                    default 8192).
@@ -474,6 +477,13 @@ int xe_tune_lookup(const char *gpu, int n_sm, const int *N, const int64_t *T, co
 /* Candidate plans the autotuner has timed in this process, and tuned shapes it took from
  * the cache file instead.  Returns XE_OK. */
 int xe_tune_stats(int64_t *timed_candidates, int64_t *from_cache);
+
+/* Process-wide counters of host work that can stall a caller, in this order: batches
+ * whose launch records were built, host ns spent building them, plans built for new batch
+ * shapes, host ns spent on those plans, scratch regrowths and plan-cache trims (each of
+ * these two synchronises the device).  Writes min(n, 6) values; returns that count or
+ * XE_EINVAL. */
+int xe_runtime_counters(int64_t *out, int n);
 
 /* Synchronise `stream`, then read and clear the device status word of the scratch bound
  * to it.  Returns XE_OK, or XE_ETIMEOUT if a kernel gave up on a bounded wait (its output

@@ -12,6 +12,8 @@
 #include <string>
 #include <vector>
 
+#include <time.h>
+
 #include <cuda_runtime.h>
 
 #include "xe.h"
@@ -57,9 +59,26 @@ struct Options {
     int count_weight = 75;                 // cost of a count-job k-iteration, % of a data one
     int part_overhead = 2;                 // modelled cost of one extra tile part, % of a
                                            // whole data tile (workspace fix-up)
+    int implicit_plans = 1;                // 1: batches of the streaming server run without
+                                           // host-built plans (whole tiles dealt round-robin,
+                                           // decoded in the kernel); 0: host plans
 };
 static Options g_opt;
 static std::mutex g_mu;
+
+// Host-side events of the runtime that can stall a caller (process-wide, under g_mu):
+// plans built (and their host time), scratch regrowths and plan-cache trims (both
+// synchronise the device), and launch records built (and their host time).
+struct RuntimeCounters {
+    int64_t plans_built = 0, plan_ns = 0, regrowths = 0, trims = 0, batches = 0, build_ns = 0;
+};
+static RuntimeCounters g_rc;
+
+static int64_t host_ns() {
+    timespec ts;
+    clock_gettime(CLOCK_MONOTONIC, &ts);
+    return int64_t(ts.tv_sec) * 1000000000LL + ts.tv_nsec;
+}
 
 // ---- plans ---------------------------------------------------------------------------
 
@@ -379,6 +398,9 @@ static bool build_plan(const std::vector<JobShape> &jobs, int eb, const TuneCfg 
 struct DevPlan {
     HostPlan host;
     void *blob = nullptr;         // tiles | segs | seg_off | tile_slots
+    bool own_blob = false;        // blob was allocated alone (the arena was full), not carved
+    cudaEvent_t ready = nullptr;  // the upload has landed (recorded on upload_stream)
+    cudaStream_t upload_stream = nullptr;
     const Tile *d_tiles = nullptr;
     const Seg *d_segs = nullptr;
     const int *d_seg_off = nullptr;
@@ -446,6 +468,8 @@ struct Device {
     std::map<std::vector<int64_t>, TuneCfg> tuned;
     std::map<cudaStream_t, Scratch *> scratch;
     std::map<std::vector<int64_t>, GraphRec *> graphs;
+    uint8_t *arena = nullptr;     // device memory the plan blobs are carved from
+    size_t arena_used = 0;
 };
 
 static std::map<int, Device *> g_devs;
@@ -603,22 +627,26 @@ static const TuneCfg *find_tuned(Device *d, const std::vector<int64_t> &key) {
     return &(d->tuned[key] = f->second);
 }
 
-constexpr size_t kMaxCachedPlans = 4096;   // a plan blob holds a few KB to ~100 KB
+constexpr size_t kMaxCachedPlans = 4096;   // a plan blob holds a few KB to a few MB
+constexpr size_t kPlanArenaBytes = size_t(64) << 20;
 
 // Bounded plan cache: a stream of ever-new batch shapes (e.g. merged stream frames) would
 // otherwise keep one device blob per shape forever.  Called before a batch builds its launch
 // records (none of which may hold a plan yet); plans of launches already queued may still be
 // read, so the cache (and the graphs that point into it) is dropped only once the device is
-// idle.
+// idle.  Half of the arena is kept free for the plans of the batch that follows.
 static int trim_plan_cache(Device *d) {
-    if (d->plans.size() < kMaxCachedPlans) return XE_OK;
+    if (d->plans.size() < kMaxCachedPlans && d->arena_used <= kPlanArenaBytes / 2) return XE_OK;
+    ++g_rc.trims;
     cudaError_t e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return fail(XE_ECUDA, "sync before dropping plans: %s", cudaGetErrorString(e));
     for (auto &kv : d->plans) {
-        cudaFree(kv.second->blob);
+        if (kv.second->own_blob) cudaFree(kv.second->blob);
+        if (kv.second->ready) cudaEventDestroy(kv.second->ready);
         delete kv.second;
     }
     d->plans.clear();
+    d->arena_used = 0;
     for (auto &kv : d->graphs) {
         cudaGraphExecDestroy(kv.second->exec);
         cudaGraphDestroy(kv.second->graph);
@@ -628,7 +656,11 @@ static int trim_plan_cache(Device *d) {
     return XE_OK;
 }
 
-static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const TuneCfg &cfg,
+// The device plan of a batch shape and configuration, for launches on stream s.  A new plan
+// is carved from the device's plan arena (one allocation per device, on first use) and
+// uploaded with a copy ordered on s, so building a plan neither allocates nor waits for the
+// device; launches on another stream wait for the upload's event.
+static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const TuneCfg &cfg, cudaStream_t s,
                     DevPlan **out) {
     std::vector<int64_t> key = shape_key(jobs, eb);
     key.push_back(cfg.n_cta);
@@ -636,9 +668,12 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
     key.push_back(cfg.sched);
     auto it = d->plans.find(key);
     if (it != d->plans.end()) {
-        *out = it->second;
+        DevPlan *p = it->second;
+        if (p->upload_stream != s) XE_CUDA(cudaStreamWaitEvent(s, p->ready, 0));
+        *out = p;
         return XE_OK;
     }
+    const int64_t t_plan = host_ns();
     DevPlan *p = new DevPlan;
     if (!build_plan(jobs, eb, cfg, p->host)) {
         delete p;
@@ -649,7 +684,17 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
     const size_t b_o = h.seg_off.size() * sizeof(int), b_l = (h.tile_slots.size() + 1) * sizeof(int);
     const size_t o_s = (b_t + 255) / 256 * 256, o_o = o_s + (b_s + 255) / 256 * 256,
                  o_l = o_o + (b_o + 255) / 256 * 256, total = o_l + b_l;
-    if (cudaMalloc(&p->blob, total) != cudaSuccess) {
+    const size_t carve = (total + 255) / 256 * 256;
+    if (!d->arena && cudaMalloc(reinterpret_cast<void **>(&d->arena), kPlanArenaBytes) != cudaSuccess) {
+        cudaGetLastError();
+        d->arena = nullptr;
+    }
+    if (d->arena && d->arena_used + carve <= kPlanArenaBytes) {
+        p->blob = d->arena + d->arena_used;
+        d->arena_used += carve;
+    } else if (cudaMalloc(&p->blob, total) == cudaSuccess) {
+        p->own_blob = true;
+    } else {
         cudaGetLastError();
         delete p;
         size_t fr = 0, tot = 0;
@@ -662,15 +707,20 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
     memcpy(host.data() + o_s, h.segs.data(), b_s);
     memcpy(host.data() + o_o, h.seg_off.data(), b_o);
     if (!h.tile_slots.empty()) memcpy(host.data() + o_l, h.tile_slots.data(), b_l - sizeof(int));
-    // A copy from pageable memory may return before it has landed, and it is ordered on the
-    // legacy stream only: wait for it, so that kernels on any stream read the whole plan.
-    cudaError_t e = cudaMemcpy(p->blob, host.data(), total, cudaMemcpyHostToDevice);
-    if (e == cudaSuccess) e = cudaStreamSynchronize(0);
+    // From pageable memory the copy returns once the bytes are staged (the vector may go) and
+    // lands in stream order on s, before any launch enqueued on s after it.
+    cudaError_t e = cudaEventCreateWithFlags(&p->ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(p->blob, host.data(), total, cudaMemcpyHostToDevice, s);
+    if (e == cudaSuccess) e = cudaEventRecord(p->ready, s);
     if (e != cudaSuccess) {
-        cudaFree(p->blob);
+        if (p->own_blob) cudaFree(p->blob);
+        if (p->ready) cudaEventDestroy(p->ready);
         delete p;
         return fail(XE_ECUDA, "plan upload failed: %s", cudaGetErrorString(e));
     }
+    p->upload_stream = s;
+    ++g_rc.plans_built;
+    g_rc.plan_ns += host_ns() - t_plan;
     uint8_t *base = static_cast<uint8_t *>(p->blob);
     p->d_tiles = reinterpret_cast<const Tile *>(base);
     p->d_segs = reinterpret_cast<const Seg *>(base + o_s);
@@ -684,6 +734,7 @@ static int get_plan(Device *d, const std::vector<JobShape> &jobs, int eb, const 
 static int grow(void **ptr, size_t *have, size_t need, bool zero, bool headroom = true) {
     if (*have >= need && *ptr) return XE_OK;
     if (*ptr) {
+        ++g_rc.regrowths;
         cudaError_t e = cudaDeviceSynchronize();  // nothing may still use the old buffer
         if (e != cudaSuccess) return fail(XE_ECUDA, "sync before regrow: %s", cudaGetErrorString(e));
         cudaFree(*ptr);
@@ -764,7 +815,7 @@ static int check_job(const uint8_t *in, int N, int64_t T, int C, const int32_t *
 // Build the launch sequence for a batch (allocating scratch and plans as needed), without
 // enqueuing anything.  `forced` overrides the plan configuration (autotuner candidates).
 static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, int algo,
-                          int accumulate, const TuneCfg *forced, std::vector<LaunchRec> &out) {
+                          int accumulate, const TuneCfg *forced, cudaStream_t s, std::vector<LaunchRec> &out) {
     out.clear();
     if (algo == XE_ALGO_IMMA) {
         for (int g0 = 0; g0 < n_jobs; g0 += kMaxJobs) {
@@ -893,6 +944,31 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             for (int k = 0; k < ng; ++k)
                 if (count_of[size_t(k)] >= 0)
                     jt.jobs[k].count_planes = const_cast<uint8_t *>(jt.jobs[count_of[size_t(k)]].planes);
+            // Batches of the streaming server (per-job accumulate flags, default tiling): no host
+            // plan.  Their shapes change from pass to pass as frames merge, and a new plan costs
+            // milliseconds of host time; whole tiles dealt round-robin over the CTAs need none.
+            if (!forced && g_job_acc && !g_job_mask && g_opt.implicit_plans && g_opt.sched < 0 &&
+                (g_opt.tile_n == 0 || g_opt.tile_n == kBN)) {
+                int tiles = 0;
+                for (int k = 0; k < jt.n_jobs; ++k) {
+                    JobDev &jd = jt.jobs[k];
+                    jd.tile0 = tiles;
+                    jd.tiles_per_chan = int(count_tiles(jd.N, kBN));
+                    tiles += jd.tiles_per_chan * jd.C;
+                }
+                LaunchRec tc = st;
+                tc.kind = 1;
+                PlanDev &pd = tc.pd;
+                pd = PlanDev{};
+                pd.implicit = 1;
+                pd.n_tiles = tiles;
+                pd.n_cta = std::min(tiles, g_opt.n_cta > 0 ? g_opt.n_cta : d->n_sm);
+                pd.status = sc->status;
+                pd.inject_stall = g_opt.inject_stall;
+                out.push_back(st);
+                out.push_back(tc);
+                continue;
+            }
             TuneCfg cfg;
             if (forced) {
                 cfg = *forced;
@@ -902,7 +978,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             }
             g_last_cfg = cfg;
             DevPlan *p = nullptr;
-            const int rc = get_plan(d, shapes, eb, cfg, &p);
+            const int rc = get_plan(d, shapes, eb, cfg, s, &p);
             if (rc) return rc;
             const size_t ws_need =
                 size_t(std::max(1, p->host.n_partial)) * size_t(kWsSlotElems) * sizeof(int32_t);
@@ -1022,7 +1098,7 @@ static int autotune(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs, cuda
             if (g_opt.sched >= 0 && si != g_opt.sched) continue;
             TuneCfg c{n_cta, widths[wi], si};
             std::vector<LaunchRec> recs;
-            int rc = build_launches(d, sc, jobs, n_jobs, XE_ALGO_TC, 0, &c, recs);
+            int rc = build_launches(d, sc, jobs, n_jobs, XE_ALGO_TC, 0, &c, s, recs);
             if (rc) return rc;
             const float ms = time_launches(recs, s, sc, 3);
             ++g_tune_stats.timed;
@@ -1054,7 +1130,10 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
         if (rc) return rc;
     }
     std::vector<LaunchRec> recs;
-    rc = build_launches(d, sc, jobs, n_jobs, algo, accumulate, nullptr, recs);
+    const int64_t t_build = host_ns();
+    rc = build_launches(d, sc, jobs, n_jobs, algo, accumulate, nullptr, s, recs);
+    ++g_rc.batches;
+    g_rc.build_ns += host_ns() - t_build;
     g_opt.inject_stall = 0;
     if (rc) return rc;
     const bool timing = g_opt.timing != 0;
@@ -1280,6 +1359,8 @@ int xe_set_option(const char *key, int64_t value) {
     } else if (!strcmp(key, "count_weight")) {
         if (value < 1 || value > 100) return fail(XE_EINVAL, "count_weight must lie in [1, 100]");
         g_opt.count_weight = int(value);
+    } else if (!strcmp(key, "implicit_plans")) {
+        g_opt.implicit_plans = value ? 1 : 0;
     } else if (!strcmp(key, "part_overhead")) {
         if (value < 0 || value > 100) return fail(XE_EINVAL, "part_overhead must lie in [0, 100]");
         g_opt.part_overhead = int(value);
@@ -1373,6 +1454,14 @@ int xe_tune_lookup(const char *gpu, int n_sm, const int *N, const int64_t *T, co
     if (tile_n) *tile_n = it->second.tile_n;
     if (sched) *sched = it->second.sched;
     return XE_OK;
+}
+
+int xe_runtime_counters(int64_t *out, int n) {
+    if (!out || n < 1) return fail(XE_EINVAL, "bad counter query");
+    std::lock_guard<std::mutex> lk(g_mu);
+    const int64_t v[6] = {g_rc.batches, g_rc.build_ns, g_rc.plans_built, g_rc.plan_ns, g_rc.regrowths, g_rc.trims};
+    for (int k = 0; k < n && k < 6; ++k) out[k] = v[k];
+    return n < 6 ? n : 6;
 }
 
 int xe_tune_stats(int64_t *timed_candidates, int64_t *from_cache) {

@@ -63,6 +63,8 @@ struct JobDev {
     int64_t s_t;
     int64_t s_seg;
     int seg;
+    int tile0;                // implicit plans: tiles of the jobs before this one in the launch
+    int tiles_per_chan;       // implicit plans: 256-wide triangle tiles of one channel
 };
 
 // Byte address of sample (c, t, n) of a job's input (see JobDev).
@@ -126,6 +128,8 @@ struct PlanDev {
     int inject_stall;         // test hook: 1 = the producer issues no copies, so waits time out
     int pair_exchange;        // 1: every split tile has 2 parts and every CTA one segment, so the
                               // two parts swap column halves instead of a last-arriver sum
+    int implicit;             // 1: no tile or segment arrays: CTA b takes whole tiles b, b + grid,
+                              // ... of the launch, decoded from the job table (implicit_tile)
 };
 
 // Triangle schedules (host-side choice; the kernel just follows the segment lists).

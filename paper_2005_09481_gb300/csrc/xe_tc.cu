@@ -44,6 +44,51 @@ __device__ __forceinline__ void epi_bar() { asm volatile("bar.sync 1, 128;" ::: 
 
 __device__ __forceinline__ void set_status(int *status, int code) { atomicCAS(status, 0, code); }
 
+// Implicit plans: tile t of the launch as a whole-tile segment.  The tiles of a job are its
+// channels' tiles in channel order, each channel's in the order the host planner enumerates
+// 256-wide tiles: row blocks of 128 inputs, in each first a 128-wide half tile where the row
+// block starts mid-way through a 256 column block, then the 256-wide tiles to its right.
+__device__ __forceinline__ void implicit_tile(const JobTable &jt, int t, Seg &sg, Tile &tl) {
+    int lo = 0, hi = jt.n_jobs - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (jt.jobs[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const JobDev &jb = jt.jobs[lo];
+    const int u = t - jb.tile0;
+    const int c = u / jb.tiles_per_chan;
+    int v = u - c * jb.tiles_per_chan;
+    int i0 = 0, j0 = 0, nj = kBN;
+    for (int r = 0; r * kBM < jb.N; ++r) {
+        const int half = r & 1;
+        const int js = r * kBM + half * kBM;
+        const int n = half + (js < jb.N ? (jb.N - js + kBN - 1) / kBN : 0);
+        if (v < n) {
+            i0 = r * kBM;
+            if (half && v == 0) {
+                j0 = i0;
+                nj = kBM;
+            } else {
+                j0 = js + (v - half) * kBN;
+            }
+            break;
+        }
+        v -= n;
+    }
+    tl = Tile{lo, c, i0, j0, nj, jb.kblocks, 0, 0};
+    sg = Seg{t, 0, jb.kblocks, -1};
+}
+
+// Segment q of this CTA (q in [q0, q1)) and its tile, from the plan arrays or implicitly.
+__device__ __forceinline__ void fetch_segment(const JobTable &jt, const PlanDev &plan, int q, Seg &sg, Tile &tl) {
+    if (plan.implicit) {
+        implicit_tile(jt, int(blockIdx.x) + q * int(gridDim.x), sg, tl);
+    } else {
+        sg = plan.segs[q];
+        tl = plan.tiles[sg.tile];
+    }
+}
+
 // Store (or add) a 32 x 32 block of final visibilities held by one warp (lane = row
 // i0 + lane, register k = column jbase + k).  The block is transposed through the warp's
 // shared buffer so that each global access covers 32 consecutive baselines of one row
@@ -155,11 +200,12 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     const uint32_t tmem = *tmem_slot;
 
     // This CTA's work: segments [q0, q1) of the plan, each a k-range of one tile.
-    const int q0 = plan.seg_off[blockIdx.x];
-    const int q1 = plan.seg_off[blockIdx.x + 1];
+    const int q0 = plan.implicit ? 0 : plan.seg_off[blockIdx.x];
+    const int q1 = plan.implicit ? (plan.n_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x)
+                                 : plan.seg_off[blockIdx.x + 1];
     // A CTA whose only segment is one part of a pair-exchanged tile finishes it with eight
     // warps: the producer and MMA warps are idle by then, and two more warps wait for it.
-    const bool wide = plan.pair_exchange && q1 - q0 == 1 && plan.segs[q0].slot >= 0;
+    const bool wide = !plan.implicit && plan.pair_exchange && q1 - q0 == 1 && plan.segs[q0].slot >= 0;
     constexpr uint32_t kFmt = 0;  // E4M3 for kind::f8f6f4, F16 for kind::f16
 
     if (warp == 4) {
@@ -175,8 +221,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
             bool ok = true;
             // Test hook: issue nothing, so the MMA warp's bounded wait runs out.
             for (int q = plan.inject_stall ? q1 : q0; ok && q < q1; ++q) {
-                const Seg sg = plan.segs[q];
-                const Tile tl = plan.tiles[sg.tile];
+                Seg sg;
+                Tile tl;
+                fetch_segment(jt, plan, q, sg, tl);
                 const JobDev &jb = jt.jobs[tl.job];
                 const uint8_t *pl = jb.planes + int64_t(tl.chan) * jb.plane_chan_bytes;
                 const uint32_t bbytes = uint32_t(tl.nj) * kRowBytes;
@@ -227,8 +274,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
             bool ok = true;
             const uint32_t d_re = tmem, d_im = tmem + 256;
             for (int q = q0; ok && q < q1; ++q) {
-                const Seg sg = plan.segs[q];
-                const Tile tl = plan.tiles[sg.tile];
+                Seg sg;
+                Tile tl;
+                fetch_segment(jt, plan, q, sg, tl);
                 // Count job: its two slots hold the validity of two consecutive sample
                 // blocks, and only the Re accumulator is formed.
                 const bool re_only = (jt.jobs[tl.job].mode & kModeCount) != 0;
@@ -301,8 +349,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         const int r = warp * 32 + lane;
         const uint32_t lane_base = uint32_t(warp * 32) << 16;
         for (int q = q0; q < q1; ++q) {
-            const Seg sg = plan.segs[q];
-            const Tile tl = plan.tiles[sg.tile];
+            Seg sg;
+            Tile tl;
+            fetch_segment(jt, plan, q, sg, tl);
             const JobDev &jb = jt.jobs[tl.job];
             if (threadIdx.x == 0) {
                 const bool ok = mbar_wait(acc_full, acc_ph, status);

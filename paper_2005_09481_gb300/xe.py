@@ -92,6 +92,7 @@ def load():
             "xe_tune_store": ([ctypes.c_char_p, i32, p, p, p, i32, i32, i32, i32, i32], i32),
             "xe_tune_lookup": ([ctypes.c_char_p, i32, p, p, p, i32, i32, p, p, p], i32),
             "xe_tune_stats": ([p, p], i32),
+            "xe_runtime_counters": ([p, i32], i32),
             "xe_stream_open": ([p, p], i32),
             "xe_stream_admit": ([p, i32], i32),
             "xe_stream_evict": ([p, i32], i32),
@@ -258,6 +259,17 @@ def tune_stats():
     a, b = ctypes.c_int64(), ctypes.c_int64()
     _check(load().xe_tune_stats(ctypes.byref(a), ctypes.byref(b)), "xe_tune_stats")
     return a.value, b.value
+
+
+def runtime_counters():
+    """Host work that can stall a caller: batches built and their host ns, plans built for new
+    shapes and their host ns, scratch regrowths and plan-cache trims (both synchronise)."""
+    import numpy as np
+    v = np.zeros(6, np.int64)
+    n = load().xe_runtime_counters(v.ctypes.data, 6)
+    if n < 0:
+        _check(n, "xe_runtime_counters")
+    return dict(zip(("batches", "build_ns", "plans_built", "plan_ns", "regrowths", "trims"), v.tolist()))
 
 
 def last_config():
