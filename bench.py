@@ -328,8 +328,8 @@ def measure_masked(steps, warmup, dev, flush, check=True):
     out = {"value": cm / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms, "steps": steps,
            "stage_ms": statistics.mean(p[0] for p in parts),
            "correlate_ms": statistics.mean(p[1] for p in parts),
-           "gpu_launches_per_step": 2, "workload": MASKED_WORKLOAD,
-           "counts": "written by the count jobs' epilogue inside the correlation kernel"}
+           "gpu_launches_per_step": 3, "workload": MASKED_WORKLOAD,
+           "counts": "written by the count jobs' epilogue, a second correlation launch after the visibilities'"}
     if check:
         import oracle
         want = oracle.correlate_masked_dense(packed, flags, N, T, 1, 1)

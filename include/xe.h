@@ -432,6 +432,8 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *   "autotune"       1 = time every (tile width, schedule) candidate the first time a
  *                    batch shape is correlated and keep the fastest for that shape;
  *   "timing"         1 = record device times of each call (see xe_last_timing);
+ *   "count_launch"   1 = the valid-sample counts of a masked call run as a second
+ *                    correlation launch after the visibilities' (default); 0 = one mixed launch;
  *   "count_weight"   cost of a count job's k-iteration (two sample blocks) in schedule 4,
  *                    percent of a data job's (1 .. 100, default 75);
  *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 4, percent of

@@ -57,6 +57,9 @@ struct Options {
     int64_t host_chunk_t = 8192;           // samples per pipelined chunk of xe_correlate_host
                                            // (0: one copy, then one correlation)
     int count_weight = 75;                 // cost of a count-job k-iteration, % of a data one
+    int count_launch = 1;                  // 1: count jobs in a launch of their own after the
+                                           // data jobs' (masked calls with counts; measured
+                                           // faster than one mixed launch); 0: one launch
     int part_overhead = 2;                 // modelled cost of one extra tile part, % of a
                                            // whole data tile (workspace fix-up)
     int implicit_plans = 1;                // 1: batches of the streaming server run without
@@ -969,38 +972,64 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 out.push_back(tc);
                 continue;
             }
-            TuneCfg cfg;
-            if (forced) {
-                cfg = *forced;
-            } else {
-                const TuneCfg *t = find_tuned(d, tune_key(shapes, eb));
-                cfg = t ? *t : heuristic(shapes, eb, d->n_sm);
-            }
-            g_last_cfg = cfg;
-            DevPlan *p = nullptr;
-            const int rc = get_plan(d, shapes, eb, cfg, s, &p);
-            if (rc) return rc;
-            const size_t ws_need =
-                size_t(std::max(1, p->host.n_partial)) * size_t(kWsSlotElems) * sizeof(int32_t);
-            max_ws = std::max(max_ws, ws_need);
-            max_counters = std::max(max_counters, p->host.tiles.size() * sizeof(int));
-            LaunchRec tc = st;
-            tc.kind = 1;
-            PlanDev &pd = tc.pd;
-            pd.tiles = p->d_tiles;
-            pd.segs = p->d_segs;
-            pd.seg_off = p->d_seg_off;
-            pd.tile_slots = p->d_tile_slots;
-            pd.n_tiles = int(p->host.tiles.size());
-            pd.n_cta = p->host.n_cta;
-            pd.ws = nullptr;          // bound below
-            pd.counters = nullptr;
-            pd.status = sc->status;
-            pd.inject_stall = g_opt.inject_stall;
-            // All CTAs of the launch must be resident together for the exchange's wait.
-            pd.pair_exchange = p->host.pair_exchange && p->host.n_cta <= d->n_sm ? 1 : 0;
+            // The correlation launch(es) of the group: one for data and count jobs together,
+            // or (option "count_launch") the data jobs, then the count jobs in a launch of their
+            // own after it (both read the planes this group's staging wrote).
+            auto make_tc = [&](const JobTable &jtab, const std::vector<JobShape> &shp, LaunchRec &tc) -> int {
+                TuneCfg cfg;
+                if (forced) {
+                    cfg = *forced;
+                } else {
+                    const TuneCfg *t = find_tuned(d, tune_key(shp, eb));
+                    cfg = t ? *t : heuristic(shp, eb, d->n_sm);
+                }
+                g_last_cfg = cfg;
+                DevPlan *p = nullptr;
+                const int rc = get_plan(d, shp, eb, cfg, s, &p);
+                if (rc) return rc;
+                const size_t ws_need =
+                    size_t(std::max(1, p->host.n_partial)) * size_t(kWsSlotElems) * sizeof(int32_t);
+                max_ws = std::max(max_ws, ws_need);
+                max_counters = std::max(max_counters, p->host.tiles.size() * sizeof(int));
+                tc = st;
+                tc.jt = jtab;
+                tc.kind = 1;
+                PlanDev &pd = tc.pd;
+                pd.tiles = p->d_tiles;
+                pd.segs = p->d_segs;
+                pd.seg_off = p->d_seg_off;
+                pd.tile_slots = p->d_tile_slots;
+                pd.n_tiles = int(p->host.tiles.size());
+                pd.n_cta = p->host.n_cta;
+                pd.ws = nullptr;          // bound below
+                pd.counters = nullptr;
+                pd.status = sc->status;
+                pd.inject_stall = g_opt.inject_stall;
+                // All CTAs of the launch must be resident together for the exchange's wait.
+                pd.pair_exchange = p->host.pair_exchange && p->host.n_cta <= d->n_sm ? 1 : 0;
+                return XE_OK;
+            };
             out.push_back(st);
-            out.push_back(tc);
+            if (g_opt.count_launch && jt.n_jobs > ng) {
+                LaunchRec data_rec, count_rec;
+                JobTable jd_tab = jt, jc_tab = jt;
+                jd_tab.n_jobs = ng;
+                jc_tab.n_jobs = jt.n_jobs - ng;
+                for (int k = 0; k < jc_tab.n_jobs; ++k) jc_tab.jobs[k] = jt.jobs[ng + k];
+                std::vector<JobShape> sd(shapes.begin(), shapes.begin() + ng), sc_(shapes.begin() + ng, shapes.end());
+                for (JobShape &x : sc_) x.weight = 100;
+                int rc = make_tc(jd_tab, sd, data_rec);
+                if (rc) return rc;
+                rc = make_tc(jc_tab, sc_, count_rec);
+                if (rc) return rc;
+                out.push_back(data_rec);
+                out.push_back(count_rec);
+            } else {
+                LaunchRec tc;
+                const int rc = make_tc(jt, shapes, tc);
+                if (rc) return rc;
+                out.push_back(tc);
+            }
         }
     }
     // Size the scratch for the largest group, then bind it into every record.
@@ -1361,6 +1390,8 @@ int xe_set_option(const char *key, int64_t value) {
         g_opt.count_weight = int(value);
     } else if (!strcmp(key, "implicit_plans")) {
         g_opt.implicit_plans = value ? 1 : 0;
+    } else if (!strcmp(key, "count_launch")) {
+        g_opt.count_launch = value ? 1 : 0;
     } else if (!strcmp(key, "part_overhead")) {
         if (value < 0 || value > 100) return fail(XE_EINVAL, "part_overhead must lie in [0, 100]");
         g_opt.part_overhead = int(value);
