@@ -221,3 +221,33 @@ def test_ten_second_cadence_extreme_values_fit_int32(xe):
     diag = [i * N - i * (i - 1) // 2 for i in range(N)]
     assert np.all(vis[diag, 0] == 128 * F * fT) and np.all(vis[:, 1] == 0)
     assert np.all(vis[:, 0] == 128 * F * fT)
+
+
+@pytest.mark.parametrize("implicit", [1, 0])
+def test_implicit_plans_cover_every_tile_shape(xe, implicit):
+    # The server's batches run whole tiles decoded in the kernel from the job table (option
+    # implicit_plans 1) instead of host-built plans (0).  Inputs at the edges of the 128-row
+    # blocks and 256-wide column tiles (half tiles, empty rows of full tiles, one input):
+    # every integration equals the oracle either way, with channels of one shape batched.
+    xe.set_option("implicit_plans", implicit)
+    try:
+        for N in (1, 17, 127, 128, 129, 255, 256, 257, 383, 385, 512, 640, 2048):
+            fT, F, C = 128, 2, 3
+            data = {c: frames_for(N, fT, F, seed=N * 10 + c) for c in range(C)}
+            with xe.Stream(N, fT, F * fT, max_chan=C, hbm_budget=1 << 31, ring_frames=2,
+                           device_source=True) as st:
+                for c in range(C):
+                    assert st.admit(c) == 0
+                dev = {c: torch.from_numpy(data[c]).cuda() for c in range(C)}
+                torch.cuda.synchronize()
+                for k in range(F):
+                    rc = st.push_frames(list(range(C)), [dev[c][k] for c in range(C)], [k] * C)
+                    assert (rc == 0).all()
+                st.flush()
+                res = drain(st, C)
+            for meta, vis in res:
+                c = meta["chan"]
+                want = oracle.correlate_dense(data[c].reshape(1, F * fT, N), N, F * fT, 1)[0]
+                np.testing.assert_array_equal(vis, want, err_msg=f"N={N} chan {c}")
+    finally:
+        xe.set_option("implicit_plans", 1)
