@@ -106,10 +106,10 @@ int xe_correlate_host(const uint8_t *host_in, int N, int64_t T, int n_chan, int3
  * Both host buffers must stay untouched until then (pinned memory is required for the
  * copies to overlap).  Successive calls on different slots overlap: the device -> host copy
  * of one result runs while the next block is copied in and correlated.  Calling on a slot
- * that is still in flight returns XE_EAGAIN.  The input is copied in chunks of
- * "host_chunk_t" samples (option), each correlated as soon as it has landed (tensor-core
- * path).  Returns as xe_correlate_host (XE_ETIMEOUT from xe_host_wait if a device wait gave
- * up). */
+ * that is still in flight returns XE_EAGAIN.  The input is copied in one piece and then
+ * correlated (tensor-core path), or, with option "host_async_chunk_t", in chunks of that
+ * many samples, each correlated as soon as it has landed.  Returns as xe_correlate_host
+ * (XE_ETIMEOUT from xe_host_wait if a device wait gave up). */
 #define XE_HOST_SLOTS 4
 int xe_correlate_host_async(const uint8_t *host_in, int N, int64_t T, int n_chan, int32_t *host_vis, int slot);
 
@@ -441,9 +441,11 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *   "implicit_plans" 1 = batches of the streaming server run whole tiles dealt round-robin
  *                    over the CTAs, decoded in the kernel from the job table, with no plan
  *                    built on the host (default); 0 = host-built plans as for other calls;
- *   "host_chunk_t"   samples per chunk of the host-buffer entry points' copy/correlate
- *                    pipeline (0 = one copy then one correlation; else a multiple of 64;
- *                    default 8192).
+ *   "host_chunk_t"   samples per chunk of xe_correlate_host's copy/correlate pipeline
+ *                    (0 = one copy then one correlation; else a multiple of 64; default
+ *                    8192);
+ *   "host_async_chunk_t"  the same for xe_correlate_host_async (default 0: its calls
+ *                    overlap one another, and whole copies and correlations measured faster).
  * Returns XE_OK or XE_EINVAL. */
 int xe_set_option(const char *key, int64_t value);
 

@@ -56,6 +56,8 @@ struct Options {
     int inject_stall = 0;                  // test hook for the bounded-wait path (next call only)
     int64_t host_chunk_t = 8192;           // samples per pipelined chunk of xe_correlate_host
                                            // (0: one copy, then one correlation)
+    int64_t host_async_chunk_t = 0;        // the same for xe_correlate_host_async, whose
+                                           // calls overlap each other already
     int count_weight = 75;                 // cost of a count-job k-iteration, % of a data one
     int count_launch = 1;                  // 1: count jobs in a launch of their own after the
                                            // data jobs' (masked calls with counts; measured
@@ -1381,10 +1383,10 @@ int xe_set_option(const char *key, int64_t value) {
         g_opt.timing = value ? 1 : 0;
     } else if (!strcmp(key, "inject_stall")) {
         g_opt.inject_stall = value ? 1 : 0;
-    } else if (!strcmp(key, "host_chunk_t")) {
+    } else if (!strcmp(key, "host_chunk_t") || !strcmp(key, "host_async_chunk_t")) {
         if (value != 0 && (value < 64 || value > XE_MAX_T || value % 64 != 0))
-            return fail(XE_EINVAL, "host_chunk_t must be 0 or a multiple of 64 in [64, %lld]", (long long)XE_MAX_T);
-        g_opt.host_chunk_t = value;
+            return fail(XE_EINVAL, "%s must be 0 or a multiple of 64 in [64, %lld]", key, (long long)XE_MAX_T);
+        (key[5] == 'c' ? g_opt.host_chunk_t : g_opt.host_async_chunk_t) = value;
     } else if (!strcmp(key, "count_weight")) {
         if (value < 1 || value > 100) return fail(XE_EINVAL, "count_weight must lie in [1, 100]");
         g_opt.count_weight = int(value);
@@ -1542,7 +1544,7 @@ static int host_enqueue(Device *d, int slot, const uint8_t *host_in, int N, int6
     if (rc) return rc;
     rc = grow(reinterpret_cast<void **>(&io.d_vis), &io.vis_bytes, vis_bytes, false);
     if (rc) return rc;
-    const int64_t chunk = g_opt.host_chunk_t;
+    const int64_t chunk = slot == kHostSlots - 1 ? g_opt.host_chunk_t : g_opt.host_async_chunk_t;
     const int64_t n_chunks = (algo == XE_ALGO_IMMA || chunk == 0 || chunk >= T) ? 1 : (T + chunk - 1) / chunk;
     const int64_t step = n_chunks == 1 ? T : chunk;
     while (int64_t(io.landed.size()) < std::min<int64_t>(n_chunks, 64)) {
