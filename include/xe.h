@@ -357,11 +357,44 @@ int xe_stream_release(xe_stream *s, int64_t handle);
 int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *integrations,
                     int64_t *dropped);
 
-/* Scheduler counters, written to out[0 .. min(n, 8)): admitted channels, frames processed,
+/* Scheduler counters, written to out[0 .. min(n, 9)): admitted channels, frames processed,
  * integrations completed, frames dropped, scheduler passes that launched work, launch groups,
- * passes that held back to fill a batch, host nanoseconds spent enqueuing launches.
- * Returns the number of values written or a negative XE_* code. */
+ * passes that held back to fill a batch, host nanoseconds spent enqueuing launches,
+ * admissions refused for the HBM budget.  Returns the number of values written or a
+ * negative XE_* code. */
 int xe_stream_counters(xe_stream *s, int64_t *out, int n);
+
+/* Checkpoint of one channel's open integration.  The paper's X-engine nodes are diskless
+ * and keep no such state (section 3.1); this lets a server that restarts, or moves a channel
+ * to another GPU, continue an integration instead of dropping it.  Frame sequence numbers
+ * count from the channel's first frame, so integration k holds frames
+ * [k * F, (k + 1) * F) with F = integ_T / frame_T. */
+typedef struct xe_snapshot {
+    int64_t integ_index;      /* integration the sums belong to */
+    int64_t next_seq;         /* sequence number of the first frame not in the sums
+                                 (= integ_index * F + frames) */
+    int64_t frames;           /* frames of the integration covered, lost ones included (< F) */
+    int64_t n_samples;        /* samples in the sums (frames that arrived x frame_T) */
+    int lost;                 /* 1 if a frame of the integration was lost */
+    int64_t t_first_arrival_ns; /* arrival time of the integration's first frame */
+} xe_snapshot;
+
+/* Copy channel `chan`'s open integration to host_vis (HOST memory, [B][2] int32, the
+ * xe_result layout; zeros when no frame of it has been correlated yet) and its bookkeeping
+ * to *info.  The sums cover the frames the scheduler has launched (frames pushed but still
+ * queued are not in them and stay queued); integrations go on running.  Waits at most
+ * timeout_ms for the scheduler and at most as long again for the copy.  Returns XE_OK,
+ * XE_EINVAL (null pointers, channel not admitted or evicted meanwhile), XE_ETIMEOUT,
+ * XE_ENOMEM, XE_ECUDA or XE_ECLOSED. */
+int xe_stream_snapshot(xe_stream *s, int chan, int32_t *host_vis, xe_snapshot *info, int timeout_ms);
+
+/* Load a snapshot into channel `chan`, which must have been admitted and have taken no frame
+ * yet, on a stream with the same N, frame_T and integ_T.  The channel then expects frame
+ * info->next_seq next and completes integration info->integ_index with the sums of
+ * host_vis (HOST memory, [B][2] int32; may be NULL when info->n_samples == 0) added in.
+ * Returns XE_OK, XE_EINVAL (channel not fresh, or info inconsistent with this stream's frame
+ * and integration lengths), XE_ECUDA or XE_ECLOSED. */
+int xe_stream_restore(xe_stream *s, int chan, const int32_t *host_vis, const xe_snapshot *info);
 
 /* Close the stream: stops its threads, waits (bounded) for in-flight work and frees all
  * of its memory.  Results not yet released become invalid. */

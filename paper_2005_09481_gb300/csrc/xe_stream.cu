@@ -15,6 +15,12 @@
 // Admission is by HBM budget: a channel is admitted only if its accumulators, frame ring and
 // share of staging memory fit the stream's budget.  Lost frames (sequence gaps) are counted
 // and mark their integration incomplete; nothing shifts integration boundaries.
+//
+// Checkpoints: xe_stream_snapshot copies a channel's open integration (its sums so far and
+// the frame count they cover) to the host; xe_stream_restore loads such a copy into a newly
+// admitted channel of another stream, which then continues the integration from the next
+// frame.  The paper's nodes are diskless and keep no such state; this is for a server that
+// is restarted or moves a channel between GPUs.
 #include <algorithm>
 #include <atomic>
 #include <chrono>
@@ -97,6 +103,14 @@ struct PassEvent {
     int refs = 0;
 };
 
+// A checkpoint request, filled in by the scheduler thread between passes.
+struct SnapReq {
+    int chan = -1;
+    int state = 0;            // 0 asked, 1 served (copy enqueued), 2 channel gone
+    bool zero = false;        // the open integration holds no sums yet
+    xe_snapshot info{};
+};
+
 }  // namespace
 }  // namespace xe
 
@@ -127,6 +141,14 @@ struct xe_stream {
     int64_t hold_since = 0;          // first pass that held back a partial batch
     bool flush_req = false;
     int64_t n_launch_groups = 0, n_launch_passes = 0, n_held = 0, launch_ns = 0;
+    int64_t n_rejected = 0;          // admissions refused for the HBM budget
+
+    // Checkpoints: one request at a time (snap_mu), served by the scheduler thread.
+    std::mutex snap_mu;
+    xe::SnapReq *snap = nullptr;
+    std::condition_variable cv_snap;
+    int32_t *snap_host = nullptr;    // pinned copy of one accumulator
+    cudaEvent_t snap_ev = nullptr;   // the copy into snap_host has landed
 };
 
 namespace xe {
@@ -379,7 +401,7 @@ bool pass(xe_stream *s) {
             s->pass_events[size_t(pe)].refs += 1;
             s->queued_slots.push_back(code);
         }
-        s->n_frames += int64_t(n_jobs);
+        s->n_frames += int64_t(used.size());      // frames read (merged runs count each frame)
         s->n_launch_groups += n_groups;
         s->n_launch_passes += n_groups > 0 ? 1 : 0;
         s->launch_ns += t_l1 - t_l0;
@@ -403,10 +425,39 @@ bool pass(xe_stream *s) {
     return true;
 }
 
+// Serve a checkpoint request (between passes, so every frame the channel counts has its
+// launches on the compute stream already): record the integration's bookkeeping and put the
+// accumulator's copy on the compute stream, after those launches and before any later one.
+void serve_snapshot(xe_stream *s) {
+    std::lock_guard<std::mutex> lk(s->mu);
+    SnapReq *q = s->snap;
+    if (!q || q->state != 0) return;
+    const Chan &ch = s->chans[size_t(q->chan)];
+    if (!ch.admitted) {
+        q->state = 2;
+        s->cv_snap.notify_all();
+        return;
+    }
+    q->info.integ_index = ch.integ_index;
+    q->info.next_seq = ch.integ_index * s->frames_per_integ + ch.frames_in_integ;
+    q->info.frames = ch.frames_in_integ;
+    q->info.n_samples = ch.samples_in_integ;
+    q->info.lost = ch.lost ? 1 : 0;
+    q->info.t_first_arrival_ns = ch.t_first;
+    q->zero = ch.fresh[ch.cur];
+    if (!q->zero)
+        cudaMemcpyAsync(s->snap_host, ch.acc[ch.cur], s->acc_bytes, cudaMemcpyDeviceToHost, s->comp_s);
+    cudaEventRecord(s->snap_ev, s->comp_s);
+    q->state = 1;
+    s->cv_snap.notify_all();
+}
+
 void scheduler_main(xe_stream *s) {
     cudaSetDevice(s->dev);
     while (!s->stop.load()) {
-        if (!pass(s)) {
+        const bool worked = pass(s);
+        serve_snapshot(s);
+        if (!worked) {
             std::unique_lock<std::mutex> lk(s->mu);
             s->cv_work.wait_for(lk, std::chrono::microseconds(200));
         }
@@ -521,8 +572,10 @@ int xe_stream_admit(xe_stream *s, int chan) {
     if (chan < 0 || chan >= int(s->chans.size())) return sfail(XE_EINVAL, "channel id out of range");
     Chan &ch = s->chans[size_t(chan)];
     if (ch.admitted) return XE_OK;
-    if (s->used_bytes + int64_t(s->per_chan_bytes) > s->cfg.hbm_budget)
+    if (s->used_bytes + int64_t(s->per_chan_bytes) > s->cfg.hbm_budget) {
+        s->n_rejected += 1;
         return sfail(XE_EBUDGET, "HBM budget full");
+    }
     if (int(s->cfg.ring_frames) > 255) return sfail(XE_EINVAL, "ring too large");
     cudaSetDevice(s->dev);
     for (int a = 0; a < 2; ++a) {
@@ -707,10 +760,92 @@ int xe_stream_stats(xe_stream *s, int64_t *admitted, int64_t *frames, int64_t *i
 int xe_stream_counters(xe_stream *s, int64_t *out, int n) {
     if (!s || !out || n < 1) return sfail(XE_EINVAL, "bad counter query");
     std::lock_guard<std::mutex> lk(s->mu);
-    const int64_t v[8] = {s->n_admitted, s->n_frames, s->n_integ, s->n_dropped,
-                          s->n_launch_passes, s->n_launch_groups, s->n_held, s->launch_ns};
-    for (int k = 0; k < n && k < 8; ++k) out[k] = v[k];
-    return n < 8 ? n : 8;
+    const int64_t v[9] = {s->n_admitted, s->n_frames, s->n_integ, s->n_dropped,
+                          s->n_launch_passes, s->n_launch_groups, s->n_held, s->launch_ns,
+                          s->n_rejected};
+    for (int k = 0; k < n && k < 9; ++k) out[k] = v[k];
+    return n < 9 ? n : 9;
+}
+
+int xe_stream_snapshot(xe_stream *s, int chan, int32_t *host_vis, xe_snapshot *info, int timeout_ms) {
+    if (!s || !host_vis || !info) return sfail(XE_EINVAL, "null stream, buffer or snapshot");
+    if (timeout_ms < 0) return sfail(XE_EINVAL, "negative timeout");
+    std::lock_guard<std::mutex> one(s->snap_mu);
+    SnapReq q;
+    q.chan = chan;
+    {
+        std::unique_lock<std::mutex> lk(s->mu);
+        if (s->closed) return sfail(XE_ECLOSED, "stream closed");
+        if (chan < 0 || chan >= int(s->chans.size()) || !s->chans[size_t(chan)].admitted)
+            return sfail(XE_EINVAL, "channel not admitted");
+        if (!s->snap_host) {
+            cudaSetDevice(s->dev);
+            if (cudaHostAlloc(reinterpret_cast<void **>(&s->snap_host), s->acc_bytes, cudaHostAllocDefault) !=
+                cudaSuccess) {
+                cudaGetLastError();
+                s->snap_host = nullptr;
+                return sfail(XE_ENOMEM, "pinned snapshot buffer allocation failed");
+            }
+            if (cudaEventCreateWithFlags(&s->snap_ev, cudaEventDisableTiming) != cudaSuccess)
+                return sfail(XE_ECUDA, "event creation failed");
+        }
+        s->snap = &q;
+        s->cv_work.notify_one();
+        const bool served = s->cv_snap.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                                [&q] { return q.state != 0; });
+        s->snap = nullptr;            // the scheduler touches q only under s->mu
+        if (!served) return sfail(XE_ETIMEOUT, "snapshot: the scheduler did not serve the request in time");
+        if (q.state == 2) return sfail(XE_EINVAL, "channel evicted");
+    }
+    const int64_t deadline = now_ns() + int64_t(timeout_ms) * 1000000LL;
+    for (;;) {
+        const cudaError_t e = cudaEventQuery(s->snap_ev);
+        if (e == cudaSuccess) break;
+        if (e != cudaErrorNotReady) return sfail(XE_ECUDA, cudaGetErrorString(e));
+        if (now_ns() > deadline) return sfail(XE_ETIMEOUT, "snapshot: the copy did not land in time");
+        std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+    if (q.zero)
+        memset(host_vis, 0, s->acc_bytes);
+    else
+        memcpy(host_vis, s->snap_host, s->acc_bytes);
+    *info = q.info;
+    return XE_OK;
+}
+
+int xe_stream_restore(xe_stream *s, int chan, const int32_t *host_vis, const xe_snapshot *info) {
+    if (!s || !info) return sfail(XE_EINVAL, "null stream or snapshot");
+    std::lock_guard<std::mutex> lk(s->mu);
+    if (s->closed) return sfail(XE_ECLOSED, "stream closed");
+    if (chan < 0 || chan >= int(s->chans.size()) || !s->chans[size_t(chan)].admitted)
+        return sfail(XE_EINVAL, "channel not admitted");
+    Chan &ch = s->chans[size_t(chan)];
+    if (ch.expected_push != 0 || !ch.fifo.empty() || ch.integ_index != 0 || ch.frames_in_integ != 0 ||
+        !ch.fresh[ch.cur])
+        return sfail(XE_EINVAL, "restore needs a channel that has taken no frame since it was admitted");
+    const xe_snapshot &q = *info;
+    const int64_t fpi = s->frames_per_integ, fT = s->cfg.frame_T;
+    const bool ok = q.integ_index >= 0 && q.integ_index < (int64_t(1) << 40) && q.frames >= 0 &&
+                    q.frames < fpi && q.n_samples >= 0 && q.n_samples % fT == 0 &&
+                    q.n_samples <= q.frames * fT && (q.lost != 0 || q.n_samples == q.frames * fT) &&
+                    q.next_seq == q.integ_index * fpi + q.frames;
+    if (!ok) return sfail(XE_EINVAL, "inconsistent snapshot for this stream's frame and integration lengths");
+    if (q.n_samples > 0) {
+        if (!host_vis) return sfail(XE_EINVAL, "null visibilities for a snapshot with sums");
+        cudaSetDevice(s->dev);
+        // On the compute stream: every later launch that adds into this accumulator follows it.
+        const cudaError_t e = cudaMemcpyAsync(ch.acc[ch.cur], host_vis, s->acc_bytes, cudaMemcpyHostToDevice, s->comp_s);
+        if (e != cudaSuccess) return sfail(XE_ECUDA, cudaGetErrorString(e));
+        ch.fresh[ch.cur] = false;
+    }
+    ch.integ_index = q.integ_index;
+    ch.frames_in_integ = q.frames;
+    ch.samples_in_integ = q.n_samples;
+    ch.lost = q.lost != 0;
+    ch.t_first = q.frames > 0 ? q.t_first_arrival_ns : 0;
+    ch.t_last = ch.t_first;
+    ch.expected_push = q.next_seq;
+    return XE_OK;
 }
 
 void xe_stream_close(xe_stream *s) {
@@ -737,6 +872,8 @@ void xe_stream_close(xe_stream *s) {
         }
     }
     for (ResultBuf &rb : s->bufs) cudaFreeHost(rb.host);
+    if (s->snap_host) cudaFreeHost(s->snap_host);
+    if (s->snap_ev) cudaEventDestroy(s->snap_ev);
     for (Pending &p : s->pending) cudaEventDestroy(p.ev);
     for (cudaEvent_t e : s->spare_events) cudaEventDestroy(e);
     for (PassEvent &pe : s->pass_events) cudaEventDestroy(pe.ev);

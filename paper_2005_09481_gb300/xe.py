@@ -104,6 +104,8 @@ def load():
             "xe_stream_stats": ([p, p, p, p, p], i32),
             "xe_stream_close": ([p], None),
             "xe_stream_counters": ([p, p, i32], i32),
+            "xe_stream_snapshot": ([p, i32, p, p, i32], i32),
+            "xe_stream_restore": ([p, i32, p, p], i32),
         }
         for name, (args, res) in sigs.items():
             fn = getattr(L, name)
@@ -576,6 +578,12 @@ class Result(ctypes.Structure):
                 ("handle", ctypes.c_int64)]
 
 
+class Snapshot(ctypes.Structure):
+    _fields_ = [("integ_index", ctypes.c_int64), ("next_seq", ctypes.c_int64),
+                ("frames", ctypes.c_int64), ("n_samples", ctypes.c_int64), ("lost", ctypes.c_int),
+                ("t_first_arrival_ns", ctypes.c_int64)]
+
+
 class Stream:
     """Streaming server (xe_stream_*): admit channels, push frames, poll integrations."""
 
@@ -657,13 +665,34 @@ class Stream:
 
     def counters(self):
         import numpy as np
-        v = np.zeros(8, np.int64)
-        n = load().xe_stream_counters(self.h, v.ctypes.data, 8)
+        v = np.zeros(9, np.int64)
+        n = load().xe_stream_counters(self.h, v.ctypes.data, 9)
         if n < 0:
             _check(n, "xe_stream_counters")
         keys = ("admitted", "frames", "integrations", "dropped", "launch_passes",
-                "launch_groups", "held_passes", "launch_host_ns")
+                "launch_groups", "held_passes", "launch_host_ns", "rejected")
         return dict(zip(keys, v.tolist()))
+
+    def snapshot(self, chan: int, timeout_ms: int = 2000):
+        """Checkpoint of a channel's open integration: (info dict, int32 numpy [B, 2])."""
+        import numpy as np
+        vis = np.zeros((self.B, 2), np.int32)
+        info = Snapshot()
+        _check(load().xe_stream_snapshot(self.h, chan, ctypes.c_void_p(vis.ctypes.data),
+                                         ctypes.byref(info), timeout_ms), "xe_stream_snapshot")
+        return {k: getattr(info, k) for k, _ in Snapshot._fields_}, vis
+
+    def restore(self, chan: int, info: dict, vis=None):
+        """Continue a checkpointed integration on a newly admitted channel."""
+        import numpy as np
+        snap = Snapshot(*[int(info[k]) for k, _ in Snapshot._fields_])
+        ptr = None
+        if vis is not None:
+            vis = np.ascontiguousarray(vis, np.int32)
+            if vis.size != 2 * self.B:
+                raise ValueError("vis must hold B x 2 int32 values")
+            ptr = ctypes.c_void_p(vis.ctypes.data)
+        _check(load().xe_stream_restore(self.h, chan, ptr, ctypes.byref(snap)), "xe_stream_restore")
 
     def close(self):
         if self.h:

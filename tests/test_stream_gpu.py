@@ -53,6 +53,8 @@ def test_integrations_equal_oracle(xe, device_source):
                 while st.push(c, fr, k) == xe.XE_EAGAIN:
                     time.sleep(0.001)
         res = drain(st, C * n_int)
+        # Every frame counts once, also when consecutive frames were merged into one job.
+        assert st.stats()["frames"] == C * F * n_int
     for meta, vis in res:
         c, q = meta["chan"], meta["integ_index"]
         assert meta["complete"] == 1 and meta["n_samples"] == F * fT
@@ -251,3 +253,106 @@ def test_implicit_plans_cover_every_tile_shape(xe, implicit):
                 np.testing.assert_array_equal(vis, want, err_msg=f"N={N} chan {c}")
     finally:
         xe.set_option("implicit_plans", 1)
+
+
+def wait_frames(st, n, timeout_s=20.0):
+    t0 = time.time()
+    while st.stats()["frames"] < n and time.time() - t0 < timeout_s:
+        time.sleep(0.002)
+    assert st.stats()["frames"] >= n
+
+
+@pytest.mark.parametrize("device_source", [False, True])
+def test_snapshot_restore_continues_an_integration(xe, device_source):
+    # A checkpoint taken after 3 of 5 frames holds exactly those frames' sums; the stream it
+    # came from goes on undisturbed, and a second stream restored from it completes the same
+    # integration from frame 3 on: both equal the oracle of all 5 frames.
+    N, fT, F = 136, 1024, 5
+    data = frames_for(N, fT, F, seed=31)
+
+    def push(st, k):
+        fr = torch.from_numpy(data[k])
+        fr = fr.cuda() if device_source else fr
+        while st.push(2, fr, k) == xe.XE_EAGAIN:
+            time.sleep(0.001)
+
+    want_all = oracle.correlate_dense(data.reshape(1, F * fT, N), N, F * fT, 1)[0]
+    with xe.Stream(N, fT, F * fT, max_chan=4, hbm_budget=1 << 30, ring_frames=3,
+                   device_source=device_source) as st:
+        assert st.admit(2) == 0
+        info0, vis0 = st.snapshot(2)
+        assert info0["frames"] == 0 and info0["next_seq"] == 0 and not vis0.any()
+        for k in range(3):
+            push(st, k)
+        st.flush()
+        wait_frames(st, 3)
+        info, vis = st.snapshot(2)
+        assert (info["integ_index"], info["next_seq"], info["frames"], info["n_samples"], info["lost"]) == \
+            (0, 3, 3, 3 * fT, 0)
+        np.testing.assert_array_equal(vis, oracle.correlate_dense(data[:3].reshape(1, 3 * fT, N), N, 3 * fT, 1)[0])
+        for k in range(3, F):
+            push(st, k)
+        (meta, got), = drain(st, 1)
+        assert meta["complete"] == 1
+        np.testing.assert_array_equal(got, want_all)
+        # After the close the channel's next integration is empty.
+        info1, vis1 = st.snapshot(2)
+        assert (info1["integ_index"], info1["frames"], info1["next_seq"]) == (1, 0, F) and not vis1.any()
+
+    with xe.Stream(N, fT, F * fT, max_chan=4, hbm_budget=1 << 30, ring_frames=3,
+                   device_source=device_source) as st2:
+        assert st2.admit(2) == 0
+        bad = dict(info, next_seq=info["next_seq"] + 1)
+        with pytest.raises(xe.XeError) as e:
+            st2.restore(2, bad, vis)
+        assert e.value.code == xe.XE_EINVAL
+        st2.restore(2, info, vis)
+        with pytest.raises(xe.XeError) as e:            # a frame older than the checkpoint
+            st2.push(2, torch.from_numpy(data[2]).cuda() if device_source else torch.from_numpy(data[2]), 2)
+        assert e.value.code == xe.XE_EINVAL
+        for k in range(3, F):
+            push(st2, k)
+        (meta, got), = drain(st2, 1)
+        assert meta["integ_index"] == 0 and meta["complete"] == 1 and meta["n_samples"] == F * fT
+        np.testing.assert_array_equal(got, want_all)
+        with pytest.raises(xe.XeError) as e:            # the channel is no longer fresh
+            st2.restore(2, info, vis)
+        assert e.value.code == xe.XE_EINVAL
+
+
+def test_snapshot_with_lost_frames_and_a_later_integration(xe):
+    # A checkpoint inside the second integration, after a lost frame, restores onto a stream
+    # whose channel then finishes that integration as incomplete with the right sums.
+    N, fT, F = 64, 512, 4
+    data = frames_for(N, fT, 2 * F, seed=47)
+    with xe.Stream(N, fT, F * fT, max_chan=2, hbm_budget=1 << 30, ring_frames=2) as st:
+        assert st.admit(0) == 0
+        for k in (0, 1, 2, 3, 4, 6):                    # frame 5 never arrives
+            while st.push(0, torch.from_numpy(data[k]), k) == xe.XE_EAGAIN:
+                time.sleep(0.001)
+        st.flush()
+        (meta0, _), = drain(st, 1)
+        wait_frames(st, 6)
+        info, vis = st.snapshot(0)
+    assert (info["integ_index"], info["frames"], info["n_samples"], info["lost"], info["next_seq"]) == \
+        (1, 3, 2 * fT, 1, 7)
+    with xe.Stream(N, fT, F * fT, max_chan=2, hbm_budget=1 << 30, ring_frames=2) as st2:
+        assert st2.admit(1) == 0
+        st2.restore(1, info, vis)
+        while st2.push(1, torch.from_numpy(data[7]), 7) == xe.XE_EAGAIN:
+            time.sleep(0.001)
+        (meta, got), = drain(st2, 1)
+    assert meta["integ_index"] == 1 and meta["complete"] == 0 and meta["n_samples"] == 3 * fT
+    kept = np.concatenate([data[4], data[6], data[7]]).reshape(1, 3 * fT, N)
+    np.testing.assert_array_equal(got, oracle.correlate_dense(kept, N, 3 * fT, 1)[0])
+
+
+def test_rejected_admissions_are_counted(xe):
+    from paper_2005_09481_gb300 import serve
+    N, fT = 128, 1024
+    per = serve.per_channel_bytes(N, fT, 2)
+    with xe.Stream(N, fT, 2 * fT, max_chan=4, hbm_budget=2 * per, ring_frames=2) as st:
+        assert st.admit(0) == 0 and st.admit(1) == 0
+        assert st.admit(2) == xe.XE_EBUDGET and st.admit(3) == xe.XE_EBUDGET
+        c = st.counters()
+        assert c["admitted"] == 2 and c["rejected"] == 2
