@@ -53,6 +53,8 @@ extern "C" {
 #define XE_ECUDA     -7   /* a CUDA runtime call failed (detail in xe_last_error) */
 #define XE_ENODEV    -8   /* no usable sm_103 device */
 #define XE_ECLOSED   -9   /* the stream was closed */
+#define XE_ECHECK    -10  /* a device-side check of a launch's descriptors failed (option
+                             "checks"); the launch wrote nothing */
 
 #define XE_MAX_T 16777215LL   /* 128 * T < 2^31 */
 #define XE_MAX_N 65536
@@ -465,6 +467,17 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *   "autotune"       1 = time every (tile width, schedule) candidate the first time a
  *                    batch shape is correlated and keep the fastest for that shape;
  *   "timing"         1 = record device times of each call (see xe_last_timing);
+ *   "checks"         1 = before every tensor-core correlation launch, one block checks its
+ *                    descriptors on the device (job shapes, operand planes inside the
+ *                    staging scratch, every tile, k-range and workspace slot of the plan
+ *                    inside what was allocated) and on a violation sets the stream's status
+ *                    word instead of trapping; the staging and correlation kernels then
+ *                    return at once and xe_device_status (or the host-buffer calls) report
+ *                    XE_ECHECK.  Default 0; the environment variable XE_CHECKS=1 turns it on
+ *                    when the library loads;
+ *   "check_corrupt"  test hook for "checks" (accepted only while it is on): 1 = the plan of
+ *                    each launch claims no tiles, 2 = job 0's per-channel plane stride is off
+ *                    by 64 bytes; both are caught before any kernel reads through them;
  *   "count_launch"   1 = the valid-sample counts of a masked call run as a second
  *                    correlation launch after the visibilities' (default); 0 = one mixed launch;
  *   "count_weight"   cost of a count job's k-iteration (two sample blocks) in schedule 4,
@@ -523,8 +536,9 @@ int xe_tune_stats(int64_t *timed_candidates, int64_t *from_cache);
 int xe_runtime_counters(int64_t *out, int n);
 
 /* Synchronise `stream`, then read and clear the device status word of the scratch bound
- * to it.  Returns XE_OK, or XE_ETIMEOUT if a kernel gave up on a bounded wait (its output
- * is then invalid). */
+ * to it.  Returns XE_OK, XE_ETIMEOUT if a kernel gave up on a bounded wait (its output is
+ * then invalid), or XE_ECHECK if a descriptor check failed (option "checks"; the launch
+ * wrote nothing). */
 int xe_device_status(void *stream);
 
 /* The library keeps scratch memory (staged operand planes, workspace, counters, a status

@@ -36,6 +36,13 @@ static int fail(int code, const char *fmt, ...) {
 
 int record_error(int code, const char *msg) { return fail(code, "%s", msg); }
 
+// The error a nonzero device status word stands for.
+static int status_error(int st) {
+    if (st >= kStatusCheck && st < kStatusCheck + 16)
+        return fail(XE_ECHECK, "device-side check %d of a launch's descriptors failed", st - kStatusCheck);
+    return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
+}
+
 #define XE_CUDA(call)                                                                     \
     do {                                                                                  \
         cudaError_t e_ = (call);                                                          \
@@ -59,6 +66,10 @@ struct Options {
     int64_t host_async_chunk_t = 0;        // the same for xe_correlate_host_async, whose
                                            // calls overlap each other already
     int count_weight = 75;                 // cost of a count-job k-iteration, % of a data one
+    int checks = 0;                        // 1: a device-side check of every correlation launch's
+                                           // descriptors runs before it (XE_ECHECK on failure)
+    int check_corrupt = 0;                 // test hook (checks on only): 1 = the plan claims no
+                                           // tiles, 2 = job 0's plane stride is off by 64 bytes
     int count_launch = 1;                  // 1: count jobs in a launch of their own after the
                                            // data jobs' (masked calls with counts; measured
                                            // faster than one mixed launch); 0: one launch
@@ -69,6 +80,13 @@ struct Options {
                                            // decoded in the kernel); 0: host plans
 };
 static Options g_opt;
+
+// XE_CHECKS=1 in the environment turns the descriptor checks on when the library loads.
+static const bool g_env_checks = [] {
+    const char *p = getenv("XE_CHECKS");
+    if (p && *p && strcmp(p, "0") != 0) g_opt.checks = 1;
+    return g_opt.checks != 0;
+}();
 static std::mutex g_mu;
 
 // Host-side events of the runtime that can stall a caller (process-wide, under g_mu):
@@ -450,11 +468,13 @@ struct HostStreams {
 constexpr int kHostSlots = XE_HOST_SLOTS + 1;   // the last one serves xe_correlate_host
 
 struct LaunchRec {
-    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor
+    int kind;                     // 0 stage, 1 tensor-core correlation, 2 int8 anchor,
+                                  // 3 descriptor check of a correlation launch (option "checks")
     int eb;
     bool masked;                  // kind 0: the masking variant of the staging kernel
     JobTable jt;
     PlanDev pd;
+    CheckLimits lim;              // kind 1 and 3: the lengths of the plan's device arrays
 };
 
 struct GraphRec {
@@ -869,6 +889,8 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             const int ng = int(std::min(act.size() - g0, group));
             std::vector<JobShape> shapes;
             LaunchRec st{};
+            st.jt.status = sc->status;
+            st.jt.checks = g_opt.checks;
             st.kind = 0;
             st.eb = eb;
             JobTable &jt = st.jt;
@@ -1007,6 +1029,11 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
                 pd.counters = nullptr;
                 pd.status = sc->status;
                 pd.inject_stall = g_opt.inject_stall;
+                tc.lim = CheckLimits{};
+                tc.lim.n_tiles = int(p->host.tiles.size());
+                tc.lim.n_segs = int(p->host.segs.size());
+                tc.lim.n_seg_off = int(p->host.seg_off.size());
+                tc.lim.n_tile_slots = int(p->host.tile_slots.size());
                 // All CTAs of the launch must be resident together for the exchange's wait.
                 pd.pair_exchange = p->host.pair_exchange && p->host.n_cta <= d->n_sm ? 1 : 0;
                 return XE_OK;
@@ -1053,8 +1080,32 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
             if (rec.kind == 1) {
                 rec.pd.ws = sc->ws;
                 rec.pd.counters = sc->counters;
+                rec.lim.planes = sc->planes;
+                rec.lim.planes_bytes = int64_t(sc->planes_bytes);
+                rec.lim.ws_slots = int64_t(sc->ws_bytes / (size_t(kWsSlotElems) * sizeof(int32_t)));
+                rec.lim.n_counters = int64_t(sc->counters_bytes / sizeof(int));
             }
         }
+    }
+    if (g_opt.checks) {
+        // Each group's checks run before its staging (which writes through the job table):
+        // one check record per correlation launch of the group, then the group's records.
+        std::vector<LaunchRec> grouped(out.begin(), out.begin() + std::ptrdiff_t(first_rec));
+        for (size_t r = first_rec; r < out.size();) {
+            size_t e = r + 1;
+            while (e < out.size() && out[e].kind != 0) ++e;
+            for (size_t k = r; k < e; ++k) {
+                if (out[k].kind != 1) continue;
+                if (g_opt.check_corrupt == 1) out[k].pd.n_tiles = 0;
+                if (g_opt.check_corrupt == 2) out[k].jt.jobs[0].plane_chan_bytes += 64;
+                LaunchRec c = out[k];
+                c.kind = 3;
+                grouped.push_back(c);
+            }
+            for (size_t k = r; k < e; ++k) grouped.push_back(out[k]);
+            r = e;
+        }
+        out.swap(grouped);
     }
     return XE_OK;
 }
@@ -1062,6 +1113,7 @@ static int build_launches(Device *d, Scratch *sc, const xe_job *jobs, int n_jobs
 static cudaError_t enqueue(const LaunchRec &r, cudaStream_t s) {
     if (r.kind == 0) return launch_stage(r.jt, r.eb, s, r.masked);
     if (r.kind == 1) return launch_tc(r.jt, r.pd, r.eb, s);
+    if (r.kind == 3) return launch_check(r.jt, r.pd, r.lim, s);
     return launch_imma(r.jt, s);
 }
 
@@ -1069,6 +1121,7 @@ static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
     cudaKernelNodeParams p{};
     args[0] = const_cast<JobTable *>(&r.jt);
     args[1] = const_cast<PlanDev *>(&r.pd);
+    args[2] = const_cast<CheckLimits *>(&r.lim);
     p.kernelParams = args;
     p.extra = nullptr;
     if (r.kind == 0) {
@@ -1081,6 +1134,11 @@ static cudaKernelNodeParams node_params(const LaunchRec &r, void **args) {
         p.gridDim = dim3(unsigned(r.pd.n_cta));
         p.blockDim = dim3(kTcThreads);
         p.sharedMemBytes = unsigned(tc_smem_bytes());
+    } else if (r.kind == 3) {
+        p.func = const_cast<void *>(check_kernel_fn());
+        p.gridDim = dim3(1);
+        p.blockDim = dim3(256);
+        p.sharedMemBytes = 0;
     } else {
         p.func = const_cast<void *>(imma_kernel_fn());
         p.gridDim = dim3(unsigned(r.jt.total_stage_blocks));
@@ -1194,7 +1252,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
             XE_CUDA(cudaGraphCreate(&g->graph, 0));
             cudaGraphNode_t prev = nullptr;
             for (const LaunchRec &r : recs) {
-                void *args[2];
+                void *args[3];
                 cudaKernelNodeParams kp = node_params(r, args);
                 cudaGraphNode_t node;
                 XE_CUDA(cudaGraphAddKernelNode(&node, g->graph, prev ? &prev : nullptr, prev ? 1 : 0, &kp));
@@ -1206,7 +1264,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
         } else {
             g = it->second;
             for (size_t k = 0; k < recs.size(); ++k) {
-                void *args[2];
+                void *args[3];
                 cudaKernelNodeParams kp = node_params(recs[k], args);
                 XE_CUDA(cudaGraphExecKernelNodeSetParams(g->exec, g->nodes[k], &kp));
             }
@@ -1217,7 +1275,7 @@ static int run_jobs(const xe_job *jobs, int n_jobs, int algo, cudaStream_t s, in
     } else {
         bool marked = false;
         for (const LaunchRec &r : recs) {
-            if (timing && !marked && r.kind != 0) {
+            if (timing && !marked && r.kind != 0 && r.kind != 3) {
                 XE_CUDA(cudaEventRecord(sc->ev[1], s));   // staging done (or none)
                 marked = true;
             }
@@ -1344,6 +1402,7 @@ const char *xe_strerror(int code) {
         case XE_ECUDA: return "CUDA error";
         case XE_ENODEV: return "no usable sm_103 device";
         case XE_ECLOSED: return "stream closed";
+        case XE_ECHECK: return "a device-side check of a launch's descriptors failed";
         default: return "unknown error";
     }
 }
@@ -1394,6 +1453,13 @@ int xe_set_option(const char *key, int64_t value) {
         g_opt.implicit_plans = value ? 1 : 0;
     } else if (!strcmp(key, "count_launch")) {
         g_opt.count_launch = value ? 1 : 0;
+    } else if (!strcmp(key, "checks")) {
+        g_opt.checks = value ? 1 : 0;
+        if (!g_opt.checks) g_opt.check_corrupt = 0;
+    } else if (!strcmp(key, "check_corrupt")) {
+        if (value < 0 || value > 2) return fail(XE_EINVAL, "check_corrupt must lie in [0, 2]");
+        if (value && !g_opt.checks) return fail(XE_EINVAL, "check_corrupt needs option \"checks\" on");
+        g_opt.check_corrupt = int(value);
     } else if (!strcmp(key, "part_overhead")) {
         if (value < 0 || value > 100) return fail(XE_EINVAL, "part_overhead must lie in [0, 100]");
         g_opt.part_overhead = int(value);
@@ -1598,7 +1664,7 @@ static int host_finish(Device *d, int slot) {
             XE_CUDA(cudaMemset(it->second->status, 0, sizeof(int)));
             if (it->second->counters) XE_CUDA(cudaMemset(it->second->counters, 0, it->second->counters_bytes));
             XE_CUDA(cudaStreamSynchronize(0));
-            return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
+            return status_error(st);
         }
     }
     return XE_OK;
@@ -1874,7 +1940,7 @@ int xe_device_status(void *stream) {
         if (it->second->counters)
             XE_CUDA(cudaMemset(it->second->counters, 0, it->second->counters_bytes));
         XE_CUDA(cudaStreamSynchronize(0));
-        return fail(XE_ETIMEOUT, "device wait timed out (status %d)", st);
+        return status_error(st);
     }
     return XE_OK;
 }

@@ -91,6 +91,10 @@ struct JobTable {
     int accumulate;           // 1: add into vis instead of overwriting
     int64_t total_stage_blocks;
     JobDev jobs[kMaxJobs];
+    int *status;              // device status word of the launch's stream
+    int checks;               // 1 (option "checks"): a descriptor check ran before this launch;
+                              // the kernels do nothing once the status word is set
+    int reserved;
 };
 
 // One output tile of the triangle: rows [i0, i0+128), columns [j0, j0+nj).
@@ -151,7 +155,24 @@ enum DeviceStatus : int {
     kStatusTimeoutProducer = 1,
     kStatusTimeoutMma = 2,
     kStatusTimeoutEpilogue = 3,
+    kStatusCheck = 16,        // + the number (0..15) of the descriptor check that failed
 };
+
+// What a launch's descriptors may address (option "checks"): the staging scratch and the
+// lengths of the plan's device arrays, as allocated on the host.
+struct CheckLimits {
+    const uint8_t *planes;    // staged operands live in [planes, planes + planes_bytes)
+    int64_t planes_bytes;
+    int64_t ws_slots;         // workspace slots of kWsSlotElems int32
+    int64_t n_counters;       // per-tile arrival counters
+    int n_tiles;              // entries of pd.tiles
+    int n_segs;               // entries of pd.segs
+    int n_seg_off;            // entries of pd.seg_off
+    int n_tile_slots;         // entries of pd.tile_slots
+};
+
+cudaError_t launch_check(const JobTable &jt, const PlanDev &pd, const CheckLimits &lim, cudaStream_t s);
+const void *check_kernel_fn();
 
 // ---- phased-array beams (xe_beam.cu) ---------------------------------------------------
 

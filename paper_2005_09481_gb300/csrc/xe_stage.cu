@@ -63,6 +63,7 @@ __global__ void __launch_bounds__(256) stage_kernel(const __grid_constant__ JobT
     __shared__ uint32_t lut[256];
 
     const int tid = threadIdx.x;
+    if (jt.checks && __syncthreads_or(tid == 0 && *reinterpret_cast<volatile int *>(jt.status) != 0)) return;
     {
         const NibbleCodes &nc = EB == 1 ? c_codes_e4m3 : c_codes_f16;
         lut[tid] = uint32_t(nc.c[tid >> 4]) | (uint32_t(nc.c[tid & 15]) << 16);
@@ -222,6 +223,8 @@ __global__ void __launch_bounds__(256) stage_e4m3_kernel(const __grid_constant__
     // than an SM has beside even one staging block, so they only start on SMs this grid has
     // left, and they wait for it to complete before reading the planes.
     asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    // With descriptor checks on, a failed check stops the staging before it reads a job.
+    if (jt.checks && __syncthreads_or(tid == 0 && *reinterpret_cast<volatile int *>(jt.status) != 0)) return;
 
     auto vec_ok = [&](const JobDev &jb) { return view_vec_ok(jb); };
     // Flag rows can be copied 16 bytes at a time when every row starts 16-byte aligned.

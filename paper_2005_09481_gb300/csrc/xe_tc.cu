@@ -178,6 +178,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
     volatile int *status = plan.status;
+    // With descriptor checks on, a failed check (or an earlier timeout not yet reported)
+    // stops the launch before it reads a descriptor; the whole CTA decides together.
+    if (jt.checks && __syncthreads_or(threadIdx.x == 0 && *status != 0)) return;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < kStages; ++s) {

@@ -16,6 +16,7 @@ from . import build as _build
 
 XE_OK, XE_EINVAL, XE_EOVERFLOW, XE_ENOMEM, XE_EBUDGET = 0, -1, -2, -3, -4
 XE_EAGAIN, XE_ETIMEOUT, XE_ECUDA, XE_ENODEV, XE_ECLOSED = -5, -6, -7, -8, -9
+XE_ECHECK = -10
 XE_MAX_T, XE_MAX_N = 16777215, 65536          # samples per integration (128 T < 2^31), inputs
 ALGOS = {"auto": 0, "tc": 1, "imma": 2}
 

@@ -36,7 +36,7 @@ def test_binding_constants_match_the_header():
     src = open(os.path.join(ROOT, "include", "xe.h")).read()
     defs = {k: int(v) for k, v in re.findall(r"#define\s+(XE_\w+)\s+(-?\d+)(?:LL)?\b", src)}
     for name in ("XE_OK", "XE_EINVAL", "XE_EOVERFLOW", "XE_ENOMEM", "XE_EBUDGET", "XE_EAGAIN",
-                 "XE_ETIMEOUT", "XE_ECUDA", "XE_ENODEV", "XE_ECLOSED", "XE_MAX_T", "XE_MAX_N"):
+                 "XE_ETIMEOUT", "XE_ECUDA", "XE_ENODEV", "XE_ECLOSED", "XE_ECHECK", "XE_MAX_T", "XE_MAX_N"):
         assert getattr(xe, name) == defs[name], name
     assert 128 * xe.XE_MAX_T < 2**31 <= 128 * (xe.XE_MAX_T + 1)
 
@@ -486,3 +486,17 @@ def test_binding_checks_tensors_before_calling_the_library():
             xe.correlate_host(x, N, T, 1, out=bad)                                         # bad outputs
     with pytest.raises(ValueError):
         xe.correlate_batch([(x, torch.zeros((1, B, 2), dtype=torch.int32), N, T, 1)])      # host input
+
+
+def test_check_corruption_hook_needs_the_checks():
+    # The corruption test hook is refused unless the descriptor checks are on, so that no
+    # corrupted descriptor can reach a kernel unchecked.
+    L = xe.load()
+    assert L.xe_set_option(b"checks", 0) == xe.XE_OK
+    assert L.xe_set_option(b"check_corrupt", 1) == xe.XE_EINVAL
+    assert L.xe_set_option(b"checks", 1) == xe.XE_OK
+    assert L.xe_set_option(b"check_corrupt", 3) == xe.XE_EINVAL
+    assert L.xe_set_option(b"check_corrupt", 2) == xe.XE_OK
+    assert L.xe_set_option(b"checks", 0) == xe.XE_OK      # also clears the hook
+    assert L.xe_set_option(b"check_corrupt", 0) == xe.XE_OK
+    assert L.xe_strerror(xe.XE_ECHECK).startswith(b"a device-side check")
