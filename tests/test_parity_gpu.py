@@ -52,6 +52,34 @@ def test_config1_plain_single_channel(xe, algo):
     assert_exact(run(xe, p, N, T, 1, algo), oracle.correlate(p, N, T, 1), algo)
 
 
+def test_maximum_input_count(xe):
+    # N = XE_MAX_N = 65536 inputs: 2.1e9 baselines, a 17.2 GB output, 65,536 triangle tiles;
+    # T = 96 samples (one full and one ragged k-block).  Checked against the oracle on
+    # sampled baselines computed one by one: every pair of a set of rows and columns at the
+    # tile edges and the array's ends, and 4096 random pairs.  The packed index passes 2^31.
+    N, T = xe.XE_MAX_N, 96
+    p = synth.uniform(N, T, 1, seed=4242)
+    dev = torch.from_numpy(p).cuda()
+    out = xe.correlate(dev, N, T, 1)
+    torch.cuda.synchronize()
+    xe.device_status()
+    edges = [0, 1, 127, 128, 129, 255, 256, 257, N // 2 - 1, N // 2, N - 257, N - 256, N - 129,
+             N - 128, N - 2, N - 1]
+    pairs = [(a, b) for a in edges for b in edges if a <= b]
+    rng = np.random.default_rng(99)
+    u, v = rng.integers(0, N, 4096), rng.integers(0, N, 4096)
+    pairs += [(int(min(a, b)), int(max(a, b))) for a, b in zip(u, v)]
+    i = np.array([a for a, _ in pairs], np.int64)
+    j = np.array([b for _, b in pairs], np.int64)
+    k = i * N - i * (i - 1) // 2 + (j - i)
+    assert k.max() > 2**31
+    got = out[0][torch.from_numpy(k).cuda()].cpu().numpy().astype(np.int64)
+    want = oracle.pairs(p, N, T, 1, np.zeros_like(i), i, j)
+    assert_exact(got, want, "N=XE_MAX_N sampled baselines")
+    del out, dev
+    torch.cuda.empty_cache()
+
+
 SHAPES = [(1, 1, 1), (2, 1, 1), (3, 5, 2), (17, 63, 1), (64, 64, 1), (100, 65, 3),
           (129, 127, 1), (255, 200, 1), (256, 1000, 1), (257, 129, 2), (300, 77, 1),
           (513, 300, 1), (640, 4096, 1)]
