@@ -18,7 +18,8 @@ bounded sample of the same workload.  --workload masked (also summarised under "
 the default line) times the flag-masked correlation with valid-sample counts;
 --workload beams (also under "beams") the 10 phased-array beams of the same input;
 --workload corner (also under "corner") the corner turn of cylinder bundles and the
-correlation read straight from the bundles.
+correlation read straight from the bundles; --workload small (also under "small") the
+latency of the smallest configuration, N = 64, T = 1024, one channel.
 """
 from __future__ import annotations
 
@@ -486,6 +487,85 @@ def measure_corner(steps, warmup, dev, flush, check=True):
     return res
 
 
+SMALL_WORKLOAD = "small single channel: N=64, T=1024, 1 channel, quantised Gaussian + plane wave"
+
+
+def measure_small(steps, warmup, dev, flush, check=True):
+    """Latency of the smallest configuration (N=64, T=1024, one channel: 9 tiles' worth of a
+    launch), through each entry point that can serve it: device time of one call after an
+    L2 flush (cold) and per call back to back (warm, input and planes in L2), the host's
+    round trip of one call (enqueue + synchronise), and the same call replayed as a
+    one-job CUDA graph and through the allocation-free entry point."""
+    import numpy as np
+    import torch
+    from paper_2005_09481_gb300 import synth, xe
+    N, T = 64, 1024
+    packed = synth.gauss_plane(N, T, 1)
+    d_in = torch.from_numpy(packed).to(dev)
+    out = xe.empty_vis(N, 1, dev)
+    stream = torch.cuda.current_stream(dev)
+    calls = {
+        "correlate": lambda: xe.correlate(d_in, N, T, 1, out=out, stream=stream),
+        "graph": lambda: xe.correlate_batch([(d_in, out, N, T, 1)], use_graph=True, stream=stream),
+        "noalloc": lambda: xe.correlate_noalloc(d_in, N, T, 1, out=out, stream=stream),
+    }
+    res = {"workload": SMALL_WORKLOAD}
+    for name, fn in calls.items():
+        for _ in range(warmup):
+            fn()
+        torch.cuda.synchronize()
+        cold = []
+        for k in range(max(20, min(steps, 200))):
+            flush.fill_(k & 0xFF)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            cold.append((a, b))
+        torch.cuda.synchronize()
+        n_warm = max(100, min(steps, 1000))
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(n_warm):
+            fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        rt = []
+        for _ in range(200):
+            t0 = time.perf_counter()
+            fn()
+            torch.cuda.synchronize()
+            rt.append(time.perf_counter() - t0)
+        res[name] = {"cold_us": statistics.median(x.elapsed_time(y) for x, y in cold) * 1e3,
+                     "warm_us_per_call": a.elapsed_time(b) * 1e3 / n_warm,
+                     "host_round_trip_us": statistics.median(rt) * 1e6}
+    xe.device_status(stream)
+    if check:
+        import oracle
+        res["exact"] = bool(np.array_equal(out.cpu().numpy(), oracle.correlate(packed, N, T, 1)))
+    return res
+
+
+def run_small_workload(args):
+    import torch
+    from paper_2005_09481_gb300 import xe
+    xe.load()
+    dev = torch.device("cuda", 0)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    uuid = str(torch.cuda.get_device_properties(dev).uuid)
+    with ClockSampler(uuid) as clk:
+        m = measure_small(args.steps, args.warmup, dev, flush)
+    ms = m["correlate"]["cold_us"] * 1e-3
+    line = {"metric": METRIC, "value": xe.cmac(64, 1024, 1) / (ms * 1e-3), "unit": UNIT, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3", "data": "synthetic",
+            "config": {"workload": SMALL_WORKLOAD, "N": 64, "T": 1024, "n_chan": 1,
+                       "l2": f"flushed before every timed call ({L2_FLUSH_BYTES >> 20} MiB write)"},
+            "small": m, "clocks": clk.summary(), "gpu_launches": 2 * args.steps}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_corner_workload(args):
     import torch
     from paper_2005_09481_gb300 import xe
@@ -569,10 +649,11 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="xe", choices=["xe", "reference"])
     ap.add_argument("--workload", default="headline",
-                    choices=["headline", "batch16", "uneven64", "stream", "masked", "beams", "corner"])
+                    choices=["headline", "batch16", "uneven64", "stream", "masked", "beams", "corner", "small"])
     ap.add_argument("--no-masked", action="store_true")
     ap.add_argument("--no-beams", action="store_true")
     ap.add_argument("--no-corner", action="store_true")
+    ap.add_argument("--no-small", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-stream", action="store_true")
     ap.add_argument("--stream-channels", type=int, default=320)
@@ -600,6 +681,8 @@ def main():
         return run_beam_workload(args)
     if args.workload == "corner":
         return run_corner_workload(args)
+    if args.workload == "small":
+        return run_small_workload(args)
 
     import numpy as np
     import torch
@@ -776,6 +859,9 @@ def main():
     corner = None
     if ws == 1 and not args.no_corner:
         corner = measure_corner(max(10, min(50, args.steps // 20)), 3, dev, flush)
+    small = None
+    if ws == 1 and not args.no_small:
+        small = measure_small(max(20, min(200, args.steps // 10)), 5, dev, flush)
 
     if rank == 0:
         bf16, hbm, src = peaks()
@@ -838,6 +924,7 @@ def main():
             "masked": masked,
             "beams": beams,
             "corner": corner,
+            "small": small,
             "paper_context": {"fiji_chip_cmac_s": 1.10e12, "note": "derived from Table tab:computing "
                               "(93.4 ms per 49152-sample block at N=2048), AMD S9300x2, 722 MHz"},
         }

@@ -201,7 +201,8 @@ int xe_plan_stats(const int *N, const int64_t *T, const int *n_chan, int n_jobs,
                   int64_t *n_tiles, int64_t *n_iters, int64_t *n_split_tiles);
 
 /* Dump the plan the scheduler builds for a batch, for a given CTA count, schedule
- * (-1 = the default choice; 0 stream-K, 1 equal k-split, 2 full waves + stream-K tail,
+ * (-1 = the default choice; 0 stream-K, 1 equal k-split (parts per tile by a fix-up cost
+ * model), 2 full waves + the last wave split the same way,
  * 3 longest-first, 4 k-aligned parts of about equal weighted cost, longest first; the
  * default for masked calls with counts, whose count jobs weigh less) and tile width
  * (0 = default, 128 or 256).  Writes into out[0..cap):

@@ -273,16 +273,44 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
     deal(best_s, &per);
 }
 
+// Fix-up cost of splitting a tile, in k-blocks of mainloop time (split schedule).
+constexpr double kPairFixKb = 8.0;     // two parts: the symmetric column-half exchange
+constexpr double kPartFixKb = 13.0;    // each further part: summed by the last arriving part
+
+// Parts per tile for tiles [t0, t1) dealt over G CTAs: up to the CTAs per tile (and the
+// k-blocks of the shortest tile), chosen to minimise max k-blocks per part + fix-up.
+static int split_parts(const std::vector<Tile> &tiles, int t0, int t1, int G) {
+    const int n = t1 - t0;
+    int min_kb = 1 << 30, max_kb = 0;
+    for (int t = t0; t < t1; ++t) {
+        min_kb = std::min(min_kb, tiles[size_t(t)].kblocks);
+        max_kb = std::max(max_kb, tiles[size_t(t)].kblocks);
+    }
+    const int s_max = std::min(n < G ? std::max(1, G / n) : 1, std::max(1, min_kb));
+    int s = 1;
+    double best = double(max_kb);
+    for (int c = 2; c <= s_max; ++c) {
+        const double cost = double(max_kb) / c + (c == 2 ? kPairFixKb : kPartFixKb * (c - 1));
+        if (cost < best) {
+            best = cost;
+            s = c;
+        }
+    }
+    return s;
+}
+
 static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weight) {
     const int n = int(p.tiles.size());
     std::vector<std::vector<Seg>> per(static_cast<size_t>(G));
     if (sched == kSchedWeighted) {
         schedule_weighted(p, G, weight, per);
     } else if (sched == kSchedSplit) {
-        int s = n < G ? std::max(1, G / n) : 1;
-        int min_kb = 1 << 30;
-        for (const Tile &t : p.tiles) min_kb = std::min(min_kb, t.kblocks);
-        s = std::min(s, std::max(1, min_kb));
+        // Parts per tile: up to the CTAs per tile, chosen by a cost model in k-blocks.  A
+        // split shortens the mainloop but each part past the first costs a fix-up: two parts
+        // swap column halves through the workspace (about kPairFixKb k-blocks of time), more
+        // parts are summed by the last arriving part (about kPartFixKb each; measured on the
+        // GB300, where 64 parts of a 64-k-block tile took ten times as long as two).
+        const int s = split_parts(p.tiles, 0, n, G);
         int64_t item = 0;
         const int64_t n_items = int64_t(n) * s;
         const int64_t g = std::min<int64_t>(G, n_items);
@@ -293,10 +321,24 @@ static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weig
                 if (hi > lo) per[size_t(item % g)].push_back(Seg{t, lo, hi, -1});
             }
     } else if (sched == kSchedHybrid) {
+        // Whole tiles in full waves; the last partial wave's tiles split by the same cost
+        // model as the split schedule over the CTAs it leaves (whole when it leaves fewer
+        // than two per tile).  An equal stream-K share of that wave over every CTA cut small
+        // tails into many parts, and their fix-up outweighed the balance.
         const int full = (n / G) * G;
         for (int t = 0; t < full; ++t)
             per[size_t(t % G)].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
-        stream_k(p.tiles, full, n, G, per);
+        const int m = n - full;
+        if (m > 0) {
+            const int s = split_parts(p.tiles, full, n, G);
+            int64_t item = 0;
+            for (int t = full; t < n; ++t)
+                for (int k = 0; k < s; ++k, ++item) {
+                    const int kb = p.tiles[size_t(t)].kblocks;
+                    const int lo = int(int64_t(k) * kb / s), hi = int(int64_t(k + 1) * kb / s);
+                    if (hi > lo) per[size_t(item % G)].push_back(Seg{t, lo, hi, -1});
+                }
+        }
     } else if (sched == kSchedLPT) {
         // Longest tile first to the least-loaded CTA; every CTA then walks its tiles in tile
         // order.  (Batches whose jobs arrive longest first are already in order.)

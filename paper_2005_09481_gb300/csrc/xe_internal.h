@@ -139,8 +139,10 @@ struct PlanDev {
 // Triangle schedules (host-side choice; the kernel just follows the segment lists).
 enum Sched : int {
     kSchedStreamK = 0,        // equal contiguous ranges of the concatenated k-iterations
-    kSchedSplit = 1,          // each tile split into s equal k-parts, parts dealt round-robin
-    kSchedHybrid = 2,         // whole tiles in full waves, the last partial wave stream-K
+    kSchedSplit = 1,          // each tile split into s equal k-parts, parts dealt round-robin;
+                              // s from a cost model (mainloop saved against fix-up)
+    kSchedHybrid = 2,         // whole tiles in full waves, the last partial wave's tiles split
+                              // as in kSchedSplit over the CTAs
     kSchedLPT = 3,            // whole tiles, longest first, to the least-loaded CTA
     kSchedWeighted = 4,       // tiles cut into k-aligned parts of about equal weighted cost
                               // (count jobs weigh less than data jobs), longest part first
