@@ -231,6 +231,10 @@ struct LeastLoaded {
 // CTAs still read nearby k-blocks at the same time (shared in L2) while light count-job
 // parts fill the gaps left by data-job parts.  A part costs kblocks/s * weight, plus a
 // modelled fix-up cost when s > 1; the s in [1, 4] with the smallest modelled makespan wins.
+// Fix-up cost of splitting a tile, in k-blocks of mainloop time (split, hybrid and weighted schedules).
+constexpr double kPairFixKb = 8.0;     // two parts: the symmetric column-half exchange
+constexpr double kPartFixKb = 13.0;    // each further part: summed by the last arriving part
+
 static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &weight,
                               std::vector<std::vector<Seg>> &per) {
     const int n = int(p.tiles.size());
@@ -247,7 +251,11 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
     if (!std::is_sorted(order.begin(), order.end(), heavier)) std::stable_sort(order.begin(), order.end(), heavier);
     auto deal = [&](int s, std::vector<std::vector<Seg>> *out) {
         LeastLoaded<double> ll(G);
-        const double over = s > 1 ? g_opt.part_overhead / 100.0 * max_kb : 0.0;
+        // Fix-up cost charged to every part of a split tile: the option's share of the longest
+        // tile, but never less than the measured absolute cost (short tiles).
+        const double over = s > 1 ? std::max(g_opt.part_overhead / 100.0 * max_kb,
+                                             s == 2 ? kPairFixKb : kPartFixKb * (s - 1))
+                                  : 0.0;
         double makespan = 0;
         for (int k = 0; k < s; ++k)
             for (int t : order) {
@@ -272,10 +280,6 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
     }
     deal(best_s, &per);
 }
-
-// Fix-up cost of splitting a tile, in k-blocks of mainloop time (split schedule).
-constexpr double kPairFixKb = 8.0;     // two parts: the symmetric column-half exchange
-constexpr double kPartFixKb = 13.0;    // each further part: summed by the last arriving part
 
 // Parts per tile for tiles [t0, t1) dealt over G CTAs: up to the CTAs per tile (and the
 // k-blocks of the shortest tile), chosen to minimise max k-blocks per part + fix-up.
