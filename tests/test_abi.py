@@ -306,6 +306,47 @@ def test_hybrid_schedule_full_waves_whole():
     assert whole >= (1152 // 152) * 152            # full waves are whole tiles
 
 
+def _parts_per_tile(d):
+    counts = {}
+    for (cta, t, lo, hi, slot) in d["segs"]:
+        counts[int(t)] = counts.get(int(t), 0) + 1
+    return sorted(set(counts.values()))
+
+
+def test_split_parts_follow_the_fix_up_cost_model():
+    # Parts per tile minimise (longest tile's k-blocks / parts) + fix-up, with 8 k-blocks for
+    # two parts (the column-half exchange) and 13 per part beyond the first (the last
+    # arriver's sum), up to the CTAs per tile; the default schedule for fewer tiles than
+    # CTAs is the split, also for jobs of different lengths.
+    def model(kb, s_max):
+        cost = {1: kb}
+        for c in range(2, s_max + 1):
+            cost[c] = kb / c + (8 if c == 2 else 13 * (c - 1))
+        return min(cost, key=lambda c: (cost[c], c))
+    for (N, T, C), n_tiles in [((64, 1024, 1), 1), ((256, 4096, 1), 2), ((512, 8192, 1), 6),
+                               ((128, 65536, 1), 1), ((2048, 4096, 1), 72), ((2048, 32768, 1), 72)]:
+        d = _check_plan([(N, T, C)], 152, -1, 0)
+        kb = (T + 63) // 64
+        want = model(kb, min(152 // n_tiles, kb))
+        assert _parts_per_tile(d) == [want], (N, T, _parts_per_tile(d), want)
+    # Worked values: one part for 16 k-blocks, two for 64, three for 128, nine for 1024 (one
+    # tile), and the headline's two.
+    assert [model(16, 152), model(64, 76), model(128, 25), model(1024, 152), model(512, 2)] == [1, 2, 3, 9, 2]
+    # Jobs of different lengths with fewer tiles than CTAs are split, not dealt whole.
+    d = _check_plan([(1024, 32768, 1), (256, 4096, 1), (512, 2048, 1)], 152, -1, 0)
+    assert max(_parts_per_tile(d)) > 1
+
+
+def test_hybrid_tail_is_split_by_the_cost_model():
+    # 178 tiles on 152 CTAs: one whole wave, then the 26 tail tiles split over the CTAs
+    # (up to 5 per tile) by the same model, not cut into a stream-K share of every CTA.
+    d = _check_plan([(2176, 8192, 2)], 152, 2, 256)
+    kb = 128
+    parts = _parts_per_tile(d)
+    assert 1 in parts and max(parts) == 3            # 128/3 + 26 < 128/4 + 39 < 128/2 + 8
+    assert kb / 3 + 26 < kb / 4 + 39 < kb / 2 + 8 < kb
+
+
 def test_schedule_options_are_the_five_single_cta_schedules():
     # Schedules 0..4 exist; there is no clustered (multi-CTA) variant any more.
     for sched in range(5):
