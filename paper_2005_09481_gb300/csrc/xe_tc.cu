@@ -339,6 +339,10 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 else mainloop(std::false_type{});
                 if (ok) mma_commit(acc_full);
             }
+            // Every MMA of this CTA is issued: a launch that depends on this grid
+            // programmatically (the count launch after the visibilities') may set up its CTAs
+            // on SMs that are free; its producer still waits for this grid to complete.
+            asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
             if (!ok) {
                 // Wait (bounded) for every MMA already issued before TMEM is released.
                 mma_commit(drain);
