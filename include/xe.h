@@ -485,7 +485,7 @@ int xe_peak_probe(int kind, double *tflops, double *aux);
  *                    percent of a data job's (1 .. 100, default 75);
  *   "part_overhead"  modelled fix-up cost of one extra tile part in schedule 4, percent of
  *                    a whole tile (0 .. 100, default 2), never below the measured absolute
- *                    cost of a split (8 k-blocks for two parts, 13 per part beyond);
+ *                    cost of a split (8 k-blocks for two parts, 20 per part beyond);
  *   "implicit_plans" 1 = batches of the streaming server run whole tiles dealt round-robin
  *                    over the CTAs, decoded in the kernel from the job table, with no plan
  *                    built on the host (default); 0 = host-built plans as for other calls;

@@ -119,7 +119,7 @@ struct TuneCfg {
 };
 
 struct HostPlan {
-    bool pair_exchange = false;   // every split tile has 2 parts and every CTA 1 segment
+    bool pair_exchange = false;   // every split tile has 2, 4 or 8 parts and every CTA 1 segment
     std::vector<Tile> tiles;
     std::vector<Seg> segs;
     std::vector<int> seg_off;     // n_cta + 1 entries
@@ -233,7 +233,9 @@ struct LeastLoaded {
 // modelled fix-up cost when s > 1; the s in [1, 4] with the smallest modelled makespan wins.
 // Fix-up cost of splitting a tile, in k-blocks of mainloop time (split, hybrid and weighted schedules).
 constexpr double kPairFixKb = 8.0;     // two parts: the symmetric column-half exchange
-constexpr double kPartFixKb = 13.0;    // each further part: summed by the last arriving part
+constexpr double kPartFixKb = 20.0;    // each further part: summed by the last arriving part
+constexpr double kExch4FixKb = 30.0;   // four parts exchanging column slices
+constexpr double kExch8FixKb = 56.0;   // eight parts exchanging column slices
 
 static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &weight,
                               std::vector<std::vector<Seg>> &per) {
@@ -282,19 +284,24 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
 }
 
 // Parts per tile for tiles [t0, t1) dealt over G CTAs: up to the CTAs per tile (and the
-// k-blocks of the shortest tile), chosen to minimise max k-blocks per part + fix-up.
-static int split_parts(const std::vector<Tile> &tiles, int t0, int t1, int G) {
+// k-blocks of the shortest tile), chosen to minimise max k-blocks per part + fix-up.  With
+// `exchange` (each part alone on its CTA), 4 or 8 parts whose slices are at least 32 columns
+// wide exchange slices; other counts are summed by the last arriving part.
+static int split_parts(const std::vector<Tile> &tiles, int t0, int t1, int G, bool exchange) {
     const int n = t1 - t0;
-    int min_kb = 1 << 30, max_kb = 0;
+    int min_kb = 1 << 30, max_kb = 0, min_nj = kBN;
     for (int t = t0; t < t1; ++t) {
         min_kb = std::min(min_kb, tiles[size_t(t)].kblocks);
         max_kb = std::max(max_kb, tiles[size_t(t)].kblocks);
+        min_nj = std::min(min_nj, tiles[size_t(t)].nj);
     }
     const int s_max = std::min(n < G ? std::max(1, G / n) : 1, std::max(1, min_kb));
     int s = 1;
     double best = double(max_kb);
     for (int c = 2; c <= s_max; ++c) {
-        const double cost = double(max_kb) / c + (c == 2 ? kPairFixKb : kPartFixKb * (c - 1));
+        double fix = c == 2 ? kPairFixKb : kPartFixKb * (c - 1);
+        if (exchange && min_nj / c >= 32 && (c == 4 || c == 8)) fix = c == 4 ? kExch4FixKb : kExch8FixKb;
+        const double cost = double(max_kb) / c + fix;
         if (cost < best) {
             best = cost;
             s = c;
@@ -314,7 +321,7 @@ static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weig
         // swap column halves through the workspace (about kPairFixKb k-blocks of time), more
         // parts are summed by the last arriving part (about kPartFixKb each; measured on the
         // GB300, where 64 parts of a 64-k-block tile took ten times as long as two).
-        const int s = split_parts(p.tiles, 0, n, G);
+        const int s = split_parts(p.tiles, 0, n, G, true);
         int64_t item = 0;
         const int64_t n_items = int64_t(n) * s;
         const int64_t g = std::min<int64_t>(G, n_items);
@@ -334,7 +341,7 @@ static void schedule(HostPlan &p, int G, int sched, const std::vector<int> &weig
             per[size_t(t % G)].push_back(Seg{t, 0, p.tiles[size_t(t)].kblocks, -1});
         const int m = n - full;
         if (m > 0) {
-            const int s = split_parts(p.tiles, full, n, G);
+            const int s = split_parts(p.tiles, full, n, G, false);
             int64_t item = 0;
             for (int t = full; t < n; ++t)
                 for (int k = 0; k < s; ++k, ++item) {
@@ -458,10 +465,13 @@ static bool build_plan(const std::vector<JobShape> &jobs, int eb, const TuneCfg 
     for (const JobShape &j : jobs) weight.push_back(std::max(1, j.weight));
     schedule(p, G, cfg.sched, weight);
     if (!finalize_parts(p)) return false;
-    // The symmetric two-part exchange waits for the partner part, so it is used only when
-    // both parts are the only work of their CTAs (all of them resident at once).
+    // The exchange of column slices waits for the other parts, so it is used only when each
+    // part is the only work of its CTA (all of them resident at once) and every split tile
+    // has 2, 4 or 8 parts of at least 32 columns.
     bool pe = true;
-    for (const Tile &t : p.tiles) pe = pe && (t.n_parts == 0 || t.n_parts == 2);
+    for (const Tile &t : p.tiles)
+        pe = pe && (t.n_parts == 0 || ((t.n_parts == 2 || t.n_parts == 4 || t.n_parts == 8) &&
+                                       t.nj % t.n_parts == 0 && t.nj / t.n_parts >= 32));
     for (int b = 0; b < p.n_cta && pe; ++b) pe = p.seg_off[size_t(b) + 1] - p.seg_off[size_t(b)] == 1;
     p.pair_exchange = pe;
     return true;

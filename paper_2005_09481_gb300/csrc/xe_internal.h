@@ -130,8 +130,9 @@ struct PlanDev {
     int *counters;            // one arrival counter per tile, zero between launches
     int *status;              // device status word (0 = ok)
     int inject_stall;         // test hook: 1 = the producer issues no copies, so waits time out
-    int pair_exchange;        // 1: every split tile has 2 parts and every CTA one segment, so the
-                              // two parts swap column halves instead of a last-arriver sum
+    int pair_exchange;        // 1: every split tile has 2, 4 or 8 parts (each at least 32
+                              // columns wide) and every CTA one segment, all resident: the parts
+                              // exchange column slices instead of a last-arriver sum
     int implicit;             // 1: no tile or segment arrays: CTA b takes whole tiles b, b + grid,
                               // ... of the launch, decoded from the job table (implicit_tile)
 };

@@ -206,8 +206,9 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
     const int q0 = plan.implicit ? 0 : plan.seg_off[blockIdx.x];
     const int q1 = plan.implicit ? (plan.n_tiles - int(blockIdx.x) + int(gridDim.x) - 1) / int(gridDim.x)
                                  : plan.seg_off[blockIdx.x + 1];
-    // A CTA whose only segment is one part of a pair-exchanged tile finishes it with eight
-    // warps: the producer and MMA warps are idle by then, and two more warps wait for it.
+    // A CTA whose only segment is one part of an exchanged tile (plans whose split tiles
+    // all have 2, 4 or 8 parts, one segment per CTA, all CTAs resident) finishes it with
+    // eight warps: the producer and MMA warps are idle by then, and two more warps wait.
     const bool wide = !plan.implicit && plan.pair_exchange && q1 - q0 == 1 && plan.segs[q0].slot >= 0;
     constexpr uint32_t kFmt = 0;  // E4M3 for kind::f8f6f4, F16 for kind::f16
 
@@ -352,7 +353,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         }
     } else if (warp < 4 && !wide) {
         // ---------------- epilogue: TMEM -> int32 -> packed triangle ----------------
-        uint32_t acc_ph = 0, xph = 0;
+        uint32_t acc_ph = 0;
         const int r = warp * 32 + lane;
         const uint32_t lane_base = uint32_t(warp * 32) << 16;
         for (int q = q0; q < q1; ++q) {
@@ -383,98 +384,6 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                         im[k] = __float2int_rn(__uint_as_float(fim[k]));
                     }
                     store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + cc, re, im, jt.accumulate | jb.accumulate, epi_stage);
-                }
-            } else if (plan.pair_exchange) {
-                // Two-part tile, both parts running now on two CTAs: part p finalises column
-                // half p.  Publish my share of the partner's half, count myself in, wait
-                // (bounded) for the partner's share of mine, then add it to my own sums.
-                const int part = sg.k_lo == 0 ? 0 : 1;
-                const int half = tl.nj / 2;
-                const int mine0 = part * half, theirs0 = (1 - part) * half;
-                int32_t *ws = plan.ws + int64_t(sg.slot) * kWsSlotElems;
-                for (int cc = 0; cc < half; cc += 32) {
-                    uint32_t fre[32], fim[32];
-                    tmem_ld_32x32b_x32(tmem + lane_base + theirs0 + cc, fre);
-                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + theirs0 + cc, fim);
-                    tmem_ld_wait();
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        __stcg(ws + int64_t(cc + k) * kBM + r, __float2int_rn(__uint_as_float(fre[k])));
-                        __stcg(ws + int64_t(kBN + cc + k) * kBM + r, __float2int_rn(__uint_as_float(fim[k])));
-                    }
-                }
-                __threadfence();
-                epi_bar();
-                if (threadIdx.x == 0) {
-                    atomicAdd(&plan.counters[sg.tile], 1);
-                    volatile int *cnt = plan.counters + sg.tile;
-                    const long long t0 = clock64();
-                    bool ok = true;
-                    while (*cnt < 2) {
-                        if (*status != 0 || clock64() - t0 > kWaitBudgetCycles) { ok = false; break; }
-                    }
-                    if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
-                    *epi_flag = ok ? 1 : 0;
-                }
-                epi_bar();
-                if (*epi_flag == 1) {
-                    __threadfence();
-                    const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + (1 - part)]) * kWsSlotElems;
-                    // On the CTA's last segment the operand stages are idle (its MMAs have
-                    // completed, the producer has nothing left to fetch): one pair of bulk
-                    // copies brings the partner's whole share (re and im, half x 128 int32
-                    // each) into them, so the chunks below read shared memory instead of
-                    // waiting on L2 loads chunk by chunk.
-                    const bool staged = q == q1 - 1;
-                    const int32_t *sh = reinterpret_cast<const int32_t *>(smem);
-                    if (staged) {
-                        const uint32_t bytes = uint32_t(half) * kBM * 4u;
-                        if (threadIdx.x == 0) {
-                            // The share was written through the generic proxy on another SM.
-                            asm volatile("fence.proxy.async.global;" ::: "memory");
-                            mbar_arrive_expect_tx(xfer, 2u * bytes);
-                            bulk_g2s(smem, w, bytes, xfer);
-                            bulk_g2s(smem + bytes, w + int64_t(kBN) * kBM, bytes, xfer);
-                        }
-                        // Bounded wait that does not stop on another CTA's error: the copies
-                        // must land before this CTA may exit.
-                        const long long t0 = clock64();
-                        bool got = false;
-                        while (!(got = mbar_try_wait(xfer, xph)) && clock64() - t0 < kWaitBudgetCycles) {}
-                        if (!got) set_status(plan.status, kStatusTimeoutEpilogue);
-                        xph ^= 1u;
-                    }
-                    for (int cc = 0; cc < half; cc += 32) {
-                        uint32_t fre[32], fim[32];
-                        tmem_ld_32x32b_x32(tmem + lane_base + mine0 + cc, fre);
-                        tmem_ld_32x32b_x32(tmem + lane_base + 256 + mine0 + cc, fim);
-                        int re[32], im[32];
-                        if (staged) {
-#pragma unroll
-                            for (int k = 0; k < 32; ++k) {
-                                re[k] = sh[(cc + k) * kBM + r];
-                                im[k] = sh[(half + cc + k) * kBM + r];
-                            }
-                        } else {
-#pragma unroll
-                            for (int k = 0; k < 32; ++k) {
-                                re[k] = __ldcg(w + int64_t(cc + k) * kBM + r);
-                                im[k] = __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
-                            }
-                        }
-                        tmem_ld_wait();
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) {
-                            re[k] += __float2int_rn(__uint_as_float(fre[k]));
-                            im[k] += __float2int_rn(__uint_as_float(fim[k]));
-                        }
-                        store_block(jb, tl.chan, tl.i0 + warp * 32, tl.j0 + mine0 + cc, re, im,
-                                    jt.accumulate | jb.accumulate, epi_stage);
-                    }
-                    epi_bar();
-                    // Both parts have read each other's share: the second to finish resets the
-                    // counter for the next launch.
-                    if (threadIdx.x == 0 && atomicAdd(&plan.counters[sg.tile], 1) == 3) plan.counters[sg.tile] = 0;
                 }
             } else {
                 // Partial tile: publish this segment's share; the last one to arrive sums all.
@@ -556,15 +465,22 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
         wbar();
         if (*epi_flag == 1) {
             tc_fence_after();
-            const int part = sg.k_lo == 0 ? 0 : 1;
-            const int half = tl.nj / 2, cols = half / 2;
-            const int mine0 = part * half, theirs0 = (1 - part) * half;
-            const int c_lo = share * cols, c_hi = c_lo + cols;
+            // Part u of the tile's s parts (s = 2, 4 or 8; the host keeps nj / s >= 32)
+            // finalises the column slice [u nj / s, (u + 1) nj / s): it publishes every other
+            // column of its sums at that column of its workspace slot, waits (bounded) for all
+            // parts to have published, and adds the other parts' values of its slice.
+            const int s = tl.n_parts;
+            int part = 0;
+            for (int u = 0; u < s; ++u)
+                if (plan.tile_slots[tl.part_off + u] == sg.slot) part = u;
+            const int wd = tl.nj / s;
+            const int mine0 = part * wd;
             int32_t *ws = plan.ws + int64_t(sg.slot) * kWsSlotElems;
-            for (int cc = c_lo; cc < c_hi; cc += 32) {
+            for (int cc = 32 * share; cc < tl.nj; cc += 64) {
+                if (cc >= mine0 && cc < mine0 + wd) continue;
                 uint32_t fre[32], fim[32];
-                tmem_ld_32x32b_x32(tmem + lane_base + theirs0 + cc, fre);
-                tmem_ld_32x32b_x32(tmem + lane_base + 256 + theirs0 + cc, fim);
+                tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
+                tmem_ld_32x32b_x32(tmem + lane_base + 256 + cc, fim);
                 tmem_ld_wait();
 #pragma unroll
                 for (int k = 0; k < 32; ++k) {
@@ -579,7 +495,7 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                 volatile int *cnt = plan.counters + sg.tile;
                 const long long t0 = clock64();
                 bool ok = true;
-                while (*cnt < 2) {
+                while (*cnt < s) {
                     if (*status != 0 || clock64() - t0 > kWaitBudgetCycles) { ok = false; break; }
                 }
                 if (!ok) set_status(plan.status, kStatusTimeoutEpilogue);
@@ -588,33 +504,59 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
             wbar();
             if (*epi_flag == 1) {
                 __threadfence();
-                const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + (1 - part)]) * kWsSlotElems;
-                // The partner's share (re and im, half x 128 int32 each) goes into the idle
-                // operand stages in one pair of bulk copies; warps 4..7 take their transpose
-                // buffers from the stages after it.
-                const uint32_t bytes = uint32_t(half) * kBM * 4u;
-                if (threadIdx.x == 0) {
-                    asm volatile("fence.proxy.async.global;" ::: "memory");
-                    mbar_arrive_expect_tx(xfer, 2u * bytes);
-                    bulk_g2s(smem, w, bytes, xfer);
-                    bulk_g2s(smem + bytes, w + int64_t(kBN) * kBM, bytes, xfer);
+                // My slice in shares of 32-column chunks: half each for slices of 64 columns
+                // or more, else all of it to share 0.
+                const int per = wd >= 64 ? wd / 2 : (share == 0 ? wd : 0);
+                const int c_lo = mine0 + (wd >= 64 ? share * per : 0), c_hi = c_lo + per;
+                // With two parts, the partner's values of my slice (re and im, wd x 128 int32
+                // each) go into the idle operand stages in one pair of bulk copies; warps 4..7
+                // take their transpose buffers from the stages after it.  With more parts the
+                // chunks read the partners' slots from L2.
+                const uint32_t bytes = uint32_t(wd) * kBM * 4u;
+                const int32_t *w1 = plan.ws + int64_t(plan.tile_slots[tl.part_off + (1 - part)]) * kWsSlotElems;
+                if (s == 2) {
+                    if (threadIdx.x == 0) {
+                        asm volatile("fence.proxy.async.global;" ::: "memory");
+                        mbar_arrive_expect_tx(xfer, 2u * bytes);
+                        bulk_g2s(smem, w1 + int64_t(mine0) * kBM, bytes, xfer);
+                        bulk_g2s(smem + bytes, w1 + int64_t(kBN + mine0) * kBM, bytes, xfer);
+                    }
+                    const long long t0 = clock64();
+                    bool got = false;
+                    while (!(got = mbar_try_wait(xfer, 0)) && clock64() - t0 < kWaitBudgetCycles) {}
+                    if (!got) set_status(plan.status, kStatusTimeoutEpilogue);
                 }
-                const long long t0 = clock64();
-                bool got = false;
-                while (!(got = mbar_try_wait(xfer, 0)) && clock64() - t0 < kWaitBudgetCycles) {}
-                if (!got) set_status(plan.status, kStatusTimeoutEpilogue);
                 const int32_t *sh = reinterpret_cast<const int32_t *>(smem);
+                // (After the largest two-part copy, re and im of 128 columns: 128 KB, so the
+                // buffers end at 162 KB, inside the 192 KB of operand stages.)
+                constexpr size_t kXferBytes = 2 * size_t(kBN / 2) * kBM * 4;
+                static_assert(kXferBytes + 4 * 32 * 33 * sizeof(int2) <= size_t(kStages) * kStageBytes,
+                              "transpose buffers of warps 4..7 must fit in the operand stages");
                 int2 *buf = share == 0 ? epi_stage
-                                       : reinterpret_cast<int2 *>(smem + 2 * bytes) + (warp - 4) * 32 * 33;
+                                       : reinterpret_cast<int2 *>(smem + kXferBytes) + (warp - 4) * 32 * 33;
                 for (int cc = c_lo; cc < c_hi; cc += 32) {
                     uint32_t fre[32], fim[32];
-                    tmem_ld_32x32b_x32(tmem + lane_base + mine0 + cc, fre);
-                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + mine0 + cc, fim);
+                    tmem_ld_32x32b_x32(tmem + lane_base + cc, fre);
+                    tmem_ld_32x32b_x32(tmem + lane_base + 256 + cc, fim);
                     int re[32], im[32];
+                    if (s == 2) {
 #pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        re[k] = sh[(cc + k) * kBM + r];
-                        im[k] = sh[(half + cc + k) * kBM + r];
+                        for (int k = 0; k < 32; ++k) {
+                            re[k] = sh[(cc - mine0 + k) * kBM + r];
+                            im[k] = sh[(wd + cc - mine0 + k) * kBM + r];
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 32; ++k) re[k] = im[k] = 0;
+                        for (int u = 0; u < s; ++u) {
+                            if (u == part) continue;
+                            const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + u]) * kWsSlotElems;
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) {
+                                re[k] += __ldcg(w + int64_t(cc + k) * kBM + r);
+                                im[k] += __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
+                            }
+                        }
                     }
                     tmem_ld_wait();
 #pragma unroll
@@ -622,13 +564,13 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                         re[k] += __float2int_rn(__uint_as_float(fre[k]));
                         im[k] += __float2int_rn(__uint_as_float(fim[k]));
                     }
-                    store_block(jb, tl.chan, tl.i0 + quarter * 32, tl.j0 + mine0 + cc, re, im,
+                    store_block(jb, tl.chan, tl.i0 + quarter * 32, tl.j0 + cc, re, im,
                                 jt.accumulate | jb.accumulate, buf);
                 }
                 wbar();
-                // Both parts have read each other's share: the second to finish resets the
+                // Every part has read the others' values: the last to finish resets the
                 // counter for the next launch.
-                if (threadIdx.x == 0 && atomicAdd(&plan.counters[sg.tile], 1) == 3) plan.counters[sg.tile] = 0;
+                if (threadIdx.x == 0 && atomicAdd(&plan.counters[sg.tile], 1) == 2 * s - 1) plan.counters[sg.tile] = 0;
             }
         }
     }

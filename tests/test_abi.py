@@ -314,24 +314,36 @@ def _parts_per_tile(d):
 
 
 def test_split_parts_follow_the_fix_up_cost_model():
-    # Parts per tile minimise (longest tile's k-blocks / parts) + fix-up, with 8 k-blocks for
-    # two parts (the column-half exchange) and 13 per part beyond the first (the last
-    # arriver's sum), up to the CTAs per tile; the default schedule for fewer tiles than
-    # CTAs is the split, also for jobs of different lengths.
-    def model(kb, s_max):
+    # Parts per tile minimise (longest tile's k-blocks / parts) + fix-up: 8 k-blocks for two
+    # parts and 30 or 56 for four or eight parts that exchange column slices (at least 32
+    # columns each, every part alone on its CTA), else 20 per part beyond the first (the
+    # last arriver's sum); up to the CTAs per tile.  The default schedule for fewer tiles
+    # than CTAs is the split, also for jobs of different lengths.
+    def model(kb, s_max, min_nj):
         cost = {1: kb}
         for c in range(2, s_max + 1):
-            cost[c] = kb / c + (8 if c == 2 else 13 * (c - 1))
+            fix = 8 if c == 2 else 20 * (c - 1)
+            if c in (4, 8) and min_nj // c >= 32:
+                fix = 30 if c == 4 else 56
+            cost[c] = kb / c + fix
         return min(cost, key=lambda c: (cost[c], c))
-    for (N, T, C), n_tiles in [((64, 1024, 1), 1), ((256, 4096, 1), 2), ((512, 8192, 1), 6),
-                               ((128, 65536, 1), 1), ((2048, 4096, 1), 72), ((2048, 32768, 1), 72)]:
+    for (N, T, C) in [(64, 1024, 1), (256, 4096, 1), (512, 8192, 1), (128, 65536, 1), (2048, 4096, 1),
+                      (2048, 32768, 1), (256, 32768, 1), (1024, 32768, 1)]:
         d = _check_plan([(N, T, C)], 152, -1, 0)
+        n_tiles, min_nj = len(d["tiles"]), int(d["tiles"][:, 4].min())
         kb = (T + 63) // 64
-        want = model(kb, min(152 // n_tiles, kb))
+        want = model(kb, min(152 // n_tiles, kb), min_nj)
         assert _parts_per_tile(d) == [want], (N, T, _parts_per_tile(d), want)
-    # Worked values: one part for 16 k-blocks, two for 64, three for 128, nine for 1024 (one
-    # tile), and the headline's two.
-    assert [model(16, 152), model(64, 76), model(128, 25), model(1024, 152), model(512, 2)] == [1, 2, 3, 9, 2]
+    # Worked values: a 16-k-block tile whole, a 128-k-block tile in four exchanging parts, a
+    # 1024-k-block tile in eight, 512-k-block tiles in four when 7 CTAs are free per tile,
+    # the headline's two.
+    assert [model(16, 152, 256), model(128, 25, 128), model(1024, 152, 256), model(512, 7, 256),
+            model(512, 2, 256)] == [1, 4, 8, 4, 2]
+    # Four or eight parts exchange slices (the plan's exchange flag is visible in the eight
+    # parts of a single 128-input tile and the two of the headline).
+    for sh in [(128, 65536, 1), (2048, 32768, 1)]:
+        d = xe.plan_dump([sh], 152)
+        assert d["n_partial"] == len(d["segs"])
     # Jobs of different lengths with fewer tiles than CTAs are split, not dealt whole.
     d = _check_plan([(1024, 32768, 1), (256, 4096, 1), (512, 2048, 1)], 152, -1, 0)
     assert max(_parts_per_tile(d)) > 1
@@ -339,12 +351,13 @@ def test_split_parts_follow_the_fix_up_cost_model():
 
 def test_hybrid_tail_is_split_by_the_cost_model():
     # 178 tiles on 152 CTAs: one whole wave, then the 26 tail tiles split over the CTAs
-    # (up to 5 per tile) by the same model, not cut into a stream-K share of every CTA.
+    # (up to 5 per tile; two segments on a CTA, so no exchange) by the same model, not cut
+    # into a stream-K share of every CTA.
     d = _check_plan([(2176, 8192, 2)], 152, 2, 256)
     kb = 128
     parts = _parts_per_tile(d)
-    assert 1 in parts and max(parts) == 3            # 128/3 + 26 < 128/4 + 39 < 128/2 + 8
-    assert kb / 3 + 26 < kb / 4 + 39 < kb / 2 + 8 < kb
+    assert 1 in parts and max(parts) == 2            # 128/2 + 8 < 128/3 + 40 < 128
+    assert kb / 2 + 8 < kb / 3 + 40 < kb
 
 
 def test_schedule_options_are_the_five_single_cta_schedules():

@@ -80,6 +80,21 @@ def test_maximum_input_count(xe):
     torch.cuda.empty_cache()
 
 
+@pytest.mark.parametrize("N,T,C,parts", [(128, 65536, 1, 8), (512, 8192, 1, 4), (300, 8192, 2, 4),
+                                         (1024, 32768, 1, 4), (2048, 4096, 1, 2)])
+def test_exchanged_parts_are_exact(xe, N, T, C, parts):
+    # Tiles split into 4 or 8 parts that exchange column slices (each part finalises its
+    # slice from the others' published sums), including 128-wide tiles cut into 32-column
+    # slices and a ragged input count; the default plan is checked to be that split.
+    d = xe.plan_dump([(N, T, C)], 152)
+    per_tile = {}
+    for (cta, t, lo, hi, slot) in d["segs"]:
+        per_tile[int(t)] = per_tile.get(int(t), 0) + 1
+    assert set(per_tile.values()) == {parts}
+    p = synth.uniform(N, T, C, seed=N + T + parts)
+    assert_exact(run(xe, p, N, T, C, "tc"), oracle.correlate_dense(p, N, T, C), f"{N}x{T}x{C} in {parts} parts")
+
+
 SHAPES = [(1, 1, 1), (2, 1, 1), (3, 5, 2), (17, 63, 1), (64, 64, 1), (100, 65, 3),
           (129, 127, 1), (255, 200, 1), (256, 1000, 1), (257, 129, 2), (300, 77, 1),
           (513, 300, 1), (640, 4096, 1)]
