@@ -285,8 +285,8 @@ static void schedule_weighted(const HostPlan &p, int G, const std::vector<int> &
 
 // Parts per tile for tiles [t0, t1) dealt over G CTAs: up to the CTAs per tile (and the
 // k-blocks of the shortest tile), chosen to minimise max k-blocks per part + fix-up.  With
-// `exchange` (each part alone on its CTA), 4 or 8 parts whose slices are at least 32 columns
-// wide exchange slices; other counts are summed by the last arriving part.
+// `exchange` (each part alone on its CTA), 2, 4 or 8 parts whose slices are at least 32
+// columns wide exchange slices; otherwise the last arriving part sums them.
 static int split_parts(const std::vector<Tile> &tiles, int t0, int t1, int G, bool exchange) {
     const int n = t1 - t0;
     int min_kb = 1 << 30, max_kb = 0, min_nj = kBN;
@@ -299,8 +299,9 @@ static int split_parts(const std::vector<Tile> &tiles, int t0, int t1, int G, bo
     int s = 1;
     double best = double(max_kb);
     for (int c = 2; c <= s_max; ++c) {
-        double fix = c == 2 ? kPairFixKb : kPartFixKb * (c - 1);
-        if (exchange && min_nj / c >= 32 && (c == 4 || c == 8)) fix = c == 4 ? kExch4FixKb : kExch8FixKb;
+        double fix = kPartFixKb * (c - 1);
+        if (exchange && min_nj / c >= 32 && (c == 2 || c == 4 || c == 8))
+            fix = c == 2 ? kPairFixKb : c == 4 ? kExch4FixKb : kExch8FixKb;
         const double cost = double(max_kb) / c + fix;
         if (cost < best) {
             best = cost;

@@ -356,8 +356,8 @@ def test_hybrid_tail_is_split_by_the_cost_model():
     d = _check_plan([(2176, 8192, 2)], 152, 2, 256)
     kb = 128
     parts = _parts_per_tile(d)
-    assert 1 in parts and max(parts) == 2            # 128/2 + 8 < 128/3 + 40 < 128
-    assert kb / 2 + 8 < kb / 3 + 40 < kb
+    assert 1 in parts and max(parts) == 3            # 128/3 + 40 < 128/2 + 20 < 128
+    assert kb / 3 + 40 < kb / 2 + 20 < kb
 
 
 def test_schedule_options_are_the_five_single_cta_schedules():
