@@ -30,7 +30,6 @@
 //                 launch may overlap the staging kernel (programmatic dependent launch):
 //                 only the producer waits for it before reading planes.
 #include <cstdint>
-#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "xe_internal.h"
@@ -546,15 +545,34 @@ __device__ __forceinline__ void tc_body(const JobTable &jt, const PlanDev &plan)
                             im[k] = sh[(wd + cc - mine0 + k) * kBM + r];
                         }
                     } else {
+                        // The other parts' values of these 32 columns, from L2: three parts
+                        // at a time, four columns at a time, all of those loads independent
+                        // and in flight together (a loop over the parts that waited for each
+                        // part's loads in turn took 16-33 us per slice).  The empty asm keeps
+                        // the compiler from hoisting later loads above it, which bounds the
+                        // registers held.
 #pragma unroll
                         for (int k = 0; k < 32; ++k) re[k] = im[k] = 0;
-                        for (int u = 0; u < s; ++u) {
-                            if (u == part) continue;
-                            const int32_t *w = plan.ws + int64_t(plan.tile_slots[tl.part_off + u]) * kWsSlotElems;
+                        for (int g0 = 0; g0 < s - 1; g0 += 3) {
+                            int64_t base[3];
 #pragma unroll
-                            for (int k = 0; k < 32; ++k) {
-                                re[k] += __ldcg(w + int64_t(cc + k) * kBM + r);
-                                im[k] += __ldcg(w + int64_t(kBN + cc + k) * kBM + r);
+                            for (int v = 0; v < 3; ++v) {
+                                const int pv = g0 + v, u = pv < part ? pv : pv + 1;
+                                base[v] = pv < s - 1 ? int64_t(plan.tile_slots[tl.part_off + u]) * kWsSlotElems +
+                                                           int64_t(cc) * kBM + r
+                                                     : -1;
+                            }
+#pragma unroll
+                            for (int k0 = 0; k0 < 32; k0 += 4) {
+#pragma unroll
+                                for (int k = k0; k < k0 + 4; ++k)
+#pragma unroll
+                                    for (int v = 0; v < 3; ++v)
+                                        if (base[v] >= 0) {
+                                            re[k] += __ldcg(plan.ws + base[v] + k * kBM);
+                                            im[k] += __ldcg(plan.ws + base[v] + (kBN + k) * kBM);
+                                        }
+                                asm volatile("" ::: "memory");
                             }
                         }
                     }
