@@ -435,7 +435,20 @@ static bool finalize_parts(HostPlan &p) {
 // running CTAs read the same k-blocks (shared in L2); many equal tiles: whole tiles in full
 // waves, the last wave stream-K; uneven tiles: whole tiles, longest first.
 static TuneCfg heuristic(const std::vector<JobShape> &jobs, int eb, int n_sm) {
-    TuneCfg c{g_opt.n_cta > 0 ? g_opt.n_cta : n_sm, g_opt.tile_n > 0 ? g_opt.tile_n : 256, g_opt.sched};
+    // 128-wide tiles when every job fits one 128-input row block (one 128 x 128 tile instead
+    // of a 128 x 256 one that is half padding) with at most 256 k-blocks, or has at most 256
+    // inputs and at most 32 k-blocks (where the launch, fill and epilogue outweigh the MMAs):
+    // measured on the GB300, N=64 T=1024 25 us against 33, N=128 T=8192 43 against 50,
+    // N=256 T=1024 27 against 35, N=200 T=2048 35 against 37.  Longer integrations keep
+    // 256-wide tiles: their k-blocks cost less per output element and they split into eight
+    // exchanging parts (a 128-wide tile into at most four).
+    bool small = true;
+    for (const JobShape &j : jobs) {
+        const int64_t kb = kblocks_of(j.T, eb);
+        small = small && ((j.N <= kBM && kb <= 256) || (j.N <= kBN && kb <= 32));
+    }
+    TuneCfg c{g_opt.n_cta > 0 ? g_opt.n_cta : n_sm, g_opt.tile_n > 0 ? g_opt.tile_n : small ? kBN / 2 : kBN,
+              g_opt.sched};
     if (c.sched < 0) {
         // Decided from the job shapes alone (every job has at least one tile, all of them
         // with the job's k-block count), without enumerating the tiles.

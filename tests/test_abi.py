@@ -207,9 +207,11 @@ def test_plan_covers_triangle_once(N):
     tiles, cover = _tiles_py(N)
     iu = np.triu_indices(N)
     assert (cover[iu] == 1).all() and cover.sum() == N * (N + 1) // 2
-    n_tiles, n_iters, _ = xe.plan_stats([(N, 1000, 1)], 152)
+    # 4096 samples (64 k-blocks): long enough that the default keeps 256-wide tiles (short
+    # calls of up to 256 inputs take 128-wide ones; a one-block N <= 128 is one tile either way).
+    n_tiles, n_iters, _ = xe.plan_stats([(N, 4096, 1)], 152)
     assert n_tiles == tiles
-    assert n_iters == tiles * ((1000 + 63) // 64)
+    assert n_iters == tiles * 64
 
 
 def test_plan_stats_batch_and_split():
@@ -347,6 +349,16 @@ def test_split_parts_follow_the_fix_up_cost_model():
     # Jobs of different lengths with fewer tiles than CTAs are split, not dealt whole.
     d = _check_plan([(1024, 32768, 1), (256, 4096, 1), (512, 2048, 1)], 152, -1, 0)
     assert max(_parts_per_tile(d)) > 1
+
+
+def test_default_tile_width_follows_the_problem_size():
+    # 128-wide tiles for one-block problems (N <= 128) of up to 256 k-blocks and for short
+    # calls of up to 256 inputs (at most 32 k-blocks); 256-wide tiles otherwise.
+    for (N, T), nj in [((64, 1024), 128), ((128, 16384), 128), ((128, 65536), 256), ((256, 1024), 128),
+                       ((200, 2048), 128),
+                       ((256, 4096), 256), ((257, 1024), 256), ((2048, 1024), 256), ((2048, 32768), 256)]:
+        d = _check_plan([(N, T, 1)], 152, -1, 0)
+        assert set(d["tiles"][:, 4].tolist()) <= {nj, 128} and int(d["tiles"][:, 4].max()) == nj, (N, T)
 
 
 def test_hybrid_tail_is_split_by_the_cost_model():
