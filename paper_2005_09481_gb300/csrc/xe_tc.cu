@@ -88,10 +88,15 @@ __device__ __forceinline__ void fetch_segment(const JobTable &jt, const PlanDev 
     }
 }
 
+// *p += v in L2 (a reduction: nothing is returned, so the thread does not wait).
+__device__ __forceinline__ void red_add_s32(int32_t *p, int32_t v) {
+    asm volatile("red.relaxed.gpu.global.add.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
 // Store (or add) a 32 x 32 block of final visibilities held by one warp (lane = row
 // i0 + lane, register k = column jbase + k).  The block is transposed through the warp's
 // shared buffer so that each global access covers 32 consecutive baselines of one row
-// (256 contiguous bytes); in accumulate mode all 32 row loads are issued before any add.
+// (256 contiguous bytes); in accumulate mode the block is added by reductions in L2.
 // A count job (kModeCount) writes only the Re part, n_ij, into its int32 [C][B] counts (its
 // vis pointer and vis_chan_elems = B), 128 contiguous bytes per row.
 __device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, int jbase,
@@ -106,44 +111,28 @@ __device__ __forceinline__ void store_block(const JobDev &jb, int chan, int i0, 
     const int j = jbase + lane;
     if (jb.mode & kModeCount) {
         // Counts: element k of the row-major upper triangle, Re part only.
-        int old[32];
-        if (acc) {
-#pragma unroll
-            for (int r = 0; r < 32; ++r) {
-                const int i = i0 + r;
-                old[r] = 0;
-                if (i < jb.N && j >= i && j < jb.N) {
-                    const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
-                    old[r] = __ldcg(vis + k);
-                }
-            }
-        }
 #pragma unroll 8
         for (int r = 0; r < 32; ++r) {
             const int i = i0 + r;
             if (i < jb.N && j >= i && j < jb.N) {
                 const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
-                vis[k] = (acc ? old[r] : 0) + stage[r * 33 + lane].x;
+                if (acc) red_add_s32(vis + k, stage[r * 33 + lane].x);
+                else vis[k] = stage[r * 33 + lane].x;
             }
         }
     } else if (acc) {
-        int2 old[32];
-#pragma unroll
-        for (int r = 0; r < 32; ++r) {
-            const int i = i0 + r;
-            old[r] = make_int2(0, 0);
-            if (i < jb.N && j >= i && j < jb.N) {
-                const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
-                old[r] = __ldcg(reinterpret_cast<const int2 *>(vis + 2 * k));
-            }
-        }
-#pragma unroll
+        // Adding into the sums: reductions performed in L2, so no warp waits for the old
+        // values (a load, add and store per element held each tile's epilogue, and with it
+        // the next tile's MMAs, on the loads' latency).  Integer addition is exact whatever
+        // the order.
+#pragma unroll 8
         for (int r = 0; r < 32; ++r) {
             const int i = i0 + r;
             if (i < jb.N && j >= i && j < jb.N) {
                 const int64_t k = int64_t(i) * N - (int64_t(i) * (i - 1)) / 2 + (j - i);
                 const int2 v = stage[r * 33 + lane];
-                *reinterpret_cast<int2 *>(vis + 2 * k) = make_int2(old[r].x + v.x, old[r].y + v.y);
+                red_add_s32(vis + 2 * k, v.x);
+                red_add_s32(vis + 2 * k + 1, v.y);
             }
         }
     } else {
