@@ -1,0 +1,109 @@
+"""A seeded sweep over shapes and forced planner options, full outputs against the CPU
+oracle (tolerance 0).  Each case draws input counts and lengths at and around the tile and
+k-block edges (128- and 256-input blocks, 64-sample blocks), a channel or job count, and a
+schedule, tile width and CTA count, so that the combinations of whole tiles, k-splits,
+exchanged parts, last-arriver sums, several segments per CTA and ragged edges are all met
+together; some cases also take f16 operands or short exact windows (integrations split
+into windows that add into the output).  Batches also add into their outputs
+(correlate_accumulate).  Every call goes through the C ABI."""
+import random
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2005_09481_gb300 import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+N_EDGES = [1, 2, 31, 63, 64, 65, 127, 128, 129, 191, 255, 256, 257, 300, 383, 384, 385, 511, 512, 513, 640,
+           767, 768, 769, 1023, 1025]
+T_EDGES = [1, 7, 63, 64, 65, 127, 128, 129, 1000, 4095, 4096, 4097, 8191, 8192, 8193, 12000]
+SCHEDS = [-1, 0, 1, 2, 3, 4]
+TILES = [0, 128, 256]
+CTAS = [0, 5, 37, 152, 300]
+OPERAND_BYTES = [1, 1, 1, 2]
+CHUNKS = [131072, 131072, 131072, 4096, 1024]
+
+
+def _cases(seed, n, batch):
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        n_jobs = rng.randint(2, 4) if batch else 1
+        jobs = []
+        for _ in range(n_jobs):
+            N, T = rng.choice(N_EDGES), rng.choice(T_EDGES)
+            # keep the oracle's dense products small: at most 2.5e9 N^2 T per job
+            while N * N * T > 2.5e9:
+                T = max(1, T // 2)
+            jobs.append((N, T, rng.randint(1, 3 if not batch else 2)))
+        opts = (rng.choice(SCHEDS), rng.choice(TILES), rng.choice(CTAS), rng.choice(OPERAND_BYTES),
+                rng.choice(CHUNKS))
+        out.append(pytest.param(jobs, opts, k, id=f"{'b' if batch else 's'}{k}-" +
+                                "+".join(f"{N}x{T}x{C}" for N, T, C in jobs) +
+                                f"-sched{opts[0]}-tile{opts[1]}-cta{opts[2]}-eb{opts[3]}-win{opts[4]}"))
+    return out
+
+
+@pytest.fixture(scope="module")
+def xe():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2005_09481_gb300 import xe as _xe
+    _xe.load()
+    return _xe
+
+
+@pytest.fixture(autouse=True)
+def _default_options(xe):
+    yield
+    xe.set_option("sched", -1)
+    xe.set_option("tile_n", 0)
+    xe.set_option("n_cta", 0)
+    xe.set_option("operand_bytes", 1)
+    xe.set_option("exact_chunk_t", 131072)
+
+
+def _set(xe, opts):
+    sched, tile, cta, eb, chunk = opts
+    xe.set_option("sched", sched)
+    xe.set_option("tile_n", tile)
+    xe.set_option("n_cta", cta)
+    xe.set_option("operand_bytes", eb)
+    xe.set_option("exact_chunk_t", chunk)
+
+
+def _assert_exact(got, want, what):
+    if not np.array_equal(got, want):
+        bad = np.argwhere(got != want)
+        k = tuple(bad[0])
+        raise AssertionError(f"{what}: {len(bad)} mismatches, first at {k}: got {got[k]} want {want[k]}")
+
+
+@pytest.mark.parametrize("jobs,opts,k", _cases(20050948, 64, batch=False))
+def test_single_calls(xe, jobs, opts, k):
+    (N, T, C), = jobs
+    p = synth.uniform(N, T, C, seed=1000 + k)
+    _set(xe, opts)
+    got = xe.correlate(torch.from_numpy(p).cuda(), N, T, C)
+    torch.cuda.synchronize()
+    xe.device_status()
+    _assert_exact(got.cpu().numpy(), oracle.correlate_dense(p, N, T, C), f"{N}x{T}x{C} {opts}")
+
+
+@pytest.mark.parametrize("jobs,opts,k", _cases(94810502, 24, batch=True))
+def test_batches_and_accumulation(xe, jobs, opts, k):
+    ps = [synth.uniform(N, T, C, seed=2000 + 10 * k + j) for j, (N, T, C) in enumerate(jobs)]
+    ins = [torch.from_numpy(p).cuda() for p in ps]
+    outs = [xe.empty_vis(N, C) for (N, T, C) in jobs]
+    _set(xe, opts)
+    xe.correlate_batch([(x, o, N, T, C) for x, o, (N, T, C) in zip(ins, outs, jobs)], use_graph=bool(k & 1))
+    # then add the same visibilities once more: every output must read 2 V
+    xe.correlate_accumulate([(x, o, N, T, C) for x, o, (N, T, C) in zip(ins, outs, jobs)])
+    torch.cuda.synchronize()
+    xe.device_status()
+    for j, ((N, T, C), p, o) in enumerate(zip(jobs, ps, outs)):
+        want = oracle.correlate_dense(p, N, T, C).astype(np.int64) * 2
+        _assert_exact(o.cpu().numpy().astype(np.int64), want, f"job {j} {N}x{T}x{C} {opts}")
