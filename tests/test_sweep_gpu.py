@@ -5,7 +5,8 @@ schedule, tile width and CTA count, so that the combinations of whole tiles, k-s
 exchanged parts, last-arriver sums, several segments per CTA and ragged edges are all met
 together; some cases also take f16 operands or short exact windows (integrations split
 into windows that add into the output).  Batches also add into their outputs
-(correlate_accumulate).  Every call goes through the C ABI."""
+(correlate_accumulate).  Flag-masked calls (with and without counts, both encodings) and
+phased-array beams get their own sweeps.  Every call goes through the C ABI."""
 import random
 
 import numpy as np
@@ -64,6 +65,7 @@ def _default_options(xe):
     xe.set_option("n_cta", 0)
     xe.set_option("operand_bytes", 1)
     xe.set_option("exact_chunk_t", 131072)
+    xe.set_option("count_launch", 1)
 
 
 def _set(xe, opts):
@@ -107,3 +109,82 @@ def test_batches_and_accumulation(xe, jobs, opts, k):
     for j, ((N, T, C), p, o) in enumerate(zip(jobs, ps, outs)):
         want = oracle.correlate_dense(p, N, T, C).astype(np.int64) * 2
         _assert_exact(o.cpu().numpy().astype(np.int64), want, f"job {j} {N}x{T}x{C} {opts}")
+
+
+def _masked_cases(seed, n):
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        N, T = rng.choice(N_EDGES), rng.choice(T_EDGES)
+        while N * N * T > 1.5e9:
+            T = max(1, T // 2)
+        C = rng.randint(1, 2)
+        flags = rng.choice(["none", "sparse", "bursts", "half"])
+        enc = rng.choice(["twos", "offset"])
+        counts = rng.random() < 0.8
+        opts = (rng.choice(SCHEDS), rng.choice(CTAS), rng.choice([0, 1]), rng.choice([131072, 131072, 4096]))
+        out.append(pytest.param(N, T, C, flags, enc, counts, opts, k,
+                                id=f"m{k}-{N}x{T}x{C}-{flags}-{enc}-{'counts' if counts else 'vis'}-"
+                                   f"sched{opts[0]}-cta{opts[1]}-cl{opts[2]}-win{opts[3]}"))
+    return out
+
+
+@pytest.mark.parametrize("N,T,C,flags,enc,with_counts,opts,k", _masked_cases(27182818, 20))
+def test_masked_calls(xe, N, T, C, flags, enc, with_counts, opts, k):
+    # Every byte value (both encodings' extremes), four flag patterns, with and without
+    # counts, under forced schedules, CTA counts, count-launch modes and exact windows.
+    rs = np.random.default_rng(3000 + k)
+    p = rs.integers(0, 256, size=(C, T, N), dtype=np.uint8)
+    if flags == "none":
+        f = None
+    elif flags == "half":
+        f = synth.flags(N, T, C, p_bad=0.5, seed=3000 + k)
+    else:
+        f = synth.flags(N, T, C, p_bad=0.02, seed=3000 + k, burst=256 if flags == "bursts" else 0)
+    sched, cta, count_launch, chunk = opts
+    xe.set_option("sched", sched)
+    xe.set_option("n_cta", cta)
+    xe.set_option("count_launch", count_launch)
+    xe.set_option("exact_chunk_t", chunk)
+    try:
+        vis, cnt = xe.correlate_masked(torch.from_numpy(p).cuda(), None if f is None else torch.from_numpy(f).cuda(),
+                                       N, T, C, encoding=enc, with_counts=with_counts)
+        torch.cuda.synchronize()
+        xe.device_status()
+    finally:
+        xe.set_option("count_launch", 1)
+    e = 1 if enc == "offset" else 0
+    _assert_exact(vis.cpu().numpy(), oracle.correlate_masked_dense(p, f, N, T, C, encoding=e), f"vis {N}x{T}x{C}")
+    if with_counts:
+        if f is None:
+            want = np.full((C, oracle.n_baselines(N)), T, np.int64)
+        else:
+            want = oracle.flag_counts_dense(f, N, T, C)
+        _assert_exact(cnt.cpu().numpy().astype(np.int64), want, f"counts {N}x{T}x{C}")
+
+
+def _beam_cases(seed, n):
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        N, T = rng.choice(N_EDGES), rng.choice(T_EDGES)
+        B = rng.choice([1, 3, 10, 16, 17, 33, 64, 65, 100, 128])
+        while N * T * B > 4e8:
+            T = max(1, T // 2)
+        C = rng.randint(1, 2)
+        out.append(pytest.param(N, T, C, B, k, id=f"y{k}-{N}x{T}x{C}-B{B}"))
+    return out
+
+
+@pytest.mark.parametrize("N,T,C,B,k", _beam_cases(16180339, 16))
+def test_beam_calls(xe, N, T, C, B, k):
+    # Every byte value and every int8 weight, -128 included; ragged and unaligned input
+    # counts (byte-load path), ragged sample tiles, beams in one or several launches.
+    rs = np.random.default_rng(4000 + k)
+    p = rs.integers(0, 256, size=(C, T, N), dtype=np.uint8)
+    w = rs.integers(-128, 128, size=(B, N, 2), dtype=np.int8)
+    got = xe.beamform(torch.from_numpy(p).cuda(), torch.from_numpy(w).cuda(), N, T, C)
+    torch.cuda.synchronize()
+    xe.device_status()
+    _assert_exact(got.cpu().numpy().astype(np.int64), oracle.beamform_dense(p, w, N, T, C, B),
+                  f"beams {N}x{T}x{C} B={B}")
