@@ -5,8 +5,8 @@ schedule, tile width and CTA count, so that the combinations of whole tiles, k-s
 exchanged parts, last-arriver sums, several segments per CTA and ragged edges are all met
 together; some cases also take f16 operands or short exact windows (integrations split
 into windows that add into the output).  Batches also add into their outputs
-(correlate_accumulate).  Flag-masked calls (with and without counts, both encodings) and
-phased-array beams get their own sweeps.  Every call goes through the C ABI."""
+(correlate_accumulate).  Flag-masked calls (with and without counts, both encodings),
+phased-array beams and streaming runs (ragged frames, lost frames) get their own sweeps.  Every call goes through the C ABI."""
 import random
 
 import numpy as np
@@ -188,3 +188,69 @@ def test_beam_calls(xe, N, T, C, B, k):
     xe.device_status()
     _assert_exact(got.cpu().numpy().astype(np.int64), oracle.beamform_dense(p, w, N, T, C, B),
                   f"beams {N}x{T}x{C} B={B}")
+
+
+def _stream_cases(seed, n):
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        N = rng.choice([1, 63, 130, 257, 384, 513])
+        fT = rng.choice([37, 64, 100, 512, 777, 1024, 2048])
+        F = rng.choice([1, 2, 3, 4, 5, 8])
+        while N * N * F * fT > 1e9:
+            fT = max(1, fT // 2)
+        n_int = rng.randint(1, 3)
+        C = rng.randint(1, max(1, min(10, 12 // n_int)))
+        ring = rng.randint(2, 6)
+        dev = rng.random() < 0.5
+        out.append(pytest.param(N, fT, F, n_int, C, ring, dev, k,
+                                id=f"st{k}-N{N}-frame{fT}x{F}-int{n_int}-ch{C}-ring{ring}-{'dev' if dev else 'host'}"))
+    return out
+
+
+@pytest.mark.parametrize("N,fT,F,n_int,C,ring,dev,k", _stream_cases(31415926, 10))
+def test_stream_runs(xe, N, fT, F, n_int, C, ring, dev, k):
+    # Ragged frame lengths, 1 to 8 frames per integration, several channels pushed in a
+    # shuffled order every tick, and about 8 % of the frames lost (never a channel's last,
+    # whose loss only a later frame would reveal): every integration equals the oracle over
+    # the frames it received, with its sample count and completeness.
+    import time
+    rng = random.Random(k)
+    n_frames = F * n_int
+    data = {c: synth.uniform(N, fT * n_frames, 1, seed=5000 + 10 * k + c)[0].reshape(n_frames, fT, N)
+            for c in range(C)}
+    lost = {(c, q) for c in range(C) for q in range(n_frames - 1) if rng.random() < 0.08}
+    with xe.Stream(N, fT, F * fT, max_chan=16, hbm_budget=8 << 30, ring_frames=ring, device_source=dev) as st:
+        for c in range(C):
+            assert st.admit(c) == 0
+        for q in range(n_frames):
+            order = list(range(C))
+            rng.shuffle(order)
+            for c in order:
+                if (c, q) in lost:
+                    continue
+                fr = torch.from_numpy(np.ascontiguousarray(data[c][q]))
+                fr = fr.cuda() if dev else fr
+                t0 = time.time()
+                while st.push(c, fr, q) == xe.XE_EAGAIN:
+                    assert time.time() - t0 < 20, "push kept returning XE_EAGAIN"
+                    time.sleep(0.0005)
+        res = []
+        t0 = time.time()
+        while len(res) < C * n_int and time.time() - t0 < 30:
+            r = st.poll(timeout_ms=100)
+            if r is not None:
+                res.append(r)
+        assert len(res) == C * n_int, f"got {len(res)} of {C * n_int} integrations"
+        assert st.stats()["dropped"] == len(lost)
+    for meta, vis in res:
+        c, g = meta["chan"], meta["integ_index"]
+        got_frames = [q for q in range(g * F, (g + 1) * F) if (c, q) not in lost]
+        assert meta["n_samples"] == len(got_frames) * fT
+        assert meta["complete"] == (1 if len(got_frames) == F else 0)
+        if got_frames:
+            block = np.concatenate([data[c][q] for q in got_frames])[None]
+            want = oracle.correlate_dense(block, N, len(got_frames) * fT, 1)[0]
+        else:
+            want = np.zeros((oracle.n_baselines(N), 2), np.int32)
+        _assert_exact(vis, want, f"chan {c} integration {g}")
