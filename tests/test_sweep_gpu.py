@@ -6,7 +6,8 @@ exchanged parts, last-arriver sums, several segments per CTA and ragged edges ar
 together; some cases also take f16 operands or short exact windows (integrations split
 into windows that add into the output).  Batches also add into their outputs
 (correlate_accumulate).  Flag-masked calls (with and without counts, both encodings),
-phased-array beams and streaming runs (ragged frames, lost frames) get their own sweeps.  Every call goes through the C ABI."""
+phased-array beams, streaming runs (ragged frames, lost frames), the corner turn with
+bundle views, and the allocation-free and host-buffer entry points get their own sweeps.  Every call goes through the C ABI."""
 import random
 
 import numpy as np
@@ -254,3 +255,67 @@ def test_stream_runs(xe, N, fT, F, n_int, C, ring, dev, k):
         else:
             want = np.zeros((oracle.n_baselines(N), 2), np.int32)
         _assert_exact(vis, want, f"chan {c} integration {g}")
+
+
+def _corner_cases(seed, n):
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        n_cyl, n_freq = rng.randint(1, 4), rng.randint(1, 4)
+        n_in = rng.choice([1, 5, 16, 20, 64, 100, 128, 256])
+        T = rng.choice(T_EDGES)
+        while (n_cyl * n_in) ** 2 * T * n_freq > 1.5e9:
+            T = max(1, T // 2)
+        win = rng.choice([131072, 131072, 1024])
+        out.append(pytest.param(n_cyl, n_freq, n_in, T, win, k,
+                                id=f"ct{k}-cyl{n_cyl}-freq{n_freq}-in{n_in}-T{T}-win{win}"))
+    return out
+
+
+@pytest.mark.parametrize("n_cyl,n_freq,n_in,T,win,k", _corner_cases(14142135, 12))
+def test_corner_turn_and_bundle_views(xe, n_cyl, n_freq, n_in, T, win, k):
+    # The corner turn with pre-sums, and the correlation read straight from the bundles
+    # through an input view (with exact windows, so views with a time offset), both against
+    # the oracle's corner turn.
+    rs = np.random.default_rng(6000 + k)
+    b = rs.integers(0, 256, size=(n_cyl, T, n_freq, n_in), dtype=np.uint8)
+    bd = torch.from_numpy(b).cuda()
+    N = n_cyl * n_in
+    frames, ps = xe.corner_turn(bd, n_cyl, n_freq, n_in, T)
+    xe.set_option("exact_chunk_t", win)
+    vis = xe.correlate_bundles(bd, n_cyl, n_freq, n_in, T)
+    torch.cuda.synchronize()
+    xe.device_status()
+    want = oracle.corner_turn(b, n_cyl, n_freq, n_in, T)
+    _assert_exact(frames.cpu().numpy(), want, "frames")
+    _assert_exact(ps.cpu().numpy(), oracle.presum(want, N, T, n_freq), "pre-sums")
+    _assert_exact(vis.cpu().numpy(), oracle.correlate_dense(want, N, T, n_freq), "bundle-view visibilities")
+
+
+def _entry_cases(seed, n):
+    rng = random.Random(seed)
+    out = []
+    for k in range(n):
+        N, T = rng.choice(N_EDGES), rng.choice(T_EDGES)
+        while N * N * T > 1.5e9:
+            T = max(1, T // 2)
+        C = rng.randint(1, 3)
+        out.append(pytest.param(N, T, C, k, id=f"e{k}-{N}x{T}x{C}"))
+    return out
+
+
+@pytest.mark.parametrize("N,T,C,k", _entry_cases(17320508, 12))
+def test_noalloc_and_host_entry_points(xe, N, T, C, k):
+    # The allocation-free entry point, the synchronous host-buffer call and the slotted
+    # asynchronous host-buffer call on the same input: each equals the oracle.
+    p = synth.uniform(N, T, C, seed=7000 + k)
+    want = oracle.correlate_dense(p, N, T, C)
+    got = xe.correlate_noalloc(torch.from_numpy(p).cuda(), N, T, C)
+    torch.cuda.synchronize()
+    xe.noalloc_status()
+    _assert_exact(got.cpu().numpy(), want, "noalloc")
+    host = torch.from_numpy(p).pin_memory()
+    _assert_exact(xe.correlate_host(host, N, T, C).numpy(), want, "host")
+    out, slot = xe.correlate_host_async(host, N, T, C, slot=k % xe.HOST_SLOTS)
+    xe.host_wait(slot)
+    _assert_exact(out.numpy(), want, "host async")
