@@ -270,6 +270,22 @@ def test_schedules_cover_every_tile_and_k_once(sched, tile_n):
         _check_plan(shapes, n_cta, sched, tile_n)
 
 
+@pytest.mark.parametrize("seed", range(12))
+def test_plan_sweep_covers_every_tile_and_k_once(seed):
+    # Seeded batches at the tile and k-block edges under every schedule (and the automatic
+    # choice), tile width and CTA count from 1 to beyond one per SM: each plan covers every
+    # baseline of every job and channel once, every k-block of every tile once, and gives
+    # the parts of each split tile distinct workspace slots.
+    rng = np.random.default_rng(100 + seed)
+    Ns = [1, 2, 63, 64, 65, 127, 128, 129, 255, 256, 257, 511, 513, 1023, 1025, 2048]
+    Ts = [1, 63, 64, 65, 1000, 4096, 8193, 32768, 65536]
+    for _ in range(10):
+        shapes = [(int(rng.choice(Ns)), int(rng.choice(Ts)), int(rng.integers(1, 3)))
+                  for _ in range(int(rng.integers(1, 5)))]
+        n_cta = int(rng.choice([1, 2, 5, 37, 144, 152, 300]))
+        _check_plan(shapes, n_cta, int(rng.choice([-1, 0, 1, 2, 3, 4])), int(rng.choice([0, 128, 256])))
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_lpt_schedule_is_the_greedy_longest_first(seed):
     # The uneven-batch schedule against a plain heap greedy: tiles longest first (ties in tile
