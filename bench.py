@@ -28,6 +28,7 @@ import hashlib
 import re
 import json
 import os
+import platform
 import statistics
 import subprocess
 import sys
@@ -637,6 +638,7 @@ def run_stream_workload(args):
             "realtime_channels": best["channels"] if best else 0,
             "p50_frame_latency_ms": best["p50_latency_ms"] if best else None,
             "p99_frame_latency_ms": best["p99_latency_ms"] if best else None,
+            "latency_hist_ms": best["latency_hist_ms"] if best else None,
             "ramp": runs}
     print(json.dumps(line), flush=True)
     return 0
@@ -911,7 +913,8 @@ def main():
             "sampled_exact": sampled_exact,
             "p99_frame_latency_ms": stream["p99_latency_ms"] if stream else None,
             "stream": ({k: stream[k] for k in ("channels", "sustained", "cmac_per_s", "p50_latency_ms",
-                                               "p99_latency_ms", "max_latency_ms", "frame_T", "integ_T",
+                                               "p99_latency_ms", "max_latency_ms", "latency_hist_ms",
+                                               "frame_T", "integ_T",
                                                "device_source", "producer_late_frames", "push_overruns",
                                                "frames_dropped", "drain_s", "counters")}
                        if stream else None),
@@ -927,6 +930,7 @@ def main():
             "small": small,
             "paper_context": {"fiji_chip_cmac_s": 1.10e12, "note": "derived from Table tab:computing "
                               "(93.4 ms per 49152-sample block at N=2048), AMD S9300x2, 722 MHz"},
+            "host": {"nproc": os.cpu_count(), "machine": platform.machine()},
         }
         print(json.dumps(line), flush=True)
     if dist is not None:

@@ -16,6 +16,8 @@ import time
 from . import xe
 
 CHIME_RATE = 390625.0
+# Lower edges (ms) of the frame-to-visibility latency histogram's buckets; the last is open.
+LATENCY_EDGES_MS = (0, 10, 20, 40, 80, 160, 320, 640)
 
 
 def per_channel_bytes(N: int, frame_T: int, ring_frames: int) -> int:
@@ -111,6 +113,10 @@ def _run_realtime(n_chan, seconds, N, frame_T, integ_T, rate, device_source, rin
         counters = st.counters()
     lat = sorted(lat_ns)
     pct = (lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] / 1e6) if lat else (lambda q: None)
+    # frame-to-visibility latency histogram: integrations per bucket [edge k, edge k + 1) ms
+    edges = list(LATENCY_EDGES_MS) + [None]
+    hist = [sum(1 for v in lat if v / 1e6 >= lo and (hi is None or v / 1e6 < hi))
+            for lo, hi in zip(edges[:-1], edges[1:])]
     cmac_frame = N * (N + 1) / 2 * frame_T
     span = t_last_push - t0 + frame_period
     realtime = span <= n_frames * frame_period * 1.02 + 0.01
@@ -125,6 +131,7 @@ def _run_realtime(n_chan, seconds, N, frame_T, integ_T, rate, device_source, rin
         "cmac_per_s": stats["frames"] * cmac_frame / span,
         "p50_latency_ms": pct(0.50), "p99_latency_ms": pct(0.99),
         "max_latency_ms": (lat[-1] / 1e6) if lat else None,
+        "latency_hist_ms": {"edges": list(LATENCY_EDGES_MS), "counts": hist},
         "drain_s": t_end - t_last_push, "device_source": device_source, "counters": counters,
         "frame_T": frame_T, "integ_T": integ_T, "N": N, "rate": rate,
     }
