@@ -75,49 +75,60 @@ __host__ __device__ constexpr uint32_t beam_tmem_cols(int ncols) {
 __device__ __forceinline__ int w_lo(int w) { return ((w + 8) & 15) - 8; }
 __device__ __forceinline__ int w_hi(int w) { return (w - w_lo(w)) / 16; }
 
-// One thread per 16-byte piece of the tile image: (chunk k, sub-tile s, row col, piece q)
-// holds inputs n = 64k + 32s + 8q .. +7, each as two e4m3 codes {K = (n, im), K = (n, re)}
-// (the order the converters produce, the nibble order of a packed sample):
+// One thread per 32-bit word of the tile image: word u of 16-byte piece q of row col of
+// (chunk k, sub-tile s) holds inputs n = 64k + 32s + 8q + 2u and n + 1, each as two e4m3
+// codes {K = (n, im), K = (n, re)} (the order the converters produce, the nibble order of a
+// packed sample):
 //   Re rows (col % 4 = 0 hi, 2 lo):  { -w_i, w_r }     Im rows (col % 4 = 1 hi, 3 lo): { w_r, w_i }
 // of weight beam b0 + col / 4.  Rows past the launch's nb beams and inputs n >= N are zero.
+// The four weight bytes of the two inputs are one aligned 32-bit load where they can be.
 __global__ void beam_weight_kernel(const int8_t *__restrict__ w, int b0, int nb, int N, int ncols,
                                    int n_chunks, uint8_t *__restrict__ wt) {
-    const int64_t total = int64_t(n_chunks) * kBeamSub * ncols * 4;
+    const int64_t total = int64_t(n_chunks) * kBeamSub * ncols * 16;
     for (int64_t e = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; e < total;
          e += int64_t(gridDim.x) * blockDim.x) {
-        const int q = int(e & 3);
-        const int col = int((e >> 2) % ncols);
-        const int64_t ks = (e >> 2) / ncols;                 // k * 2 + s
+        const int u2 = int(e & 3), q = int((e >> 2) & 3);
+        const int col = int((e >> 4) % ncols);
+        const int64_t ks = (e >> 4) / ncols;                 // k * kBeamSub + s
         const int b = col >> 2, part = col & 3;
-        uint32_t v[4];
+        const int64_t n0 = ks * 32 + 8 * q + 2 * u2;
+        int wv[2][2] = {{0, 0}, {0, 0}};                     // [input][re, im]
+        if (b < nb && n0 < N) {
+            const int8_t *src = w + (int64_t(b0 + b) * N + n0) * 2;
+            if (n0 + 1 < N && (reinterpret_cast<uintptr_t>(src) & 3) == 0) {
+                const uint32_t x = *reinterpret_cast<const uint32_t *>(src);
 #pragma unroll
-        for (int u2 = 0; u2 < 4; ++u2) {
-            uint32_t pair = 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                const int64_t n = ks * 32 + 8 * q + 2 * u2 + h;
-                int wr = 0, wi = 0;
-                if (b < nb && n < N) {
-                    wr = w[(int64_t(b0 + b) * N + n) * 2 + 0];
-                    wi = w[(int64_t(b0 + b) * N + n) * 2 + 1];
+                for (int h = 0; h < 2; ++h) {
+                    wv[h][0] = int(int8_t(x >> (16 * h)));
+                    wv[h][1] = int(int8_t(x >> (16 * h + 8)));
                 }
-                const bool hi = part < 2;
-                const int pr = hi ? w_hi(wr) : w_lo(wr), pi = hi ? w_hi(wi) : w_lo(wi);
-                const bool im_row = part & 1;
-                const int k_re = im_row ? pi : pr;      // coefficient of the input's re part
-                const int k_im = im_row ? pr : -pi;     // coefficient of its im part
-                pair |= (encode_small_int(k_im, 1) | (encode_small_int(k_re, 1) << 8)) << (16 * h);
+            } else {
+                wv[0][0] = src[0];
+                wv[0][1] = src[1];
+                if (n0 + 1 < N) {
+                    wv[1][0] = src[2];
+                    wv[1][1] = src[3];
+                }
             }
-            v[u2] = pair;
         }
-        uint8_t *dst = wt + (ks * ncols + col) * 64 + ((q ^ ((col >> 1) & 3)) << 4);
-        *reinterpret_cast<uint4 *>(dst) = make_uint4(v[0], v[1], v[2], v[3]);
+        const bool hi = part < 2, im_row = part & 1;
+        uint32_t pair = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int wr = wv[h][0], wi = wv[h][1];
+            const int pr = hi ? w_hi(wr) : w_lo(wr), pi = hi ? w_hi(wi) : w_lo(wi);
+            const int k_re = im_row ? pi : pr;      // coefficient of the input's re part
+            const int k_im = im_row ? pr : -pi;     // coefficient of its im part
+            pair |= (encode_small_int(k_im, 1) | (encode_small_int(k_re, 1) << 8)) << (16 * h);
+        }
+        uint8_t *dst = wt + (ks * ncols + col) * 64 + ((q ^ ((col >> 1) & 3)) << 4) + 4 * u2;
+        *reinterpret_cast<uint32_t *>(dst) = pair;
     }
 }
 
 cudaError_t launch_beam_weights(const int8_t *w, int b0, int nb, int N, int ncols, uint8_t *wt, cudaStream_t s) {
     const int n_chunks = (N + kBeamChunk - 1) / kBeamChunk;
-    const int64_t total = int64_t(n_chunks) * kBeamSub * ncols * 4;
+    const int64_t total = int64_t(n_chunks) * kBeamSub * ncols * 16;
     const int64_t blocks = (total + 255) / 256;
     beam_weight_kernel<<<unsigned(blocks < 4096 ? blocks : 4096), 256, 0, s>>>(w, b0, nb, N, ncols, n_chunks, wt);
     return cudaGetLastError();
