@@ -20,6 +20,14 @@ CHIME_RATE = 390625.0
 LATENCY_EDGES_MS = (0, 10, 20, 40, 80, 160, 320, 640)
 
 
+def latency_histogram(lat_ns) -> list[int]:
+    """Counts of latencies (ns) per bucket [LATENCY_EDGES_MS[k], LATENCY_EDGES_MS[k + 1]) ms,
+    the last bucket open-ended."""
+    edges = list(LATENCY_EDGES_MS) + [None]
+    return [sum(1 for v in lat_ns if v / 1e6 >= lo and (hi is None or v / 1e6 < hi))
+            for lo, hi in zip(edges[:-1], edges[1:])]
+
+
 def per_channel_bytes(N: int, frame_T: int, ring_frames: int) -> int:
     """Device bytes one channel slot holds: accumulators + frame ring + staging share (up to
     min(4, ring_frames) frames of a channel are correlated as one job)."""
@@ -113,10 +121,7 @@ def _run_realtime(n_chan, seconds, N, frame_T, integ_T, rate, device_source, rin
         counters = st.counters()
     lat = sorted(lat_ns)
     pct = (lambda q: lat[min(len(lat) - 1, int(q * len(lat)))] / 1e6) if lat else (lambda q: None)
-    # frame-to-visibility latency histogram: integrations per bucket [edge k, edge k + 1) ms
-    edges = list(LATENCY_EDGES_MS) + [None]
-    hist = [sum(1 for v in lat if v / 1e6 >= lo and (hi is None or v / 1e6 < hi))
-            for lo, hi in zip(edges[:-1], edges[1:])]
+    hist = latency_histogram(lat)
     cmac_frame = N * (N + 1) / 2 * frame_T
     span = t_last_push - t0 + frame_period
     realtime = span <= n_frames * frame_period * 1.02 + 0.01

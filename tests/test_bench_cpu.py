@@ -77,3 +77,14 @@ def test_main_arm_fails_loudly_without_a_gpu():
                        cwd=bench.ROOT, capture_output=True, text=True, timeout=300)
     assert r.returncode != 0
     assert not [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+
+
+def test_latency_histogram_buckets():
+    from paper_2005_09481_gb300 import serve
+    ms = 1_000_000
+    lat = [0, 9 * ms, 10 * ms, 19.9 * ms, 45 * ms, 639 * ms, 640 * ms, 5000 * ms]
+    h = serve.latency_histogram(lat)
+    assert len(h) == len(serve.LATENCY_EDGES_MS)
+    assert h == [2, 2, 0, 1, 0, 0, 1, 2]
+    assert sum(h) == len(lat)
+    assert serve.latency_histogram([]) == [0] * len(serve.LATENCY_EDGES_MS)
