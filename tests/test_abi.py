@@ -582,3 +582,28 @@ def test_check_corruption_hook_needs_the_checks():
     assert L.xe_set_option(b"checks", 0) == xe.XE_OK      # also clears the hook
     assert L.xe_set_option(b"check_corrupt", 0) == xe.XE_OK
     assert L.xe_strerror(xe.XE_ECHECK).startswith(b"a device-side check")
+
+
+def test_stream_config_validation_before_any_device_call():
+    # Every field of the stream configuration is checked before the library touches a
+    # device: bad shapes are XE_EINVAL, an integration too long for int32 sums XE_EOVERFLOW.
+    L = xe.load()
+    good = dict(N=64, frame_T=1024, integ_T=4096, max_chan=4, hbm_budget=1 << 30, ring_frames=3)
+
+    def opened(**kw):
+        c = dict(good, **kw)
+        cfg = xe.StreamCfg(c["N"], c["frame_T"], c["integ_T"], c["max_chan"], c["hbm_budget"],
+                           c["ring_frames"], 390625.0, 0)
+        h = ctypes.c_void_p()
+        rc = L.xe_stream_open(ctypes.byref(cfg), ctypes.byref(h))
+        if rc == xe.XE_OK:
+            L.xe_stream_close(h)
+        return rc
+
+    for kw in (dict(N=0), dict(N=xe.XE_MAX_N + 1), dict(frame_T=0), dict(frame_T=131073, integ_T=131073),
+               dict(integ_T=1000), dict(integ_T=4097), dict(max_chan=0), dict(max_chan=65537),
+               dict(ring_frames=1), dict(ring_frames=65)):
+        assert opened(**kw) == xe.XE_EINVAL, kw
+    assert opened(frame_T=8192, integ_T=8192 * 2049) == xe.XE_EOVERFLOW
+    assert opened() in (xe.XE_OK, xe.XE_ENODEV)
+    assert L.xe_stream_open(None, None) == xe.XE_EINVAL
